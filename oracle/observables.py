@@ -1,0 +1,66 @@
+"""Observables of a walk state.  TEST INFRASTRUCTURE.
+
+* norm:            sum_x |psi(x)|^2 (unitarity, Eq. un-cond).
+* mean position:   <psi|X|psi> / <psi|psi> with X the lattice position operator
+                   (Sec. 5.2, X = sum_x x |x><x| (x) I), coordinates in the
+                   fixed window [0, N) of the periodic box (lattice coordinates
+                   (a, b) in 2D, physical coordinates in 3D).
+* particle weight: the weight of the positive-frequency part, i.e. of the
+                   eigenspace of U_k with eigenvalue exp(-i omega_k) (Eq. eigen-D,
+                   s = +).  U_k = cos(omega) I - i G_k with G_k Hermitian, so
+                   G_k = i (U_k - U_k^dagger)/2 and the projector is
+                   (I + sgn(G_k))/2, sgn taken through a Hermitian eigensolver,
+                   with sgn(0) = 0 where omega_k is 0 or pi (both halves share).
+"""
+
+import numpy as np
+
+from .walk import site_coordinates
+from .spectral import dft, symbol_grid
+
+__all__ = ["norm", "mean_position", "particle_weights", "projectors"]
+
+
+def norm(psi):
+    """sum |psi|^2 over sites and components."""
+    return float(np.sum(np.abs(np.asarray(psi)) ** 2))
+
+
+def mean_position(dim, psi):
+    """<x_i> = sum x_i |psi(x)|^2 / sum |psi(x)|^2, one value per axis."""
+    psi = np.asarray(psi)
+    N = psi.shape[1]
+    dens = np.sum(np.abs(psi) ** 2, axis=0)
+    tot = np.sum(dens)
+    return [float(np.sum(c * dens) / tot) for c in site_coordinates(dim, N)]
+
+
+def projectors(D):
+    """(P_plus, P_minus) for stacked unitary symbols D (..., s, s)."""
+    G = 0.5j * (D - np.conj(np.swapaxes(D, -1, -2)))
+    G = 0.5 * (G + np.conj(np.swapaxes(G, -1, -2)))
+    lam, V = np.linalg.eigh(G)
+    scale = np.max(np.abs(lam), axis=-1, keepdims=True)
+    sgn = np.where(lam > 1e-13, 1.0, np.where(lam < -1e-13, -1.0, 0.0))
+    sgn = np.where(scale > 1e-13, sgn, 0.0)
+    S = np.einsum("...ij,...j,...kj->...ik", V, sgn, np.conj(V))
+    eye = np.eye(D.shape[-1])
+    return 0.5 * (eye + S), 0.5 * (eye - S)
+
+
+def particle_weights(dim, m, psi, chunk=1 << 16):
+    """(w_plus, w_minus): weights of the positive / negative frequency parts."""
+    psi = np.asarray(psi, dtype=complex)
+    s = psi.shape[0]
+    N = psi.shape[1]
+    ph = dft(psi, dim).reshape(s, -1)
+    D = symbol_grid(dim, m, N).reshape(-1, s, s)
+    wp = wm = 0.0
+    for lo in range(0, D.shape[0], chunk):
+        hi = min(lo + chunk, D.shape[0])
+        Pp, Pm = projectors(D[lo:hi])
+        v = ph[:, lo:hi].T
+        wp += float(np.real(np.einsum("ki,kij,kj->", np.conj(v), Pp, v)))
+        wm += float(np.real(np.einsum("ki,kij,kj->", np.conj(v), Pm, v)))
+    tot = float(np.sum(np.abs(ph) ** 2))
+    return wp / tot, wm / tot
