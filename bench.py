@@ -1,0 +1,306 @@
+"""Benchmark of the Dirac quantum-walk hot path on GB300.
+
+Default workload: the BCC box N = 512 (33,554,432 sites, 1.07 GB complex64 field,
+larger than L2), m = 0.1, a Gaussian packet of width 32 sites.  One bench step =
+S stencil steps of the walk (qw_step, complex64) followed by the observables
+reduction (qw_observables, FP64 accumulation).  `value` = site-steps/s over the
+timed steps; the roofline object reports the stencil kernel's achieved HBM
+bandwidth (algorithmic bytes: one read + one write of the field per launch)
+against the measured copy bandwidth.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the slow plain program) on a
+bounded sample of the same workload, on the host cores.
+Multi-GPU (torchrun): replicas only -- every rank runs the same workload on its
+own GPU with no collective on the data path; value = all ranks' site-steps over
+the slowest rank's time.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = {"name": "bcc_N512_stencil_c64", "dim": 3, "N": 512, "mass": 0.1, "sigma": 32.0,
+            "k0": (0.3, 0.2, 0.1), "substeps": 20}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--N", type=int, default=None, help="override the box side (profiling runs)")
+    ap.add_argument("--substeps", type=int, default=None, help="override stencil steps per bench step")
+    args = ap.parse_args()
+    if args.N is not None:
+        WORKLOAD["N"] = args.N
+        WORKLOAD["name"] = "bcc_N%d_stencil_c64" % args.N
+    if args.substeps is not None:
+        WORKLOAD["substeps"] = args.substeps
+    return args
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "qw_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_cpu_baseline(seconds=12.0):
+    """FP64 oracle (numpy) stencil on a bounded BCC sample: site-steps/s on the host."""
+    from oracle import walk
+    from paper_1603_06442_gb300 import inputs
+    N = 64
+    m = WORKLOAD["mass"]
+    a = inputs.gaussian_packet(3, N, (N / 2,) * 3, N / 16, WORKLOAD["k0"], [0.5, 0.5, 0.5, 0.5])
+    psi = walk.from_device(3, N, a)
+    mats = walk.transition_matrices(3, m)
+    sites = N ** 3 // 4
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        psi = walk.step(3, m, psi, 1, mats=mats)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": sites * steps / dt, "unit": "site-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "BCC N=64 box (%d sites), %d oracle update steps in FP64 numpy, %.1f s" % (sites, steps, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    t_steps = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_cpu_baseline(seconds=3.0)
+        if i >= args.warmup:
+            t_steps.append(r)
+        base = r
+    vals = [r["value"] for r in t_steps]
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": "site-steps/s", "value": v, "unit": "site-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 3000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "note": "oracle timed on a bounded BCC N=64 sample"},
+            "cpu_baseline": {"value": v, "unit": "site-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": v, "unit": "site-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1603_06442_gb300 import binding as qb, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    W = WORKLOAD
+    dim, N, S = W["dim"], W["N"], W["substeps"]
+    plan = qb.Plan(dim, N, W["mass"], "c64")
+    a = inputs.gaussian_packet(dim, N, (N / 2,) * 3, W["sigma"], W["k0"], [0.5, 0.5j, 0.5, -0.5j])
+    host = torch.from_numpy(a.astype(np.complex64)).pin_memory()
+    psi = host.to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sites = plan.sites
+    field_bytes = plan.elems * 8
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up
+    for _ in range(args.warmup):
+        plan.step(psi, S, stream)
+        plan.observables(psi, stream)
+    barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clocks:
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            plan.step(psi, S, stream)
+            ev[i][1].record(stream)
+            obs = plan.observables(psi, stream)
+            ev[i][2].record(stream)
+        t_end.record(stream)
+        barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    stencil_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
+    ms = total_ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = sites * S * args.steps * world / (ms / 1e3)
+    launches_per_step = S + (1 if S % 2 else 0) + 2
+
+    # end-to-end through the public API with host buffers: H2D of the field,
+    # S steps, observables read back to the host, every step.
+    e2e_ms = None
+    e2e_steps = max(2, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        psi.copy_(host, non_blocking=True)
+        plan.step(psi, S, stream)
+        plan.observables(psi, stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra = extra_measurements(qb, dev, stream)
+
+    if rank != 0:
+        plan.close()
+        return
+    peak, peak_kind = measured_peaks()
+    per_launch_ms = stencil_ms / (args.steps * S)
+    achieved = 2 * field_bytes / (per_launch_ms / 1e3) / 1e9
+    line = {
+        "metric": "site-steps/s", "value": value, "unit": "site-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+        "data": "synthetic",
+        "config": {"workload": W["name"], "dim": dim, "N": N, "sites": sites, "mass": W["mass"],
+                   "stencil_steps_per_step": S, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "no flush: the %.2f GB field is larger than L2 (129 MB)" % (field_bytes / 1e9),
+                   "input": "Gaussian packet sigma=%g sites, k0=%s" % (W["sigma"], list(W["k0"]))},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "step3d_kernel<float>", "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": 2 * field_bytes,
+                     "avg_launch_ms": per_launch_ms},
+        "e2e": {"value": sites * S / (e2e_ms / 1e3), "unit": "site-steps/s",
+                "h2d_bytes_per_step": field_bytes, "d2h_bytes_per_step": 48, "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps * launches_per_step,
+        "clocks": clocks.summary(),
+        "final_obs": obs,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = oracle_cpu_baseline()
+    if extra:
+        line["extra"] = extra
+    plan.close()
+    print(json.dumps(line), flush=True)
+
+
+def extra_measurements(qb, dev, stream):
+    """Secondary numbers of the metric: FP64 plain stencil on the same box."""
+    import torch
+    out = {}
+    W = WORKLOAD
+    plan = qb.Plan(3, W["N"], W["mass"], "c128")
+    psi = torch.zeros(plan.elems, dtype=torch.complex128, device=dev)
+    psi[::7] = 1e-3
+    plan.step(psi, 2, stream)
+    torch.cuda.synchronize(dev)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 6
+    s0.record(stream)
+    plan.step(psi, n, stream)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = s0.elapsed_time(s1) / n
+    out["fp64_stencil"] = {"site_steps_per_s": plan.sites / (ms / 1e3), "ms_per_step": ms,
+                           "hbm_GBps": 2 * plan.elems * 16 / (ms / 1e3) / 1e9}
+    plan.close()
+    return out
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,112 @@
+/*
+ * qw.h -- C ABI of the GB300 Dirac quantum-walk library (libqw.so).
+ *
+ * The walk is the Dirac quantum walk of D'Ariano, Mosco, Perinotti, Tosini,
+ * "Discrete Time Dirac Quantum Walk in 3+1 Dimensions" (Entropy 2016):
+ * a 2-component spinor field on the periodic chain (Sec. 3.2, decoupled 1D
+ * walk) or a 4-component field on the periodic square lattice (Eq. weyl2d) or
+ * BCC lattice (Eqs. bcc-vecs, weyl3d), coupled by the mass m with n^2 + m^2 = 1
+ * (Sec. 3.2).  One step is the update rule of Eq. upd-rule,
+ *     psi'(x) = sum_{h in S + {0}} U_h psi(x - h),
+ * whose Fourier symbol is D_k = sum_h exp(-i k.h) U_h (Eq. walk-K).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Field layout ("device layout"), complex values interleaved (re, im):
+ *   dim 1: [s=2][x]          N sites
+ *   dim 2: [s=4][y][x]       N x N sites, lattice coordinates (x, y) = (a, b)
+ *                            along h1 = (1,0), h2 = (0,1)
+ *   dim 3: [c=2][s=4][z][y][x], M = N/2 cells per axis.  Coset c holds the BCC
+ *                            site with physical coordinates 2*(x,y,z) + c*(1,1,1)
+ *                            of the periodic box [0,N)^3 (Sec. 4, the vertex set
+ *                            2Z^3 u (2Z^3 + t)); N must be even.
+ * Element type: QW_C64 = two float32 (8 bytes), QW_C128 = two float64 (16 bytes).
+ * Field pointers are DEVICE pointers (cudaMalloc / torch CUDA tensors) unless a
+ * name says _host; they must be aligned to the element size and hold
+ * qw_plan_field_elems(plan) elements.  The caller owns them.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls are asynchronous on that stream unless stated otherwise.
+ * Errors: every call returns a qw_status and never aborts; a failed CUDA call
+ * gives QW_ECUDA.  qw_last_error() returns the message of the calling thread's
+ * last failure.  Plans are not thread-safe: one host thread per plan at a time.
+ */
+#ifndef QW_H
+#define QW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QW_OK = 0,
+  QW_EINVAL = 1,    /* bad argument (dimension, size, mass, null pointer, ...) */
+  QW_ENOMEM = 2,    /* device or host allocation failed                     */
+  QW_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed           */
+  QW_ETIMEOUT = 4,  /* a bounded device- or host-side wait gave up           */
+  QW_EAGAIN = 5,    /* not admitted now (budget / queue full); try later     */
+  QW_EBUSY = 6,     /* object in use                                         */
+  QW_ENOTFOUND = 7  /* unknown ticket                                        */
+} qw_status;
+
+typedef enum { QW_C64 = 0, QW_C128 = 1 } qw_dtype;
+
+typedef struct qw_plan_s* qw_plan;
+
+/* Observables of one field (Sec. 5.2): the norm sum_x |psi(x)|^2; the mean
+ * position <x_i> = sum_x x_i |psi(x)|^2 / norm per axis in the fixed window
+ * [0, N) of the periodic box (physical coordinates in 3D, lattice coordinates
+ * in 2D; unused axes are 0); the weights of the positive- and negative-
+ * frequency parts (eigenvalue exp(-+i omega_k) of D_k, Eq. eigen-D), i.e.
+ * sum_k psi^_k^dag (I +- G_k/sin(omega_k))/2 psi^_k / sum_k |psi^_k|^2 where
+ * D_k = cos(omega_k) I - i G_k; at sin(omega_k) = 0 both halves share. */
+typedef struct {
+  double norm;
+  double x_mean[3];
+  double w_particle;
+  double w_antiparticle;
+} qw_obs;
+
+/* Last error message of the calling thread ("" if none).  Never NULL. */
+const char* qw_last_error(void);
+
+/* Library version string. */
+const char* qw_version(void);
+
+/* Create a plan for the walk of dimension `dim` (1, 2 or 3) on the periodic box
+ * of side N (N >= 2; even for dim 3), mass m in [0, 1] (n = sqrt(1 - m^2),
+ * Sec. 3.2) and element type `dtype`.  Allocates on the current CUDA device a
+ * scratch field of the same size (ping-pong buffer) and small reduction
+ * buffers; the plan owns them.  *out receives the plan.
+ * Errors: QW_EINVAL (bad dim/N/m/dtype, null out), QW_ENOMEM, QW_ECUDA. */
+qw_status qw_plan_create(int dim, int64_t N, double mass, qw_dtype dtype, qw_plan* out);
+
+/* Release a plan and its device memory (synchronises the device first). */
+qw_status qw_plan_destroy(qw_plan plan);
+
+/* Number of complex elements of one field in the device layout
+ * (s * sites: 2N, 4N^2, or 2*4*(N/2)^3); -1 for a null plan. */
+int64_t qw_plan_field_elems(qw_plan plan);
+
+/* Number of lattice sites (N, N^2, or N^3/4 for the BCC box); -1 for null. */
+int64_t qw_plan_sites(qw_plan plan);
+
+/* Advance psi_dev in place by `nsteps` >= 0 applications of the update rule
+ * (Eq. upd-rule; the plain position-space form of Sec. 4).  Uses the plan's
+ * scratch field; the stencil variant (temporal fusion depth, tile) is the one
+ * chosen by the plan (see qw_plan_set_fusion).  Asynchronous on `stream`.
+ * Errors: QW_EINVAL (null plan/pointer, nsteps < 0), QW_ECUDA. */
+qw_status qw_step(qw_plan plan, void* psi_dev, int64_t nsteps, void* stream);
+
+/* Compute the observables of psi_dev (see qw_obs).  Blocks the host until the
+ * reductions on `stream` are done, then fills *out.
+ * Errors: QW_EINVAL, QW_ECUDA. */
+qw_status qw_observables(qw_plan plan, const void* psi_dev, qw_obs* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QW_H */

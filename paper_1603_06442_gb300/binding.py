@@ -1,0 +1,178 @@
+"""Thin ctypes binding of libqw.so: the C ABI of include/qw.h under the same names.
+
+Argument marshalling only.  Fields are CUDA tensors (torch complex64 /
+complex128, contiguous, device layout of include/qw.h) or raw device addresses;
+streams default to torch's current stream.  Every step of the walk runs in the
+CUDA library; if libqw.so is missing this module raises instead of falling back.
+"""
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libqw.so")
+
+QW_OK, QW_EINVAL, QW_ENOMEM, QW_ECUDA, QW_ETIMEOUT, QW_EAGAIN, QW_EBUSY, QW_ENOTFOUND = range(8)
+QW_C64, QW_C128 = 0, 1
+STATUS_NAMES = {0: "QW_OK", 1: "QW_EINVAL", 2: "QW_ENOMEM", 3: "QW_ECUDA", 4: "QW_ETIMEOUT",
+                5: "QW_EAGAIN", 6: "QW_EBUSY", 7: "QW_ENOTFOUND"}
+
+
+class QwError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class qw_obs(ctypes.Structure):
+    _fields_ = [("norm", ctypes.c_double), ("x_mean", ctypes.c_double * 3),
+                ("w_particle", ctypes.c_double), ("w_antiparticle", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"norm": self.norm, "x_mean": list(self.x_mean), "w_particle": self.w_particle,
+                "w_antiparticle": self.w_antiparticle}
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "qw_last_error": (ctypes.c_char_p, []),
+    "qw_version": (ctypes.c_char_p, []),
+    "qw_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "qw_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "qw_plan_field_elems": (ctypes.c_int64, [ctypes.c_void_p]),
+    "qw_plan_sites": (ctypes.c_int64, [ctypes.c_void_p]),
+    "qw_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "qw_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(qw_obs),
+                                      ctypes.c_void_p]),
+}
+
+
+def exported_names():
+    return list(_SIGS)
+
+
+def load(path=LIB_PATH):
+    """Load libqw.so once; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libqw.so not found at %s: build it first (__graft_entry__.build())" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != QW_OK:
+        raise QwError(status, load().qw_last_error().decode())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def qw_last_error():
+    return load().qw_last_error().decode()
+
+
+def qw_version():
+    return load().qw_version().decode()
+
+
+def qw_plan_create(dim, N, mass, dtype):
+    h = ctypes.c_void_p()
+    _check(load().qw_plan_create(int(dim), int(N), float(mass), int(dtype), ctypes.byref(h)))
+    return h.value
+
+
+def qw_plan_destroy(plan):
+    _check(load().qw_plan_destroy(plan))
+
+
+def qw_plan_field_elems(plan):
+    return load().qw_plan_field_elems(plan)
+
+
+def qw_plan_sites(plan):
+    return load().qw_plan_sites(plan)
+
+
+def qw_step(plan, psi, nsteps, stream=None):
+    _check(load().qw_step(plan, _ptr(psi), int(nsteps), _stream(stream)))
+
+
+def qw_observables(plan, psi, stream=None):
+    out = qw_obs()
+    _check(load().qw_observables(plan, _ptr(psi), ctypes.byref(out), _stream(stream)))
+    return out.as_dict()
+
+
+class Plan:
+    """Owning wrapper of a qw_plan (destroyed with the object)."""
+
+    def __init__(self, dim, N, mass, dtype="c64"):
+        self.dim, self.N, self.mass = int(dim), int(N), float(mass)
+        self.dtype = QW_C64 if dtype in ("c64", QW_C64) else QW_C128
+        self.handle = qw_plan_create(self.dim, self.N, self.mass, self.dtype)
+        self.elems = qw_plan_field_elems(self.handle)
+        self.sites = qw_plan_sites(self.handle)
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.complex64 if self.dtype == QW_C64 else torch.complex128
+
+    def field_shape(self):
+        N = self.N
+        if self.dim == 1:
+            return (2, N)
+        if self.dim == 2:
+            return (4, N, N)
+        M = N // 2
+        return (2, 4, M, M, M)
+
+    def check_field(self, psi):
+        if not psi.is_cuda or not psi.is_contiguous() or psi.dtype != self.torch_dtype \
+                or psi.numel() != self.elems:
+            raise ValueError("field must be a contiguous CUDA %s tensor with %d elements"
+                             % (self.torch_dtype, self.elems))
+
+    def step(self, psi, nsteps, stream=None):
+        self.check_field(psi)
+        qw_step(self.handle, psi, nsteps, stream)
+
+    def observables(self, psi, stream=None):
+        self.check_field(psi)
+        return qw_observables(self.handle, psi, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            qw_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,174 @@
+// C ABI entry points: errors, plans, the stepping driver and observables.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "qw_internal.cuh"
+
+namespace qw {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+qw_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return e == cudaErrorMemoryAllocation ? QW_ENOMEM : QW_ECUDA;
+}
+
+bool make_geometry(int dim, int64_t N, Geometry* g) {
+  if (dim < 1 || dim > 3 || N < 2) return false;
+  g->dim = dim;
+  g->N = N;
+  g->s = (dim == 1) ? 2 : 4;
+  if (dim == 1) {
+    g->ncoset = 1;
+    g->nx = N;
+    g->ny = g->nz = 1;
+  } else if (dim == 2) {
+    g->ncoset = 1;
+    g->nx = g->ny = N;
+    g->nz = 1;
+  } else {
+    if (N % 2 != 0) return false;
+    g->ncoset = 2;
+    g->nx = g->ny = g->nz = N / 2;
+  }
+  g->vol = g->nx * g->ny * g->nz;
+  g->elems = (int64_t)g->ncoset * g->s * g->vol;
+  g->sites = (int64_t)g->ncoset * g->vol;
+  return true;
+}
+
+static qw_status use_device(const qw_plan_s* p) {
+  int cur = -1;
+  QW_CHECK_CUDA(cudaGetDevice(&cur));
+  if (cur != p->device) QW_CHECK_CUDA(cudaSetDevice(p->device));
+  return QW_OK;
+}
+
+}  // namespace qw
+
+using namespace qw;
+
+extern "C" {
+
+const char* qw_last_error(void) { return g_last_error.c_str(); }
+
+const char* qw_version(void) { return "qw-gb300 0.1 (sm_103a)"; }
+
+qw_status qw_plan_create(int dim, int64_t N, double mass, qw_dtype dtype, qw_plan* out) {
+  if (!out) {
+    set_error("qw_plan_create: out is NULL");
+    return QW_EINVAL;
+  }
+  *out = nullptr;
+  Geometry g;
+  if (!make_geometry(dim, N, &g)) {
+    set_error("qw_plan_create: bad dim=%d / N=%lld (dim in 1..3, N >= 2, N even for dim 3)", dim, (long long)N);
+    return QW_EINVAL;
+  }
+  if (!(mass >= 0.0 && mass <= 1.0)) {
+    set_error("qw_plan_create: mass %g outside [0, 1]", mass);
+    return QW_EINVAL;
+  }
+  if (dtype != QW_C64 && dtype != QW_C128) {
+    set_error("qw_plan_create: bad dtype %d", (int)dtype);
+    return QW_EINVAL;
+  }
+  qw_plan_s* p = new (std::nothrow) qw_plan_s();
+  if (!p) {
+    set_error("qw_plan_create: host allocation failed");
+    return QW_ENOMEM;
+  }
+  p->g = g;
+  p->mass = mass;
+  p->n = std::sqrt(1.0 - mass * mass);
+  p->dtype = dtype;
+  p->elem_bytes = (dtype == QW_C64) ? 8 : 16;
+  qw_status st = QW_OK;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaMalloc(&p->scratch, (size_t)g.elems * p->elem_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->red_partials, sizeof(double) * 4 * kObsBlocks);
+  if (e == cudaSuccess) e = cudaMalloc(&p->red_result, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMallocHost(&p->red_host, sizeof(double) * 4);
+  if (e != cudaSuccess) {
+    st = cuda_fail(e, "qw_plan_create: allocation");
+    qw_plan_destroy(p);
+    return st;
+  }
+  *out = p;
+  return QW_OK;
+}
+
+qw_status qw_plan_destroy(qw_plan p) {
+  if (!p) return QW_OK;
+  cudaDeviceSynchronize();
+  if (p->scratch) cudaFree(p->scratch);
+  if (p->red_partials) cudaFree(p->red_partials);
+  if (p->red_result) cudaFree(p->red_result);
+  if (p->red_host) cudaFreeHost(p->red_host);
+  delete p;
+  return QW_OK;
+}
+
+int64_t qw_plan_field_elems(qw_plan p) { return p ? p->g.elems : -1; }
+
+int64_t qw_plan_sites(qw_plan p) { return p ? p->g.sites : -1; }
+
+qw_status qw_step(qw_plan p, void* psi, int64_t nsteps, void* stream) {
+  if (!p || !psi || nsteps < 0) {
+    set_error("qw_step: null plan/field or nsteps < 0");
+    return QW_EINVAL;
+  }
+  if (nsteps == 0) return QW_OK;
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* cur = psi;
+  void* nxt = p->scratch;
+  for (int64_t i = 0; i < nsteps; ++i) {
+    st = launch_step(p->g, p->dtype, p->n, p->mass, cur, nxt, s);
+    if (st != QW_OK) return st;
+    void* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  if (cur != psi)
+    QW_CHECK_CUDA(cudaMemcpyAsync(psi, cur, (size_t)p->g.elems * p->elem_bytes, cudaMemcpyDeviceToDevice, s));
+  return QW_OK;
+}
+
+qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) {
+  if (!p || !psi || !out) {
+    set_error("qw_observables: null argument");
+    return QW_EINVAL;
+  }
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = launch_position_moments(p->g, p->dtype, psi, p->red_partials, p->red_result, s);
+  if (st != QW_OK) return st;
+  QW_CHECK_CUDA(cudaMemcpyAsync(p->red_host, p->red_result, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  QW_CHECK_CUDA(cudaStreamSynchronize(s));
+  const double* r = p->red_host;
+  out->norm = r[0];
+  for (int j = 0; j < 3; ++j) out->x_mean[j] = (j < p->g.dim && r[0] > 0) ? r[1 + j] / r[0] : 0.0;
+  out->w_particle = NAN;
+  out->w_antiparticle = NAN;
+  return QW_OK;
+}
+
+}  // extern "C"

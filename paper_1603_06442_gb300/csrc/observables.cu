@@ -1,0 +1,130 @@
+// Position-space observables (Sec. 5.2): the norm sum_x |psi(x)|^2 and the
+// first moments sum_x x_i |psi(x)|^2 of the position operator X, in FP64.
+//
+// Each thread takes a segment of SEG consecutive x-cells of one row (fixed
+// coset, z, y), sums the density and x*density over the segment in the field's
+// precision, then adds the segment totals into FP64 accumulators (the y and z
+// moments of a segment are y*norm and z*norm).  Warp-shuffle and shared-memory
+// reductions give one partial per block; a single block then folds the
+// partials in a fixed order, so the result is deterministic.
+#include <cuda_runtime.h>
+
+#include "qw_internal.cuh"
+
+namespace qw {
+
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce 4 doubles over the block; thread 0 gets the totals in acc[].
+__device__ __forceinline__ void block_sum4(double acc[4]) {
+  __shared__ double sh[kObsThreads / 32][4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) acc[j] = warp_sum(acc[j]);
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sh[wid][j] = acc[j];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      double v = lane < kObsThreads / 32 ? sh[lane][j] : 0.0;
+      acc[j] = warp_sum(v);
+    }
+  }
+}
+
+template <typename R, int SEG>
+__global__ void __launch_bounds__(kObsThreads) moments_kernel(const typename Cplx<R>::T* __restrict__ psi,
+                                                              Geometry g, double* __restrict__ partials) {
+  using C = typename Cplx<R>::T;
+  const int64_t segs_per_row = g.nx / SEG;
+  const int64_t rows = (int64_t)g.ncoset * g.nz * g.ny;
+  const int64_t nseg = rows * segs_per_row;
+  const double scale = (g.dim == 3) ? 2.0 : 1.0;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t sidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sidx < nseg;
+       sidx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = sidx / segs_per_row;
+    const int64_t x0 = (sidx - row * segs_per_row) * SEG;
+    const int64_t y = row % g.ny;
+    const int64_t zc = row / g.ny;
+    const int64_t z = zc % g.nz;
+    const int c = (int)(zc / g.nz);
+    const C* base = psi + (int64_t)c * g.s * g.vol + (z * g.ny + y) * g.nx + x0;
+    R nf = 0, xf = 0;
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) {
+      R d = 0;
+      for (int s = 0; s < g.s; ++s) {
+        C v = __ldg(base + (int64_t)s * g.vol + j);
+        d = fma(v.x, v.x, d);
+        d = fma(v.y, v.y, d);
+      }
+      nf += d;
+      xf = fma((R)j, d, xf);
+    }
+    const double n = (double)nf;
+    const double off = (double)c;
+    acc[0] += n;
+    acc[1] += scale * ((double)xf + (double)x0 * n) + off * n;
+    acc[2] += (scale * (double)y + off) * n;
+    acc[3] += (scale * (double)z + off) * n;
+  }
+  block_sum4(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) partials[(int64_t)blockIdx.x * 4 + j] = acc[j];
+  }
+}
+
+__global__ void __launch_bounds__(kObsThreads) fold_partials_kernel(const double* __restrict__ partials, int nblk,
+                                                                    double* __restrict__ result) {
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] += partials[b * 4 + j];
+  }
+  block_sum4(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) result[j] = acc[j];
+  }
+}
+
+template <typename R>
+static void launch_moments_t(const Geometry& g, const void* psi, double* partials, cudaStream_t st) {
+  using C = typename Cplx<R>::T;
+  const C* p = static_cast<const C*>(psi);
+  if (g.nx % 8 == 0)
+    moments_kernel<R, 8><<<kObsBlocks, kObsThreads, 0, st>>>(p, g, partials);
+  else if (g.nx % 4 == 0)
+    moments_kernel<R, 4><<<kObsBlocks, kObsThreads, 0, st>>>(p, g, partials);
+  else if (g.nx % 2 == 0)
+    moments_kernel<R, 2><<<kObsBlocks, kObsThreads, 0, st>>>(p, g, partials);
+  else
+    moments_kernel<R, 1><<<kObsBlocks, kObsThreads, 0, st>>>(p, g, partials);
+}
+
+qw_status launch_position_moments(const Geometry& g, qw_dtype dt, const void* psi, double* partials,
+                                  double* result, cudaStream_t st) {
+  if (dt == QW_C64)
+    launch_moments_t<float>(g, psi, partials, st);
+  else
+    launch_moments_t<double>(g, psi, partials, st);
+  QW_CHECK_LAUNCH("moments launch");
+  fold_partials_kernel<<<1, kObsThreads, 0, st>>>(partials, kObsBlocks, result);
+  QW_CHECK_LAUNCH("fold launch");
+  return QW_OK;
+}
+
+}  // namespace qw

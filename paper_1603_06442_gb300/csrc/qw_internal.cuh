@@ -1,0 +1,85 @@
+// Internal declarations shared by the translation units of libqw.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qw.h"
+
+namespace qw {
+
+// ---- errors ---------------------------------------------------------------
+void set_error(const char* fmt, ...);
+qw_status cuda_fail(cudaError_t e, const char* what);
+
+#define QW_CHECK_CUDA(call)                                        \
+  do {                                                             \
+    cudaError_t qw_e_ = (call);                                    \
+    if (qw_e_ != cudaSuccess) return ::qw::cuda_fail(qw_e_, #call); \
+  } while (0)
+
+#define QW_CHECK_LAUNCH(what)                                      \
+  do {                                                             \
+    cudaError_t qw_e_ = cudaGetLastError();                        \
+    if (qw_e_ != cudaSuccess) return ::qw::cuda_fail(qw_e_, what);  \
+  } while (0)
+
+// ---- geometry -------------------------------------------------------------
+// One field in the device layout: ncoset x s planes of `vol` complex values,
+// each plane [z][y][x] with extents (nz, ny, nx).  1D: nx = N, ny = nz = 1;
+// 2D: nx = ny = N; 3D (BCC): nx = ny = nz = M = N/2 and ncoset = 2.
+struct Geometry {
+  int dim;
+  int64_t N;
+  int s;
+  int ncoset;
+  int64_t nx, ny, nz;
+  int64_t vol;    // nx * ny * nz
+  int64_t elems;  // ncoset * s * vol
+  int64_t sites;  // ncoset * vol
+};
+
+bool make_geometry(int dim, int64_t N, Geometry* g);
+
+// Mass coefficients of one step.  With the Weyl sums S carrying the factor 4
+// of the +-1 +- i entries, one output is  nq * S + i m * psi_other  with
+// nq = n/4 (2D, 3D) or n (1D).  FP32 keeps nq and m as hi + lo pairs so that
+// the fused multiply-adds use the FP64 values to ~2^-48 (no per-step bias).
+struct Coef32 {
+  float nq_hi, nq_lo, m_hi, m_lo;
+};
+struct Coef64 {
+  double nq, m;
+};
+Coef32 make_coef32(int dim, double n, double m);
+Coef64 make_coef64(int dim, double n, double m);
+
+// ---- kernels (stencil.cu) ---------------------------------------------------
+// One update out = U in (Eq. upd-rule); in != out.
+qw_status launch_step(const Geometry& g, qw_dtype dt, double n, double m, const void* in, void* out,
+                      cudaStream_t st);
+
+// ---- reductions (observables.cu) -------------------------------------------
+// Partial sums (norm, sum x|psi|^2, sum y|psi|^2, sum z|psi|^2) per block into
+// `partials` (4 * kObsBlocks doubles), then one block folds them in a fixed
+// order into `result` (4 doubles).  Deterministic for a given geometry.
+constexpr int kObsBlocks = 608;  // 4 x 152 SMs
+constexpr int kObsThreads = 256;
+qw_status launch_position_moments(const Geometry& g, qw_dtype dt, const void* psi, double* partials,
+                                  double* result, cudaStream_t st);
+
+}  // namespace qw
+
+// ---- the plan ---------------------------------------------------------------
+struct qw_plan_s {
+  qw::Geometry g;
+  double mass;
+  double n;
+  qw_dtype dtype;
+  int device;
+  size_t elem_bytes;
+  void* scratch;        // one field: ping-pong partner of the caller's buffer
+  double* red_partials; // 4 * kObsBlocks doubles
+  double* red_result;   // 4 doubles (device)
+  double* red_host;     // 4 doubles (pinned host)
+};

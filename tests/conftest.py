@@ -15,3 +15,11 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="session")
+def qwlib():
+    """Build (if stale) and load libqw.so."""
+    from paper_1603_06442_gb300 import build, binding
+    build.build()
+    return binding.load()

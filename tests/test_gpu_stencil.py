@@ -1,0 +1,163 @@
+"""GPU parity of the stencil path (qw_step) and the position observables against the oracle.
+
+Tolerances (relative L2 over the whole field):
+  complex128: 1e-11;  complex64: 1e-5 per 1000 steps (at least 1e-5).
+Inputs come from paper_1603_06442_gb300.inputs (seeded); expected values from oracle/.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1603_06442_gb300 import inputs
+from oracle import walk, spectral, observables
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def tol(dtype, t):
+    return 1e-11 if dtype == "c128" else 1e-5 * max(1.0, t / 1000.0)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def qb(qwlib):
+    from paper_1603_06442_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return binding
+
+
+def to_dev(a, dtype):
+    npdt = np.complex64 if dtype == "c64" else np.complex128
+    return torch.from_numpy(np.ascontiguousarray(a.astype(npdt))).cuda()
+
+
+def run_steps(qb, dim, N, m, dtype, a, t):
+    plan = qb.Plan(dim, N, m, dtype)
+    x = to_dev(a, dtype)
+    plan.step(x, t)
+    torch.cuda.synchronize()
+    out = x.cpu().numpy().astype(np.complex128)
+    plan.close()
+    return out
+
+
+CASES = [
+    (1, 2), (1, 37), (1, 1000),
+    (2, 2), (2, 3), (2, 40), (2, 67),
+    (3, 2), (3, 4), (3, 20), (3, 70),
+]
+
+
+@pytest.mark.parametrize("dim,N", CASES)
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("t", [0, 1, 2, 7])
+def test_stencil_parity(qb, dim, N, dtype, t):
+    m = 0.23
+    a = inputs.random_field(dim, N, seed=dim * 1000 + N)
+    got = run_steps(qb, dim, N, m, dtype, a, t)
+    exp = walk.to_device(dim, N, walk.step(dim, m, walk.from_device(dim, N, a), t))
+    assert rel_l2(got, exp) <= tol(dtype, t)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("m", [0.0, 1.0])
+def test_stencil_degenerate_masses(qb, dtype, m):
+    for dim, N in ((1, 16), (2, 10), (3, 12)):
+        a = inputs.random_field(dim, N, seed=7)
+        got = run_steps(qb, dim, N, m, dtype, a, 5)
+        exp = walk.to_device(dim, N, walk.step(dim, m, walk.from_device(dim, N, a), 5))
+        assert rel_l2(got, exp) <= tol(dtype, 5)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_config_1d_packet(qb, dtype):
+    """1D, N = 1024, m = 0.1, t = 512, Gaussian packet sigma = 16 at x = 512, k0 = 0.2."""
+    N, m, t = 1024, 0.1, 512
+    a = inputs.gaussian_packet(1, N, 512, 16.0, 0.2, [1.0, 0.0])
+    got = run_steps(qb, 1, N, m, dtype, a, t)
+    exp = walk.step(1, m, a, t)
+    err = rel_l2(got, exp)
+    assert err <= tol(dtype, t), err
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_config_bcc128_t1000(qb, dtype):
+    """BCC N = 128 (524,288 sites), m = 0.05, t = 1000, packet sigma = 8, k0 = (0.1, 0, 0)."""
+    N, m, t = 128, 0.05, 1000
+    chi = np.array([1, 0, 1, 0]) / np.sqrt(2)
+    a = inputs.gaussian_packet(3, N, (64, 64, 64), 8.0, (0.1, 0.0, 0.0), chi)
+    got = run_steps(qb, 3, N, m, dtype, a, t)
+    exp = walk.to_device(3, N, spectral.evolve(3, m, walk.from_device(3, N, a), t))
+    err = rel_l2(got, exp)
+    nd = abs(np.sum(np.abs(got) ** 2) - 1.0)
+    print("BCC128 t=1000 %s rel-L2 %.3e norm drift %.3e" % (dtype, err, nd))
+    assert err <= tol(dtype, t), err
+
+
+def _subbox_oracle(a_dev_layout, N, m, t, centre):
+    """Value at the even physical site `centre` after t steps, computed by the oracle on a
+    periodic sub-box of side L >= 2t + 1 (a multiple of 4) centred there: within t steps
+    the centre only sees sites within t hops, which the sub-box holds unwrapped."""
+    L = 4 * ((t + 1 + 1) // 2)
+    M = N // 2
+    o = np.asarray(centre) - L // 2                 # even origin keeps the coset structure
+    q = np.arange(L // 2)
+    ix = [(o[j] // 2 + q) % M for j in range(3)]
+    sub = np.stack([a_dev_layout[c][:, ix[2]][:, :, ix[1]][:, :, :, ix[0]] for c in (0, 1)])
+    psi = walk.step(3, m, walk.from_device(3, L, sub), t)
+    return psi[:, L // 2, L // 2, L // 2]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_bcc512_sampled(qb, dtype):
+    """Full-size BCC box N = 512 (33,554,432 sites): sampled sites against sub-box oracle runs."""
+    N, m, t = 512, 0.3, 6
+    rng = np.random.default_rng(11)
+    shp = inputs.field_shape(3, N)
+    a = (rng.standard_normal(shp, dtype=np.float32) + 1j * rng.standard_normal(shp, dtype=np.float32))
+    got = run_steps(qb, 3, N, m, dtype, a, t)
+    worst = 0.0
+    for _ in range(12):
+        centre = 2 * rng.integers(0, N // 2, size=3)
+        exp = _subbox_oracle(a.astype(np.complex128), N, m, t, centre)
+        M = N // 2
+        g = got[0, :, centre[2] // 2 % M, centre[1] // 2 % M, centre[0] // 2 % M]
+        worst = max(worst, np.linalg.norm(g - exp) / np.linalg.norm(exp))
+    assert worst <= (1e-11 if dtype == "c128" else 1e-5), worst
+
+
+@pytest.mark.parametrize("dim,N", [(1, 64), (1, 1000), (2, 24), (2, 33), (3, 16), (3, 42)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_position_observables(qb, dim, N, dtype):
+    a = inputs.gaussian_packet(dim, N, [N / 3] * dim, N / 10, [0.2] * dim,
+                               [1, 0] if dim == 1 else [0.6, 0.8j, 0, 0])
+    a = a + 0.3 * inputs.random_field(dim, N, 5)
+    a *= 1.7
+    plan = qb.Plan(dim, N, 0.1, dtype)
+    x = to_dev(a, dtype)
+    obs = plan.observables(x)
+    plan.close()
+    psi = walk.from_device(dim, N, a.astype(np.complex64 if dtype == "c64" else np.complex128))
+    rtol = 1e-12 if dtype == "c128" else 1e-6
+    assert abs(obs["norm"] - observables.norm(psi)) <= rtol * observables.norm(psi)
+    exp = observables.mean_position(dim, psi)
+    for j in range(dim):
+        assert abs(obs["x_mean"][j] - exp[j]) <= rtol * N, (j, obs["x_mean"][j], exp[j])
+    for j in range(dim, 3):
+        assert obs["x_mean"][j] == 0.0
+
+
+def test_step_rejects_bad_arguments(qb):
+    plan = qb.Plan(1, 8, 0.1, "c64")
+    with pytest.raises(qb.QwError):
+        qb.qw_step(plan.handle, 0, 1)
+    with pytest.raises(qb.QwError):
+        x = torch.zeros(16, dtype=torch.complex64, device="cuda")
+        qb.qw_step(plan.handle, x, -1)
+    plan.close()
