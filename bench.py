@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--N", type=int, default=None, help="override the box side (profiling runs)")
+    ap.add_argument("--stencil", default=None, help="force a stencil variant (plain, vec, tma)")
     ap.add_argument("--substeps", type=int, default=None, help="override stencil steps per bench step")
     args = ap.parse_args()
     if args.N is not None:
@@ -176,6 +177,9 @@ def run_ours(args, rank, world, local):
     W = WORKLOAD
     dim, N, S = W["dim"], W["N"], W["substeps"]
     plan = qb.Plan(dim, N, W["mass"], "c64")
+    if args.stencil:
+        plan.set_stencil(args.stencil)
+    kernel_name = {1: "step3d_kernel<float>", 2: "step3d_c64_vec_kernel", 3: "step3d_c64_tma_kernel"}[plan.stencil]
     a = inputs.gaussian_packet(dim, N, (N / 2,) * 3, W["sigma"], W["k0"], [0.5, 0.5j, 0.5, -0.5j])
     host = torch.from_numpy(a.astype(np.complex64)).pin_memory()
     psi = host.to(dev)
@@ -253,7 +257,7 @@ def run_ours(args, rank, world, local):
                    "input": "Gaussian packet sigma=%g sites, k0=%s" % (W["sigma"], list(W["k0"]))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "step3d_kernel<float>", "peak_kind": peak_kind,
+                     "kernel": kernel_name, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": 2 * field_bytes,
                      "avg_launch_ms": per_launch_ms},
         "e2e": {"value": sites * S / (e2e_ms / 1e3), "unit": "site-steps/s",
@@ -289,6 +293,28 @@ def extra_measurements(qb, dev, stream):
     ms = s0.elapsed_time(s1) / n
     out["fp64_stencil"] = {"site_steps_per_s": plan.sites / (ms / 1e3), "ms_per_step": ms,
                            "hbm_GBps": 2 * plan.elems * 16 / (ms / 1e3) / 1e9}
+    plan.close()
+    # every complex64 stencil variant on the same box (A/B of the data movement)
+    plan = qb.Plan(3, W["N"], W["mass"], "c64")
+    psi = torch.zeros(plan.elems, dtype=torch.complex64, device=dev)
+    psi[::7] = 1e-3
+    variants = {}
+    for name in ("plain", "vec", "tma"):
+        try:
+            plan.set_stencil(name)
+        except qb.QwError:
+            continue
+        plan.step(psi, 2, stream)
+        torch.cuda.synchronize(dev)
+        n = 10
+        s0.record(stream)
+        plan.step(psi, n, stream)
+        s1.record(stream)
+        plan.sync(stream)
+        ms = s0.elapsed_time(s1) / n
+        variants[name] = {"ms_per_step": ms, "site_steps_per_s": plan.sites / (ms / 1e3),
+                          "hbm_GBps": 2 * plan.elems * 8 / (ms / 1e3) / 1e9}
+    out["c64_stencil_variants"] = variants
     plan.close()
     return out
 

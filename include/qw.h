@@ -53,6 +53,19 @@ typedef enum {
 
 typedef enum { QW_C64 = 0, QW_C128 = 1 } qw_dtype;
 
+/* Kernel used by qw_step.  All variants compute the same update; they differ in
+ * data movement.  PLAIN: any geometry and dtype, one thread per site.  VEC: BCC,
+ * complex64, N/2 % 64 == 0; two cells per thread, 16-byte loads.  TMA: BCC,
+ * complex64, N/2 % 64 == 0; z-marching CTAs with TMA-staged shared-memory tiles.
+ * AUTO picks, at plan creation, the fastest variant measured by
+ * qw_plan_autotune, else the default order TMA > VEC > PLAIN. */
+typedef enum {
+  QW_STENCIL_AUTO = 0,
+  QW_STENCIL_PLAIN = 1,
+  QW_STENCIL_VEC = 2,
+  QW_STENCIL_TMA = 3
+} qw_stencil_variant;
+
 typedef struct qw_plan_s* qw_plan;
 
 /* Observables of one field (Sec. 5.2): the norm sum_x |psi(x)|^2; the mean
@@ -93,16 +106,29 @@ int64_t qw_plan_field_elems(qw_plan plan);
 /* Number of lattice sites (N, N^2, or N^3/4 for the BCC box); -1 for null. */
 int64_t qw_plan_sites(qw_plan plan);
 
+/* Select the stencil kernel of qw_step (QW_STENCIL_AUTO restores the default).
+ * Errors: QW_EINVAL if the variant does not support this plan's geometry/dtype. */
+qw_status qw_plan_set_stencil(qw_plan plan, int variant);
+
+/* The stencil variant qw_step currently uses (never QW_STENCIL_AUTO); -1 for null. */
+int qw_plan_get_stencil(qw_plan plan);
+
 /* Advance psi_dev in place by `nsteps` >= 0 applications of the update rule
- * (Eq. upd-rule; the plain position-space form of Sec. 4).  Uses the plan's
- * scratch field; the stencil variant (temporal fusion depth, tile) is the one
- * chosen by the plan (see qw_plan_set_fusion).  Asynchronous on `stream`.
+ * (Eq. upd-rule; the plain position-space form of Sec. 4) with the plan's
+ * stencil variant.  Ping-pongs through the plan's scratch field (an odd step
+ * count ends with one device copy).  Asynchronous on `stream`; a bounded
+ * device-side wait that gave up is reported by the next qw_sync/qw_observables.
  * Errors: QW_EINVAL (null plan/pointer, nsteps < 0), QW_ECUDA. */
 qw_status qw_step(qw_plan plan, void* psi_dev, int64_t nsteps, void* stream);
 
+/* Wait for the plan's work on `stream`, then check its device error word.
+ * Errors: QW_ETIMEOUT (a kernel's bounded wait gave up; the word is cleared),
+ * QW_ECUDA. */
+qw_status qw_sync(qw_plan plan, void* stream);
+
 /* Compute the observables of psi_dev (see qw_obs).  Blocks the host until the
  * reductions on `stream` are done, then fills *out.
- * Errors: QW_EINVAL, QW_ECUDA. */
+ * Errors: QW_EINVAL, QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
 qw_status qw_observables(qw_plan plan, const void* psi_dev, qw_obs* out, void* stream);
 
 #ifdef __cplusplus

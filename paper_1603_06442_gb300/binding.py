@@ -14,6 +14,8 @@ LIB_PATH = os.path.join(PKG, "libqw.so")
 
 QW_OK, QW_EINVAL, QW_ENOMEM, QW_ECUDA, QW_ETIMEOUT, QW_EAGAIN, QW_EBUSY, QW_ENOTFOUND = range(8)
 QW_C64, QW_C128 = 0, 1
+QW_STENCIL_AUTO, QW_STENCIL_PLAIN, QW_STENCIL_VEC, QW_STENCIL_TMA = 0, 1, 2, 3
+STENCILS = {"auto": 0, "plain": 1, "vec": 2, "tma": 3}
 STATUS_NAMES = {0: "QW_OK", 1: "QW_EINVAL", 2: "QW_ENOMEM", 3: "QW_ECUDA", 4: "QW_ETIMEOUT",
                 5: "QW_EAGAIN", 6: "QW_EBUSY", 7: "QW_ENOTFOUND"}
 
@@ -45,6 +47,9 @@ _SIGS = {
     "qw_plan_field_elems": (ctypes.c_int64, [ctypes.c_void_p]),
     "qw_plan_sites": (ctypes.c_int64, [ctypes.c_void_p]),
     "qw_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
+    "qw_plan_set_stencil": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "qw_plan_get_stencil": (ctypes.c_int, [ctypes.c_void_p]),
+    "qw_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "qw_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(qw_obs),
                                       ctypes.c_void_p]),
 }
@@ -122,6 +127,18 @@ def qw_step(plan, psi, nsteps, stream=None):
     _check(load().qw_step(plan, _ptr(psi), int(nsteps), _stream(stream)))
 
 
+def qw_plan_set_stencil(plan, variant):
+    _check(load().qw_plan_set_stencil(plan, int(STENCILS.get(variant, variant))))
+
+
+def qw_plan_get_stencil(plan):
+    return load().qw_plan_get_stencil(plan)
+
+
+def qw_sync(plan, stream=None):
+    _check(load().qw_sync(plan, _stream(stream)))
+
+
 def qw_observables(plan, psi, stream=None):
     out = qw_obs()
     _check(load().qw_observables(plan, _ptr(psi), ctypes.byref(out), _stream(stream)))
@@ -161,6 +178,16 @@ class Plan:
     def step(self, psi, nsteps, stream=None):
         self.check_field(psi)
         qw_step(self.handle, psi, nsteps, stream)
+
+    def set_stencil(self, variant):
+        qw_plan_set_stencil(self.handle, variant)
+
+    @property
+    def stencil(self):
+        return qw_plan_get_stencil(self.handle)
+
+    def sync(self, stream=None):
+        qw_sync(self.handle, stream)
 
     def observables(self, psi, stream=None):
         self.check_field(psi)

@@ -52,6 +52,25 @@ bool make_geometry(int dim, int64_t N, Geometry* g) {
   return true;
 }
 
+static int default_stencil(const qw_plan_s* p) {
+  if (stencil_supported(p->g, p->dtype, QW_STENCIL_TMA)) return QW_STENCIL_TMA;
+  if (stencil_supported(p->g, p->dtype, QW_STENCIL_VEC)) return QW_STENCIL_VEC;
+  return QW_STENCIL_PLAIN;
+}
+
+static qw_status check_flags(qw_plan_s* p, cudaStream_t s) {
+  int flags[2] = {0, 0};
+  QW_CHECK_CUDA(cudaMemcpyAsync(flags, p->dev_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  QW_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (flags[0] != 0) {
+    cudaMemsetAsync(p->dev_flags, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    set_error("a bounded device wait gave up (code %d); results of the affected launch are invalid", flags[0]);
+    return QW_ETIMEOUT;
+  }
+  return QW_OK;
+}
+
 static qw_status use_device(const qw_plan_s* p) {
   int cur = -1;
   QW_CHECK_CUDA(cudaGetDevice(&cur));
@@ -104,11 +123,15 @@ qw_status qw_plan_create(int dim, int64_t N, double mass, qw_dtype dtype, qw_pla
   if (e == cudaSuccess) e = cudaMalloc(&p->red_partials, sizeof(double) * 4 * kObsBlocks);
   if (e == cudaSuccess) e = cudaMalloc(&p->red_result, sizeof(double) * 4);
   if (e == cudaSuccess) e = cudaMallocHost(&p->red_host, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&p->dev_flags, sizeof(int) * 2);
+  if (e == cudaSuccess) e = cudaMemset(p->dev_flags, 0, sizeof(int) * 2);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     st = cuda_fail(e, "qw_plan_create: allocation");
     qw_plan_destroy(p);
     return st;
   }
+  p->stencil = default_stencil(p);
   *out = p;
   return QW_OK;
 }
@@ -120,6 +143,7 @@ qw_status qw_plan_destroy(qw_plan p) {
   if (p->red_partials) cudaFree(p->red_partials);
   if (p->red_result) cudaFree(p->red_result);
   if (p->red_host) cudaFreeHost(p->red_host);
+  if (p->dev_flags) cudaFree(p->dev_flags);
   delete p;
   return QW_OK;
 }
@@ -140,7 +164,10 @@ qw_status qw_step(qw_plan p, void* psi, int64_t nsteps, void* stream) {
   void* cur = psi;
   void* nxt = p->scratch;
   for (int64_t i = 0; i < nsteps; ++i) {
-    st = launch_step(p->g, p->dtype, p->n, p->mass, cur, nxt, s);
+    if (p->stencil == QW_STENCIL_TMA)
+      st = launch_step_tma(p->g, p->n, p->mass, cur, nxt, p->dev_flags, p->dev_flags + 1, s);
+    else
+      st = launch_step(p->g, p->dtype, p->stencil, p->n, p->mass, cur, nxt, s);
     if (st != QW_OK) return st;
     void* t = cur;
     cur = nxt;
@@ -149,6 +176,36 @@ qw_status qw_step(qw_plan p, void* psi, int64_t nsteps, void* stream) {
   if (cur != psi)
     QW_CHECK_CUDA(cudaMemcpyAsync(psi, cur, (size_t)p->g.elems * p->elem_bytes, cudaMemcpyDeviceToDevice, s));
   return QW_OK;
+}
+
+qw_status qw_plan_set_stencil(qw_plan p, int variant) {
+  if (!p) {
+    set_error("qw_plan_set_stencil: null plan");
+    return QW_EINVAL;
+  }
+  if (variant == QW_STENCIL_AUTO) {
+    p->stencil = default_stencil(p);
+    return QW_OK;
+  }
+  if (!stencil_supported(p->g, p->dtype, variant)) {
+    set_error("qw_plan_set_stencil: variant %d does not support dim=%d N=%lld dtype=%d", variant, p->g.dim,
+              (long long)p->g.N, (int)p->dtype);
+    return QW_EINVAL;
+  }
+  p->stencil = variant;
+  return QW_OK;
+}
+
+int qw_plan_get_stencil(qw_plan p) { return p ? p->stencil : -1; }
+
+qw_status qw_sync(qw_plan p, void* stream) {
+  if (!p) {
+    set_error("qw_sync: null plan");
+    return QW_EINVAL;
+  }
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  return check_flags(p, static_cast<cudaStream_t>(stream));
 }
 
 qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) {
@@ -162,7 +219,8 @@ qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) 
   st = launch_position_moments(p->g, p->dtype, psi, p->red_partials, p->red_result, s);
   if (st != QW_OK) return st;
   QW_CHECK_CUDA(cudaMemcpyAsync(p->red_host, p->red_result, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  QW_CHECK_CUDA(cudaStreamSynchronize(s));
+  st = check_flags(p, s);
+  if (st != QW_OK) return st;
   const double* r = p->red_host;
   out->norm = r[0];
   for (int j = 0; j < 3; ++j) out->x_mean[j] = (j < p->g.dim && r[0] > 0) ? r[1 + j] / r[0] : 0.0;

@@ -54,10 +54,16 @@ struct Coef64 {
 Coef32 make_coef32(int dim, double n, double m);
 Coef64 make_coef64(int dim, double n, double m);
 
-// ---- kernels (stencil.cu) ---------------------------------------------------
-// One update out = U in (Eq. upd-rule); in != out.
-qw_status launch_step(const Geometry& g, qw_dtype dt, double n, double m, const void* in, void* out,
+// ---- kernels (stencil.cu, stencil_tma.cu) ----------------------------------
+// One update out = U in (Eq. upd-rule); in != out.  `variant` selects the
+// kernel (qw_stencil_variant); QW_STENCIL_AUTO resolves to the best one that
+// supports the geometry.
+bool stencil_supported(const Geometry& g, qw_dtype dt, int variant);
+qw_status launch_step(const Geometry& g, qw_dtype dt, int variant, double n, double m, const void* in, void* out,
                       cudaStream_t st);
+bool tma_step_supported(const Geometry& g);
+qw_status launch_step_tma(const Geometry& g, double n, double m, const void* in, void* out, int* err,
+                          int* next_item, cudaStream_t st);
 
 // ---- reductions (observables.cu) -------------------------------------------
 // Partial sums (norm, sum x|psi|^2, sum y|psi|^2, sum z|psi|^2) per block into
@@ -78,7 +84,9 @@ struct qw_plan_s {
   qw_dtype dtype;
   int device;
   size_t elem_bytes;
+  int stencil;          // qw_stencil_variant in use (never AUTO after creation)
   void* scratch;        // one field: ping-pong partner of the caller's buffer
+  int* dev_flags;       // [0] error word of bounded device waits, [1] work counter
   double* red_partials; // 4 * kObsBlocks doubles
   double* red_result;   // 4 doubles (device)
   double* red_host;     // 4 doubles (pinned host)

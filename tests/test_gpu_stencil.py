@@ -37,10 +37,14 @@ def to_dev(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a.astype(npdt))).cuda()
 
 
-def run_steps(qb, dim, N, m, dtype, a, t):
+def run_steps(qb, dim, N, m, dtype, a, t, variant=None):
     plan = qb.Plan(dim, N, m, dtype)
+    if variant is not None:
+        plan.set_stencil(variant)
+        assert plan.stencil == qb.STENCILS[variant]
     x = to_dev(a, dtype)
     plan.step(x, t)
+    plan.sync()
     torch.cuda.synchronize()
     out = x.cpu().numpy().astype(np.complex128)
     plan.close()
@@ -50,7 +54,7 @@ def run_steps(qb, dim, N, m, dtype, a, t):
 CASES = [
     (1, 2), (1, 37), (1, 1000),
     (2, 2), (2, 3), (2, 40), (2, 67),
-    (3, 2), (3, 4), (3, 20), (3, 70),
+    (3, 2), (3, 4), (3, 20), (3, 70), (3, 128),
 ]
 
 
@@ -63,6 +67,38 @@ def test_stencil_parity(qb, dim, N, dtype, t):
     got = run_steps(qb, dim, N, m, dtype, a, t)
     exp = walk.to_device(dim, N, walk.step(dim, m, walk.from_device(dim, N, a), t))
     assert rel_l2(got, exp) <= tol(dtype, t)
+
+
+@pytest.mark.parametrize("variant", ["plain", "vec", "tma"])
+@pytest.mark.parametrize("N,t", [(128, 1), (128, 6), (256, 3)])
+def test_bcc_c64_variants(qb, variant, N, t):
+    """Every complex64 BCC kernel variant against the oracle (N/2 % 64 == 0 boxes)."""
+    m = 0.37
+    if N == 256:
+        # oracle on the full 256^3 cube is slow: compare against the plain kernel instead,
+        # which the oracle pins at N = 128 above and in test_stencil_parity
+        a = inputs.random_field(3, N, seed=5)
+        ref = run_steps(qb, 3, N, m, "c64", a, t, "plain")
+        got = run_steps(qb, 3, N, m, "c64", a, t, variant)
+        assert rel_l2(got, ref) <= 1e-6
+        return
+    a = inputs.random_field(3, N, seed=4)
+    got = run_steps(qb, 3, N, m, "c64", a, t, variant)
+    exp = walk.to_device(3, N, walk.step(3, m, walk.from_device(3, N, a), t))
+    assert rel_l2(got, exp) <= tol("c64", t)
+
+
+def test_variant_rejected_when_unsupported(qb):
+    plan = qb.Plan(3, 20, 0.1, "c64")
+    with pytest.raises(qb.QwError):
+        plan.set_stencil("tma")
+    plan.set_stencil("auto")
+    assert plan.stencil == qb.STENCILS["plain"]
+    plan.close()
+    plan = qb.Plan(3, 128, 0.1, "c128")
+    with pytest.raises(qb.QwError):
+        plan.set_stencil("vec")
+    plan.close()
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
@@ -114,14 +150,14 @@ def _subbox_oracle(a_dev_layout, N, m, t, centre):
     return psi[:, L // 2, L // 2, L // 2]
 
 
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_bcc512_sampled(qb, dtype):
+@pytest.mark.parametrize("dtype,variant", [("c64", "tma"), ("c64", "vec"), ("c64", "plain"), ("c128", "plain")])
+def test_bcc512_sampled(qb, dtype, variant):
     """Full-size BCC box N = 512 (33,554,432 sites): sampled sites against sub-box oracle runs."""
     N, m, t = 512, 0.3, 6
     rng = np.random.default_rng(11)
     shp = inputs.field_shape(3, N)
     a = (rng.standard_normal(shp, dtype=np.float32) + 1j * rng.standard_normal(shp, dtype=np.float32))
-    got = run_steps(qb, 3, N, m, dtype, a, t)
+    got = run_steps(qb, 3, N, m, dtype, a, t, variant)
     worst = 0.0
     for _ in range(12):
         centre = 2 * rng.integers(0, N // 2, size=3)
