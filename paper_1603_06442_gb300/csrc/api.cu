@@ -131,6 +131,20 @@ qw_status qw_plan_create(int dim, int64_t N, double mass, qw_dtype dtype, qw_pla
     qw_plan_destroy(p);
     return st;
   }
+  if (tma_step_supported(g) && dtype == QW_C64) {
+    int nsm = 0;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+    std::vector<int4> items = tma_item_table(g, 2 * nsm);
+    if (e == cudaSuccess) e = cudaMalloc(&p->tma_items, items.size() * sizeof(int4));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->tma_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "qw_plan_create: TMA item table");
+      qw_plan_destroy(p);
+      return st;
+    }
+    p->tma_nitems = (int)items.size();
+  }
   p->stencil = default_stencil(p);
   *out = p;
   return QW_OK;
@@ -144,6 +158,7 @@ qw_status qw_plan_destroy(qw_plan p) {
   if (p->red_result) cudaFree(p->red_result);
   if (p->red_host) cudaFreeHost(p->red_host);
   if (p->dev_flags) cudaFree(p->dev_flags);
+  if (p->tma_items) cudaFree(p->tma_items);
   delete p;
   return QW_OK;
 }
@@ -165,7 +180,8 @@ qw_status qw_step(qw_plan p, void* psi, int64_t nsteps, void* stream) {
   void* nxt = p->scratch;
   for (int64_t i = 0; i < nsteps; ++i) {
     if (p->stencil == QW_STENCIL_TMA)
-      st = launch_step_tma(p->g, p->n, p->mass, cur, nxt, p->dev_flags, p->dev_flags + 1, s);
+      st = launch_step_tma(p->g, p->n, p->mass, cur, nxt, p->tma_items, p->tma_nitems, p->dev_flags,
+                           p->dev_flags + 1, s);
     else
       st = launch_step(p->g, p->dtype, p->stencil, p->n, p->mass, cur, nxt, s);
     if (st != QW_OK) return st;

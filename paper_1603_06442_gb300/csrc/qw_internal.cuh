@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "qw.h"
 
 namespace qw {
@@ -62,8 +64,10 @@ bool stencil_supported(const Geometry& g, qw_dtype dt, int variant);
 qw_status launch_step(const Geometry& g, qw_dtype dt, int variant, double n, double m, const void* in, void* out,
                       cudaStream_t st);
 bool tma_step_supported(const Geometry& g);
-qw_status launch_step_tma(const Geometry& g, double n, double m, const void* in, void* out, int* err,
-                          int* next_item, cudaStream_t st);
+// Work items {tile, z_begin, z_end, 0} of the TMA stencil for `resident` CTAs.
+std::vector<int4> tma_item_table(const Geometry& g, int resident);
+qw_status launch_step_tma(const Geometry& g, double n, double m, const void* in, void* out, const int4* items,
+                          int nitems, int* err, int* next_item, cudaStream_t st);
 
 // ---- reductions (observables.cu) -------------------------------------------
 // Partial sums (norm, sum x|psi|^2, sum y|psi|^2, sum z|psi|^2) per block into
@@ -87,6 +91,8 @@ struct qw_plan_s {
   int stencil;          // qw_stencil_variant in use (never AUTO after creation)
   void* scratch;        // one field: ping-pong partner of the caller's buffer
   int* dev_flags;       // [0] error word of bounded device waits, [1] work counter
+  int4* tma_items;      // work-item table of the TMA stencil (device), or null
+  int tma_nitems;
   double* red_partials; // 4 * kObsBlocks doubles
   double* red_result;   // 4 doubles (device)
   double* red_host;     // 4 doubles (pinned host)

@@ -7,8 +7,8 @@
 //   output coset 1 at layer z reads coset 0 at layers z (h_z = +1) and z+1,
 // so each coset-layer is brought into shared memory once by one TMA tensor copy
 // (all four components, box [x0-2, x0+TX+2) x [y0-1, y0+TY+1)) and used by two
-// consecutive iterations.  The copy of the next layer pair is in flight while
-// the current one is computed (mbarrier completion, bounded waits).
+// consecutive iterations.  The copies of the next two layer pairs are in flight
+// while the current one is computed (mbarrier completion, bounded waits).
 // Cells outside [0, M) of an edge tile are zero-filled by the TMA unit and then
 // overwritten with their periodic images (loaded one iteration ahead).
 // Algorithmic traffic: one read and one write of the field per step; halo rows
@@ -16,6 +16,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+
+#include <vector>
 
 #include "qw_internal.cuh"
 
@@ -29,7 +31,7 @@ constexpr int ROWF = 2 * BXC;             // floats per row
 constexpr int CSTR = BY * ROWF;           // floats per component
 constexpr int BUF_FLOATS = 4 * CSTR;
 constexpr int BUF_BYTES = BUF_FLOATS * 4;
-constexpr int NSLOT = 3;                  // ring depth per coset
+constexpr int NSLOT = 4;                  // ring depth per coset: two layer pairs in flight
 constexpr int MAX_FIX = 3;                // periodic-image cells per thread per buffer
 constexpr int SMEM_BYTES = 2 * NSLOT * BUF_BYTES + 2 * NSLOT * 8 + 128;  // + alignment slack
 constexpr long long kSpinLimit = 1ll << 22;
@@ -189,7 +191,8 @@ struct Fix {
 
 __global__ void __launch_bounds__(NT, 2)
     step3d_c64_tma_kernel(const __grid_constant__ CUtensorMap map, const float2* __restrict__ in,
-                          float2* __restrict__ out, int M, int zchunk, Coef32 cf, int* err, int* next_item) {
+                          float2* __restrict__ out, int M, const int4* __restrict__ items, int nitems, Coef32 cf,
+                          int* err, int* next_item) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_item;
   // TMA destinations must be 128-byte aligned: align the dynamic block by hand
@@ -198,21 +201,19 @@ __global__ void __launch_bounds__(NT, 2)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * NSLOT * BUF_BYTES);
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int64_t plane = (int64_t)M * M, vol = plane * M;
-  const int tiles_x = M / TX, tiles_y = M / TY;
-  const int ntiles = tiles_x * tiles_y;
-  const int nchunks = (M + zchunk - 1) / zchunk;
-  const int nitems = ntiles * nchunks;
+  const int tiles_x = M / TX;
 
   for (;;) {
-    // dynamic schedule; consecutive items are consecutive z-chunks of one tile,
-    // so chunk-boundary layers and tile halos are shared in L2 by running CTAs
+    // dynamic schedule over a guided item table (long z-chunks first, short
+    // ones last): few pipeline restarts and a short tail
     if (tid == 0) s_item = atomicAdd(next_item, 1);
     __syncthreads();
     const int item = s_item;
     if (item >= nitems) break;
-    const int tile = item / nchunks, chunk = item % nchunks;
+    const int4 it = items[item];
+    const int tile = it.x;
     const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
-    const int zs = chunk * zchunk, ze = min(M, zs + zchunk);
+    const int zs = it.y, ze = it.z;
 
     // Periodic images of this tile's out-of-range box cells.  The region is the
     // edge columns (all rows) plus the edge rows (remaining columns); the k-th
@@ -282,37 +283,47 @@ __global__ void __launch_bounds__(NT, 2)
         if (i < fx.n) *reinterpret_cast<float2*>(b + fx.soff[i]) = v[i];
     };
 
-    float2 f1a[MAX_FIX], f0a[MAX_FIX], f1b[MAX_FIX], f0b[MAX_FIX];
+    // fix-up registers: A = pair waited on this iteration, B = next, C = fetched now
+    float2 f1a[MAX_FIX], f0a[MAX_FIX], f1b[MAX_FIX], f0b[MAX_FIX], f1c[MAX_FIX], f0c[MAX_FIX];
     bool ok = true;
-    // prologue: coset 1 layers zs-1, zs; coset 0 layers zs, zs+1
+    // prologue: coset 1 layers zs-1 .. zs+1, coset 0 layers zs .. zs+2
+    const bool two = (zs + 1 < ze);
     if (tid == 0) {
       fence_proxy_async();
       issue(slot1(zs - 1), 1, zs - 1);
-      issue(slot1(zs), 1, zs);
       issue(slot0(zs), 0, zs);
+      issue(slot1(zs), 1, zs);
       issue(slot0(zs + 1), 0, zs + 1);
+      if (two) {
+        issue(slot1(zs + 1), 1, zs + 1);
+        issue(slot0(zs + 2), 0, zs + 2);
+      }
     }
-    fetch_fix(1, zs - 1, f1b);
-    fetch_fix(0, zs, f0b);
+    fetch_fix(1, zs - 1, f1c);
+    fetch_fix(0, zs, f0c);
     fetch_fix(1, zs, f1a);
     fetch_fix(0, zs + 1, f0a);
+    if (two) {
+      fetch_fix(1, zs + 1, f1b);
+      fetch_fix(0, zs + 2, f0b);
+    }
     ok &= mbar_wait(&bars[slot1(zs - 1)], par1(zs - 1), err);
     ok &= mbar_wait(&bars[slot0(zs)], par0(zs), err);
-    store_fix(slot1(zs - 1), f1b);
-    store_fix(slot0(zs), f0b);
+    store_fix(slot1(zs - 1), f1c);
+    store_fix(slot0(zs), f0c);
     ok = __syncthreads_and(ok);
 
     for (int z = zs; z < ze && ok; ++z) {
-      // prefetch the next layer pair: coset 1 layer z+1, coset 0 layer z+2
-      const bool more = (z + 1 < ze);
+      // prefetch two layer pairs ahead: coset 1 layer z+2, coset 0 layer z+3
+      const bool more = (z + 2 < ze);
       if (more) {
         if (tid == 0) {
           fence_proxy_async();
-          issue(slot1(z + 1), 1, z + 1);
-          issue(slot0(z + 2), 0, z + 2);
+          issue(slot1(z + 2), 1, z + 2);
+          issue(slot0(z + 3), 0, z + 3);
         }
-        fetch_fix(1, z + 1, f1b);
-        fetch_fix(0, z + 2, f0b);
+        fetch_fix(1, z + 2, f1c);
+        fetch_fix(0, z + 3, f0c);
       }
       ok &= mbar_wait(&bars[slot1(z)], par1(z), err);
       ok &= mbar_wait(&bars[slot0(z + 1)], par0(z + 1), err);
@@ -336,6 +347,8 @@ __global__ void __launch_bounds__(NT, 2)
       for (int i = 0; i < MAX_FIX; ++i) {
         f1a[i] = f1b[i];
         f0a[i] = f0b[i];
+        f1b[i] = f1c[i];
+        f0b[i] = f0c[i];
       }
     }
     if (!ok) {
@@ -369,8 +382,33 @@ bool tma_step_supported(const Geometry& g) {
   return g.dim == 3 && g.nx % zm::TX == 0 && g.nx >= zm::TX && g.nx <= 4096;
 }
 
-qw_status launch_step_tma(const Geometry& g, double n, double m, const void* in, void* out, int* err,
-                          int* next_item, cudaStream_t st) {
+std::vector<int4> tma_item_table(const Geometry& g, int resident) {
+  // Every tile's z-range is cut the same way: chunks of 64 layers while more
+  // than a quarter of the box remains, then halving down to 8.  Items are
+  // ordered chunk by chunk over all tiles, so the short chunks come last (the
+  // tail of the dynamic schedule) and running CTAs work on neighbouring tiles
+  // at similar depths (shared halo rows stay in L2).
+  const int M = (int)g.nx;
+  const int ntiles = (M / zm::TX) * (M / zm::TY);
+  std::vector<int> cuts;  // chunk boundaries
+  int z = 0;
+  while (z < M) {
+    const int rem = M - z;
+    int c = 64;
+    while (c > 8 && (c > rem || (int64_t)ntiles * rem < (int64_t)resident * c)) c /= 2;
+    if (c > rem) c = rem;
+    cuts.push_back(z);
+    z += c;
+  }
+  cuts.push_back(M);
+  std::vector<int4> items;
+  for (size_t k = 0; k + 1 < cuts.size(); ++k)
+    for (int t = 0; t < ntiles; ++t) items.push_back(make_int4(t, cuts[k], cuts[k + 1], 0));
+  return items;
+}
+
+qw_status launch_step_tma(const Geometry& g, double n, double m, const void* in, void* out, const int4* items,
+                          int nitems, int* err, int* next_item, cudaStream_t st) {
   qw_status s = get_encoder();
   if (s != QW_OK) return s;
   const int M = (int)g.nx;
@@ -395,18 +433,11 @@ qw_status launch_step_tma(const Geometry& g, double n, double m, const void* in,
   int dev = 0, nsm = 0;
   QW_CHECK_CUDA(cudaGetDevice(&dev));
   QW_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int ntiles = (M / zm::TX) * (M / zm::TY);
-  // z-chunks of 32 layers (fewer when the box is small): enough items for a
-  // dynamic schedule over every resident CTA
   const int resident = 2 * nsm;
-  int zchunk = 32;
-  while (zchunk > 8 && (int64_t)ntiles * ((M + zchunk - 1) / zchunk) < 8 * resident) zchunk /= 2;
-  if (zchunk > M) zchunk = M;
-  const int nitems = ntiles * ((M + zchunk - 1) / zchunk);
   const int grid = nitems < resident ? nitems : resident;
   QW_CHECK_CUDA(cudaMemsetAsync(next_item, 0, sizeof(int), st));
   zm::step3d_c64_tma_kernel<<<grid, zm::NT, zm::SMEM_BYTES, st>>>(map, static_cast<const float2*>(in),
-                                                                   static_cast<float2*>(out), M, zchunk,
+                                                                   static_cast<float2*>(out), M, items, nitems,
                                                                    make_coef32(3, n, m), err, next_item);
   QW_CHECK_LAUNCH("tma stencil launch");
   return QW_OK;
