@@ -121,13 +121,36 @@ int qw_plan_get_stencil(qw_plan plan);
  * Errors: QW_EINVAL (null plan/pointer, nsteps < 0), QW_ECUDA. */
 qw_status qw_step(qw_plan plan, void* psi_dev, int64_t nsteps, void* stream);
 
+/* Build the spectral-path state of the plan: FFT pass plans and twiddle
+ * tables, and the FP64 table of omega_k = atan2(sin omega_k, n u_k) (Sec. 3.2,
+ * cos omega_k = n u_k) for every stored wave vector (one per site in 1D/2D,
+ * two per cell on the BCC lattice: 8 bytes per site).  Synchronous; done
+ * implicitly by the first qw_evolve_spectral / qw_observables call.
+ * Needs every axis length (N, or N/2 for dim 3) of the form 2^a 3^b.
+ * Errors: QW_EINVAL (axis length not 2^a 3^b), QW_ENOMEM, QW_ECUDA. */
+qw_status qw_plan_prepare_spectral(qw_plan plan);
+
+/* Evolve psi_dev in place to time t >= 0 in the Fourier form of Sec. 4:
+ * forward DFT of every component plane (hand-written batched FFT), the
+ * per-wave-vector product with D_k^t = cos(omega_k t) I - i sin(omega_k t) G_k/sin(omega_k)
+ * (D_k = cos(omega_k) I - i G_k, Sec. 3.2), with the BCC two-coset reduction of
+ * Eqs. bcc-dft / bcc-idft, and the inverse DFT.  omega_k t is reduced modulo
+ * 2 pi in FP64; the cost does not depend on t.  Asynchronous on `stream`
+ * (after the first call's synchronous preparation).  Same result as t calls
+ * of the update rule, up to rounding.
+ * Errors: QW_EINVAL (null plan/pointer, t < 0, axis length not 2^a 3^b),
+ * QW_ENOMEM, QW_ECUDA. */
+qw_status qw_evolve_spectral(qw_plan plan, void* psi_dev, int64_t t, void* stream);
+
 /* Wait for the plan's work on `stream`, then check its device error word.
  * Errors: QW_ETIMEOUT (a kernel's bounded wait gave up; the word is cleared),
  * QW_ECUDA. */
 qw_status qw_sync(qw_plan plan, void* stream);
 
 /* Compute the observables of psi_dev (see qw_obs).  Blocks the host until the
- * reductions on `stream` are done, then fills *out.
+ * reductions on `stream` are done, then fills *out.  The particle weights come
+ * from a forward DFT of a copy in the plan's scratch field; for boxes whose
+ * axis lengths are not 2^a 3^b they are NaN.
  * Errors: QW_EINVAL, QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
 qw_status qw_observables(qw_plan plan, const void* psi_dev, qw_obs* out, void* stream);
 

@@ -50,6 +50,8 @@ _SIGS = {
     "qw_plan_set_stencil": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "qw_plan_get_stencil": (ctypes.c_int, [ctypes.c_void_p]),
     "qw_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "qw_plan_prepare_spectral": (ctypes.c_int, [ctypes.c_void_p]),
+    "qw_evolve_spectral": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "qw_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(qw_obs),
                                       ctypes.c_void_p]),
 }
@@ -135,6 +137,14 @@ def qw_plan_get_stencil(plan):
     return load().qw_plan_get_stencil(plan)
 
 
+def qw_plan_prepare_spectral(plan):
+    _check(load().qw_plan_prepare_spectral(plan))
+
+
+def qw_evolve_spectral(plan, psi, t, stream=None):
+    _check(load().qw_evolve_spectral(plan, _ptr(psi), int(t), _stream(stream)))
+
+
 def qw_sync(plan, stream=None):
     _check(load().qw_sync(plan, _stream(stream)))
 
@@ -185,6 +195,13 @@ class Plan:
     @property
     def stencil(self):
         return qw_plan_get_stencil(self.handle)
+
+    def prepare_spectral(self):
+        qw_plan_prepare_spectral(self.handle)
+
+    def evolve_spectral(self, psi, t, stream=None):
+        self.check_field(psi)
+        qw_evolve_spectral(self.handle, psi, t, stream)
 
     def sync(self, stream=None):
         qw_sync(self.handle, stream)

@@ -71,6 +71,23 @@ static qw_status check_flags(qw_plan_s* p, cudaStream_t s) {
   return QW_OK;
 }
 
+static qw_status prepare_spectral(qw_plan_s* p) {
+  if (p->spec_ready) return QW_OK;
+  qw_status st = fft_plan_create(&p->fft, p->g, p->dtype);
+  if (st != QW_OK) {
+    fft_plan_destroy(&p->fft);
+    return st;
+  }
+  const int nq = p->g.dim == 3 ? 2 : 1;
+  QW_CHECK_CUDA(cudaMalloc(&p->omega, sizeof(double) * nq * p->g.vol));
+  QW_CHECK_CUDA(cudaMalloc(&p->spec_partials, sizeof(double) * 2 * kObsBlocks));
+  st = launch_omega_table(p->g, spec_axes(p->g, p->fft), p->n, p->mass, p->omega, 0);
+  if (st != QW_OK) return st;
+  QW_CHECK_CUDA(cudaDeviceSynchronize());
+  p->spec_ready = true;
+  return QW_OK;
+}
+
 static qw_status use_device(const qw_plan_s* p) {
   int cur = -1;
   QW_CHECK_CUDA(cudaGetDevice(&cur));
@@ -121,8 +138,8 @@ qw_status qw_plan_create(int dim, int64_t N, double mass, qw_dtype dtype, qw_pla
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaMalloc(&p->scratch, (size_t)g.elems * p->elem_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->red_partials, sizeof(double) * 4 * kObsBlocks);
-  if (e == cudaSuccess) e = cudaMalloc(&p->red_result, sizeof(double) * 4);
-  if (e == cudaSuccess) e = cudaMallocHost(&p->red_host, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&p->red_result, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMallocHost(&p->red_host, sizeof(double) * 8);
   if (e == cudaSuccess) e = cudaMalloc(&p->dev_flags, sizeof(int) * 2);
   if (e == cudaSuccess) e = cudaMemset(p->dev_flags, 0, sizeof(int) * 2);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -159,6 +176,9 @@ qw_status qw_plan_destroy(qw_plan p) {
   if (p->red_host) cudaFreeHost(p->red_host);
   if (p->dev_flags) cudaFree(p->dev_flags);
   if (p->tma_items) cudaFree(p->tma_items);
+  fft_plan_destroy(&p->fft);
+  if (p->omega) cudaFree(p->omega);
+  if (p->spec_partials) cudaFree(p->spec_partials);
   delete p;
   return QW_OK;
 }
@@ -214,6 +234,33 @@ qw_status qw_plan_set_stencil(qw_plan p, int variant) {
 
 int qw_plan_get_stencil(qw_plan p) { return p ? p->stencil : -1; }
 
+qw_status qw_plan_prepare_spectral(qw_plan p) {
+  if (!p) {
+    set_error("qw_plan_prepare_spectral: null plan");
+    return QW_EINVAL;
+  }
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  return prepare_spectral(p);
+}
+
+qw_status qw_evolve_spectral(qw_plan p, void* psi, int64_t t, void* stream) {
+  if (!p || !psi || t < 0) {
+    set_error("qw_evolve_spectral: null plan/field or t < 0");
+    return QW_EINVAL;
+  }
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  st = prepare_spectral(p);
+  if (st != QW_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = fft_forward(p->fft, p->g.dim, psi, s);
+  if (st != QW_OK) return st;
+  st = launch_evolve_pointwise(p->g, spec_axes(p->g, p->fft), p->dtype, p->n, p->mass, p->omega, t, psi, s);
+  if (st != QW_OK) return st;
+  return fft_inverse(p->fft, p->g.dim, psi, s);
+}
+
 qw_status qw_sync(qw_plan p, void* stream) {
   if (!p) {
     set_error("qw_sync: null plan");
@@ -234,14 +281,31 @@ qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   st = launch_position_moments(p->g, p->dtype, psi, p->red_partials, p->red_result, s);
   if (st != QW_OK) return st;
-  QW_CHECK_CUDA(cudaMemcpyAsync(p->red_host, p->red_result, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  // particle weights need the spectrum: forward DFT of a copy in the scratch field
+  const bool kspace = fft_size_ok(p->g.nx) && fft_size_ok(p->g.ny) && fft_size_ok(p->g.nz);
+  if (kspace) {
+    st = prepare_spectral(p);
+    if (st != QW_OK) return st;
+    QW_CHECK_CUDA(cudaMemcpyAsync(p->scratch, psi, (size_t)p->g.elems * p->elem_bytes, cudaMemcpyDeviceToDevice, s));
+    st = fft_forward(p->fft, p->g.dim, p->scratch, s);
+    if (st != QW_OK) return st;
+    st = launch_particle_weights(p->g, spec_axes(p->g, p->fft), p->dtype, p->n, p->mass, p->scratch,
+                                 p->spec_partials, p->red_result + 4, s);
+    if (st != QW_OK) return st;
+  }
+  QW_CHECK_CUDA(cudaMemcpyAsync(p->red_host, p->red_result, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
   st = check_flags(p, s);
   if (st != QW_OK) return st;
   const double* r = p->red_host;
   out->norm = r[0];
   for (int j = 0; j < 3; ++j) out->x_mean[j] = (j < p->g.dim && r[0] > 0) ? r[1 + j] / r[0] : 0.0;
-  out->w_particle = NAN;
-  out->w_antiparticle = NAN;
+  if (kspace && r[4] > 0) {
+    out->w_particle = 0.5 * (1.0 + r[5] / r[4]);
+    out->w_antiparticle = 0.5 * (1.0 - r[5] / r[4]);
+  } else {
+    out->w_particle = NAN;
+    out->w_antiparticle = NAN;
+  }
   return QW_OK;
 }
 

@@ -1,0 +1,495 @@
+// Batched in-place DFT passes along one axis of the device layout (the Fourier
+// form of Sec. 4 needs forward and inverse DFTs of every component plane; the
+// paper names the Cooley-Tukey FFT, this is a mixed-radix Stockham variant).
+//
+// Conventions: forward X[k] = sum_n x[n] exp(-2 pi i k n / L), inverse with
+// exp(+...) and no normalisation (the pointwise step applies 1/|V|).
+//
+// One pass transforms lines of length L <= kMaxLine whose elements sit at
+//     o * (L * S) + j * S + i          (o < O outer, j < L, i < S inner),
+// CTA tiles of C lines x L elements live in shared memory (ping-pong buffers,
+// line-minor with an odd pitch so both load patterns are conflict-free), and
+// every stage is a radix-R butterfly (R in 8, 4, 3, 2) of the Stockham
+// autosort recursion: natural order in, natural order out.
+//
+// Axes longer than kMaxLine are split L = A * B (Cooley-Tukey index map):
+// a pass of length A with stride B (followed by the twiddle
+// exp(-2 pi i k b / L)) and a pass of length B on contiguous segments.  The
+// spectrum is then left in the digit-permuted order position B k1 + k2 <->
+// frequency k1 + A k2, which the pointwise kernels decode; the inverse undoes
+// the passes in reverse order, so fields return in natural order.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "qw_fft.cuh"
+#include "qw_internal.cuh"
+
+namespace qw {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using t = float2; };
+template <> struct Cx<double> { using t = double2; };
+
+template <typename V>
+__device__ __forceinline__ V cmul(V a, V b) {
+  V r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename V>
+__device__ __forceinline__ V cmulc(V a, V b) {  // a * conj(b)
+  V r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.y * b.x - a.x * b.y;
+  return r;
+}
+template <typename V>
+__device__ __forceinline__ V cadd(V a, V b) {
+  a.x += b.x;
+  a.y += b.y;
+  return a;
+}
+template <typename V>
+__device__ __forceinline__ V csub(V a, V b) {
+  a.x -= b.x;
+  a.y -= b.y;
+  return a;
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, typename V>
+__device__ __forceinline__ V mul_mi(V a) {
+  V r;
+  if (INV) {
+    r.x = -a.y;
+    r.y = a.x;
+  } else {
+    r.x = a.y;
+    r.y = -a.x;
+  }
+  return r;
+}
+
+template <bool INV, typename V>
+__device__ __forceinline__ void dft2(V& a0, V& a1) {
+  V t = a0;
+  a0 = cadd(t, a1);
+  a1 = csub(t, a1);
+}
+
+template <bool INV, typename V>
+__device__ __forceinline__ void dft4(V& a0, V& a1, V& a2, V& a3) {
+  V s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  V s13 = cadd(a1, a3), d13 = mul_mi<INV>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+template <bool INV, typename T, typename V>
+__device__ __forceinline__ void dft3(V& a0, V& a1, V& a2) {
+  const T h = (T)0.86602540378443864676;  // sqrt(3)/2
+  V t1 = cadd(a1, a2), t2 = csub(a1, a2);
+  V b0 = cadd(a0, t1);
+  V m;
+  m.x = a0.x - (T)0.5 * t1.x;
+  m.y = a0.y - (T)0.5 * t1.y;
+  // forward: X1 = m - i h t2, X2 = m + i h t2 (inverse swaps)
+  V r;
+  r.x = h * t2.y;
+  r.y = -h * t2.x;  // -i h t2
+  if (INV) {
+    r.x = -r.x;
+    r.y = -r.y;
+  }
+  a0 = b0;
+  a1 = cadd(m, r);
+  a2 = csub(m, r);
+}
+
+template <bool INV, typename T, typename V>
+__device__ __forceinline__ void dft8(V (&a)[8]) {
+  // even/odd split into two radix-4 transforms
+  dft4<INV>(a[0], a[2], a[4], a[6]);
+  dft4<INV>(a[1], a[3], a[5], a[7]);
+  const T r2 = (T)0.70710678118654752440;
+  // twiddles w8^k, w8 = exp(-+ 2 pi i / 8)
+  V o1 = a[3], o2 = a[5], o3 = a[7];
+  V w1, w3;
+  if (INV) {
+    w1.x = r2 * (o1.x - o1.y);
+    w1.y = r2 * (o1.x + o1.y);
+    w3.x = -r2 * (o3.x + o3.y);
+    w3.y = r2 * (o3.x - o3.y);
+  } else {
+    w1.x = r2 * (o1.x + o1.y);
+    w1.y = r2 * (o1.y - o1.x);
+    w3.x = r2 * (o3.y - o3.x);
+    w3.y = -r2 * (o3.x + o3.y);
+  }
+  V w2 = mul_mi<INV>(o2);
+  V e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6], o0 = a[1];
+  a[0] = cadd(e0, o0);
+  a[4] = csub(e0, o0);
+  a[1] = cadd(e1, w1);
+  a[5] = csub(e1, w1);
+  a[2] = cadd(e2, w2);
+  a[6] = csub(e2, w2);
+  a[3] = cadd(e3, w3);
+  a[7] = csub(e3, w3);
+}
+
+// omega_N^m = exp(-2 pi i m / N) from the two-level table (m < N)
+template <typename V>
+__device__ __forceinline__ V twiddle_big(const V* hi, const V* lo, int64_t m, int tlo_bits) {
+  const int64_t mh = m >> tlo_bits;
+  const int64_t ml = m & ((int64_t(1) << tlo_bits) - 1);
+  return cmul(hi[mh], lo[ml]);
+}
+
+template <typename T, bool INV>
+__global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __restrict__ data, FftPass p,
+                                                       const typename Cx<T>::t* __restrict__ tw_line,
+                                                       const typename Cx<T>::t* __restrict__ tw_hi,
+                                                       const typename Cx<T>::t* __restrict__ tw_lo) {
+  using V = typename Cx<T>::t;
+  extern __shared__ __align__(16) unsigned char fft_smem[];
+  V* bufA = reinterpret_cast<V*>(fft_smem);
+  V* bufB = bufA + (size_t)p.L * p.pitch;
+  const int L = p.L, C = p.C, pitch = p.pitch;
+  const int64_t S = p.S;
+  const int64_t nlines = p.O * S;
+  const int64_t l0 = (int64_t)blockIdx.x * C;
+  const int ncol = (int)((nlines - l0) < C ? (nlines - l0) : C);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int total = L * ncol;
+
+  // ---- load (and undo the inter-pass twiddle on the inverse) ----
+  for (int e = tid; e < total; e += nthr) {
+    int j, c;
+    if (S == 1) {
+      c = e / L;
+      j = e - c * L;
+    } else {
+      j = e / ncol;
+      c = e - j * ncol;
+    }
+    const int64_t l = l0 + c;
+    const int64_t o = l / S, i = l - o * S;
+    V v = data[o * (int64_t)L * S + (int64_t)j * S + i];
+    if (INV && p.twiddle) v = cmulc(v, twiddle_big(tw_hi, tw_lo, (int64_t)j * (i / p.tw_div), p.tlo_bits));
+    bufA[j * pitch + c] = v;
+  }
+  __syncthreads();
+
+  // ---- Stockham stages ----
+  V* in = bufA;
+  V* out = bufB;
+  int Ns = 1;
+  for (int s = 0; s < p.nstages; ++s) {
+    const int R = p.radix[s];
+    const int nb = L / R;
+    const int tstep = L / (Ns * R);  // table stride of omega_{Ns R}
+    for (int b = tid; b < nb * ncol; b += nthr) {
+      const int jb = b / ncol, c = b - jb * ncol;
+      const int k = jb % Ns;
+      const int idxD = (jb / Ns) * Ns * R + k;
+      if (R == 8) {
+        V a[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          a[r] = in[(jb + r * nb) * pitch + c];
+          if (r > 0 && Ns > 1) {
+            const V w = tw_line[r * k * tstep];
+            a[r] = INV ? cmulc(a[r], w) : cmul(a[r], w);
+          }
+        }
+        dft8<INV, T>(a);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) out[(idxD + r * Ns) * pitch + c] = a[r];
+      } else if (R == 4) {
+        V a[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          a[r] = in[(jb + r * nb) * pitch + c];
+          if (r > 0 && Ns > 1) {
+            const V w = tw_line[r * k * tstep];
+            a[r] = INV ? cmulc(a[r], w) : cmul(a[r], w);
+          }
+        }
+        dft4<INV>(a[0], a[1], a[2], a[3]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) out[(idxD + r * Ns) * pitch + c] = a[r];
+      } else if (R == 3) {
+        V a[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          a[r] = in[(jb + r * nb) * pitch + c];
+          if (r > 0 && Ns > 1) {
+            const V w = tw_line[r * k * tstep];
+            a[r] = INV ? cmulc(a[r], w) : cmul(a[r], w);
+          }
+        }
+        dft3<INV, T>(a[0], a[1], a[2]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) out[(idxD + r * Ns) * pitch + c] = a[r];
+      } else {
+        V a0 = in[jb * pitch + c], a1 = in[(jb + nb) * pitch + c];
+        if (Ns > 1) {
+          const V w = tw_line[k * tstep];
+          a1 = INV ? cmulc(a1, w) : cmul(a1, w);
+        }
+        dft2<INV>(a0, a1);
+        out[idxD * pitch + c] = a0;
+        out[(idxD + Ns) * pitch + c] = a1;
+      }
+    }
+    __syncthreads();
+    V* t = in;
+    in = out;
+    out = t;
+    Ns *= R;
+  }
+
+  // ---- store (apply the inter-pass twiddle on the forward) ----
+  for (int e = tid; e < total; e += nthr) {
+    int j, c;
+    if (S == 1) {
+      c = e / L;
+      j = e - c * L;
+    } else {
+      j = e / ncol;
+      c = e - j * ncol;
+    }
+    const int64_t l = l0 + c;
+    const int64_t o = l / S, i = l - o * S;
+    V v = in[j * pitch + c];
+    if (!INV && p.twiddle) v = cmul(v, twiddle_big(tw_hi, tw_lo, (int64_t)j * (i / p.tw_div), p.tlo_bits));
+    data[o * (int64_t)L * S + (int64_t)j * S + i] = v;
+  }
+}
+
+// ---------------------------------------------------------------- planning
+static bool radix_plan(int L, int* radix, int* n) {
+  int k = 0;
+  int r = L;
+  while (r % 8 == 0 && r > 0) { radix[k++] = 8; r /= 8; }
+  while (r % 4 == 0 && r > 0) { radix[k++] = 4; r /= 4; }
+  while (r % 2 == 0 && r > 0) { radix[k++] = 2; r /= 2; }
+  while (r % 3 == 0 && r > 0) { radix[k++] = 3; r /= 3; }
+  if (r != 1 || k > kMaxStages) return false;
+  *n = k;
+  return true;
+}
+
+bool fft_size_ok(int64_t L) {
+  if (L < 1) return false;
+  while (L % 2 == 0) L /= 2;
+  while (L % 3 == 0) L /= 3;
+  return L == 1;
+}
+
+// Split an axis of length L into 1-3 pass lengths <= maxline (each 2^a 3^b).
+static bool split_axis(int64_t L, int maxline, std::vector<int>* parts) {
+  parts->clear();
+  if (L <= maxline) {
+    parts->push_back((int)L);
+    return true;
+  }
+  // greedy: first factor = the largest 2^a 3^b <= maxline dividing L, recurse on the rest
+  int64_t rest = L;
+  while (rest > maxline) {
+    int best = 0;
+    for (int64_t a = 1; a <= maxline; a *= 2)
+      for (int64_t b = a; b <= maxline; b *= 3)
+        if (rest % b == 0 && b > best && rest / b > 1) best = (int)b;
+    if (best <= 1) return false;
+    parts->push_back(best);
+    rest /= best;
+    if (parts->size() >= 3) return false;
+  }
+  parts->push_back((int)rest);
+  return true;
+}
+
+template <typename T>
+static void host_table(std::vector<typename Cx<T>::t>* out, int64_t N, int64_t count, int64_t mult) {
+  out->resize(count);
+  for (int64_t m = 0; m < count; ++m) {
+    // exp(-2 pi i (m * mult mod N) / N), exact integer reduction before the angle
+    const int64_t e = (m * mult) % N;
+    const double ang = -2.0 * M_PI * (double)e / (double)N;
+    (*out)[m].x = (T)std::cos(ang);
+    (*out)[m].y = (T)std::sin(ang);
+  }
+}
+
+template <typename T>
+static qw_status upload(const std::vector<typename Cx<T>::t>& h, void** dev) {
+  QW_CHECK_CUDA(cudaMalloc(dev, h.size() * sizeof(h[0])));
+  QW_CHECK_CUDA(cudaMemcpy(*dev, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice));
+  return QW_OK;
+}
+
+template <typename T>
+static qw_status build_pass(FftPass* p, int L, int64_t S, int64_t O, int64_t tw_N, int64_t tw_div, bool twiddle) {
+  p->L = L;
+  p->S = S;
+  p->O = O;
+  if (!radix_plan(L, p->radix, &p->nstages)) {
+    set_error("FFT length %d is not 2^a 3^b", L);
+    return QW_EINVAL;
+  }
+  const int esz = (int)sizeof(typename Cx<T>::t);
+  const int budget = kFftSmemBytes / (2 * esz);  // elements per ping-pong buffer
+  int C = budget / L;
+  C = C > 16 ? 16 : (C < 1 ? 1 : C);
+  int64_t nlines = O * S;
+  if (C > nlines) C = (int)nlines;
+  p->C = C;
+  p->pitch = (C % 2 == 0) ? C + 1 : C;
+  p->smem = 2 * (size_t)L * p->pitch * esz;
+  p->twiddle = twiddle ? 1 : 0;
+  p->tw_N = tw_N;
+  p->tw_div = tw_div;
+  p->tlo_bits = 12;
+  // per-line table omega_L^m, and the two-level table of omega_{tw_N}
+  std::vector<typename Cx<T>::t> h;
+  host_table<T>(&h, L, L, 1);
+  qw_status st = upload<T>(h, &p->tw_line);
+  if (st != QW_OK) return st;
+  if (twiddle) {
+    const int64_t T_lo = int64_t(1) << p->tlo_bits;
+    host_table<T>(&h, tw_N, T_lo, 1);
+    st = upload<T>(h, &p->tw_lo);
+    if (st != QW_OK) return st;
+    host_table<T>(&h, tw_N, (tw_N + T_lo - 1) / T_lo, T_lo);
+    st = upload<T>(h, &p->tw_hi);
+    if (st != QW_OK) return st;
+  }
+  return QW_OK;
+}
+
+template <typename T>
+static qw_status fft_plan_t(FftPlan* f, const Geometry& g) {
+  const int maxline = (sizeof(T) == 4) ? kMaxLineF32 : kMaxLineF64;
+  f->npass = 0;
+  const int P = g.ncoset * g.s;
+  const int64_t ext[3] = {g.nx, g.ny, g.nz};
+  for (int ax = 0; ax < g.dim && ax < 3; ++ax) {
+    const int axis = (g.dim == 3) ? ax : ax;  // 3D: x, y, z; 2D: x, y; 1D: x
+    const int64_t L = ext[axis];
+    if (!fft_size_ok(L)) {
+      set_error("spectral path needs 2^a 3^b axis lengths (got %lld)", (long long)L);
+      return QW_EINVAL;
+    }
+    std::vector<int> parts;
+    if (!split_axis(L, maxline, &parts)) {
+      set_error("axis length %lld cannot be split into <= 3 passes of <= %d", (long long)L, maxline);
+      return QW_EINVAL;
+    }
+    int64_t base = 1;  // stride of this axis
+    for (int a = 0; a < axis; ++a) base *= ext[a];
+    const int64_t outer_total = (int64_t)P * g.vol / (L * base);  // independent lines of this axis
+    FftAxis& A = f->axis[ax];
+    A.nparts = (int)parts.size();
+    for (size_t q = 0; q < parts.size(); ++q) A.part[q] = parts[q];
+    A.first = f->npass;
+    // pass q transforms digit q: length parts[q], stride = base * prod(parts[q+1..]),
+    // segments of length seg = parts[q] * stride repeat over outer * prod(parts[..q-1])
+    int64_t seg = L * base;
+    int64_t before = 1;
+    for (size_t q = 0; q < parts.size(); ++q) {
+      const int64_t Lq = parts[q];
+      const int64_t stride = seg / Lq;
+      const int64_t O = outer_total * before;
+      const bool tw = (q + 1 < parts.size());
+      qw_status st = build_pass<T>(&f->pass[f->npass], (int)Lq, stride, O, seg / base, base, tw);
+      if (st != QW_OK) return st;
+      f->npass++;
+      seg = stride;
+      before *= Lq;
+    }
+    A.count = f->npass - A.first;
+  }
+  return QW_OK;
+}
+
+qw_status fft_plan_create(FftPlan* f, const Geometry& g, qw_dtype dt) {
+  *f = FftPlan();
+  f->dtype = dt;
+  return dt == QW_C64 ? fft_plan_t<float>(f, g) : fft_plan_t<double>(f, g);
+}
+
+void fft_plan_destroy(FftPlan* f) {
+  for (int i = 0; i < f->npass; ++i) {
+    if (f->pass[i].tw_line) cudaFree(f->pass[i].tw_line);
+    if (f->pass[i].tw_hi) cudaFree(f->pass[i].tw_hi);
+    if (f->pass[i].tw_lo) cudaFree(f->pass[i].tw_lo);
+  }
+  f->npass = 0;
+}
+
+template <typename T, bool INV>
+static qw_status run_pass(const FftPass& p, void* data, cudaStream_t st) {
+  using V = typename Cx<T>::t;
+  static bool attr[2] = {false, false};
+  if (!attr[INV]) {
+    QW_CHECK_CUDA(cudaFuncSetAttribute(fft_pass_kernel<T, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kFftSmemBytes + 64));
+    attr[INV] = true;
+  }
+  const int64_t nlines = p.O * p.S;
+  const int64_t grid = (nlines + p.C - 1) / p.C;
+  if (grid > 0x7fffffff) {
+    set_error("FFT grid too large");
+    return QW_EINVAL;
+  }
+  fft_pass_kernel<T, INV><<<(unsigned)grid, 256, p.smem, st>>>(static_cast<V*>(data), p,
+                                                               static_cast<const V*>(p.tw_line),
+                                                               static_cast<const V*>(p.tw_hi),
+                                                               static_cast<const V*>(p.tw_lo));
+  QW_CHECK_LAUNCH("fft pass launch");
+  return QW_OK;
+}
+
+qw_status fft_forward_axis(const FftPlan& f, int ax, void* data, cudaStream_t st) {
+  const FftAxis& A = f.axis[ax];
+  for (int q = 0; q < A.count; ++q) {
+    const FftPass& p = f.pass[A.first + q];
+    qw_status s = f.dtype == QW_C64 ? run_pass<float, false>(p, data, st) : run_pass<double, false>(p, data, st);
+    if (s != QW_OK) return s;
+  }
+  return QW_OK;
+}
+
+qw_status fft_inverse_axis(const FftPlan& f, int ax, void* data, cudaStream_t st) {
+  const FftAxis& A = f.axis[ax];
+  for (int q = A.count - 1; q >= 0; --q) {
+    const FftPass& p = f.pass[A.first + q];
+    qw_status s = f.dtype == QW_C64 ? run_pass<float, true>(p, data, st) : run_pass<double, true>(p, data, st);
+    if (s != QW_OK) return s;
+  }
+  return QW_OK;
+}
+
+qw_status fft_forward(const FftPlan& f, int dim, void* data, cudaStream_t st) {
+  for (int ax = 0; ax < dim; ++ax) {
+    qw_status s = fft_forward_axis(f, ax, data, st);
+    if (s != QW_OK) return s;
+  }
+  return QW_OK;
+}
+
+qw_status fft_inverse(const FftPlan& f, int dim, void* data, cudaStream_t st) {
+  for (int ax = dim - 1; ax >= 0; --ax) {
+    qw_status s = fft_inverse_axis(f, ax, data, st);
+    if (s != QW_OK) return s;
+  }
+  return QW_OK;
+}
+
+}  // namespace qw

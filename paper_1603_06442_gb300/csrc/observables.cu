@@ -17,31 +17,7 @@ template <typename R> struct Cplx;
 template <> struct Cplx<float> { using T = float2; };
 template <> struct Cplx<double> { using T = double2; };
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Reduce 4 doubles over the block; thread 0 gets the totals in acc[].
-__device__ __forceinline__ void block_sum4(double acc[4]) {
-  __shared__ double sh[kObsThreads / 32][4];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) acc[j] = warp_sum(acc[j]);
-  if (lane == 0) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) sh[wid][j] = acc[j];
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      double v = lane < kObsThreads / 32 ? sh[lane][j] : 0.0;
-      acc[j] = warp_sum(v);
-    }
-  }
-}
+__device__ __forceinline__ void block_sum4(double (&acc)[4]) { block_sum<4, kObsThreads>(acc); }
 
 template <typename R, int SEG>
 __global__ void __launch_bounds__(kObsThreads) moments_kernel(const typename Cplx<R>::T* __restrict__ psi,

@@ -1,0 +1,60 @@
+// FFT plan types of the spectral path (fft.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qw.h"
+
+namespace qw {
+
+struct Geometry;
+
+constexpr int kMaxStages = 16;
+constexpr int kFftSmemBytes = 131072;   // two ping-pong tiles
+constexpr int kMaxLineF32 = 8192;       // longest single-pass line (complex64)
+constexpr int kMaxLineF64 = 4096;       // (complex128)
+
+// One in-place pass: DFTs of length L over elements o*(L*S) + j*S + i.
+struct FftPass {
+  int L;
+  int64_t S;
+  int64_t O;
+  int C;            // lines per CTA
+  int pitch;        // shared-memory line pitch (elements)
+  size_t smem;      // dynamic shared memory bytes
+  int nstages;
+  int radix[kMaxStages];
+  int twiddle;      // apply exp(-+2 pi i k (i / tw_div) / tw_N) after (forward) / before (inverse)
+  int64_t tw_N;
+  int64_t tw_div;
+  int tlo_bits;
+  void* tw_line = nullptr;  // exp(-2 pi i m / L), m < L
+  void* tw_hi = nullptr;    // two-level table of exp(-2 pi i m / tw_N)
+  void* tw_lo = nullptr;
+};
+
+struct FftAxis {
+  int nparts;       // 1..3 digits of the axis length
+  int part[3];
+  int first;        // index of the first pass
+  int count;
+};
+
+struct FftPlan {
+  qw_dtype dtype = QW_C64;
+  int npass = 0;
+  FftPass pass[9];
+  FftAxis axis[3];
+};
+
+bool fft_size_ok(int64_t L);
+qw_status fft_plan_create(FftPlan* f, const Geometry& g, qw_dtype dt);
+void fft_plan_destroy(FftPlan* f);
+// Forward over all axes (x, then y, then z) / inverse (z, y, x); unnormalised.
+qw_status fft_forward(const FftPlan& f, int dim, void* data, cudaStream_t st);
+qw_status fft_inverse(const FftPlan& f, int dim, void* data, cudaStream_t st);
+qw_status fft_forward_axis(const FftPlan& f, int ax, void* data, cudaStream_t st);
+qw_status fft_inverse_axis(const FftPlan& f, int ax, void* data, cudaStream_t st);
+
+}  // namespace qw

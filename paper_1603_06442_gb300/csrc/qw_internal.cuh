@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "qw.h"
+#include "qw_fft.cuh"
 
 namespace qw {
 
@@ -69,6 +70,32 @@ std::vector<int4> tma_item_table(const Geometry& g, int resident);
 qw_status launch_step_tma(const Geometry& g, double n, double m, const void* in, void* out, const int4* items,
                           int nitems, int* err, int* next_item, cudaStream_t st);
 
+// ---- device reduction helpers ------------------------------------------------
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum NV doubles over a block of NT threads; thread 0 holds the totals.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum(double (&acc)[NV]) {
+  __shared__ double sh[NT / 32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) acc[j] = warp_sum_d(acc[j]);
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sh[wid][j] = acc[j];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = warp_sum_d(lane < NT / 32 ? sh[lane][j] : 0.0);
+  }
+  __syncthreads();
+}
+
 // ---- reductions (observables.cu) -------------------------------------------
 // Partial sums (norm, sum x|psi|^2, sum y|psi|^2, sum z|psi|^2) per block into
 // `partials` (4 * kObsBlocks doubles), then one block folds them in a fixed
@@ -77,6 +104,22 @@ constexpr int kObsBlocks = 608;  // 4 x 152 SMs
 constexpr int kObsThreads = 256;
 qw_status launch_position_moments(const Geometry& g, qw_dtype dt, const void* psi, double* partials,
                                   double* result, cudaStream_t st);
+
+// ---- spectral path (spectral.cu) ---------------------------------------------
+struct SpecAxes {  // digit split of each axis (storage order -> frequency)
+  int nparts[3];
+  int part[3][3];
+  int64_t len[3];
+};
+SpecAxes spec_axes(const Geometry& g, const FftPlan& f);
+qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,
+                             cudaStream_t st);
+// psi_hat (forward DFT, storage order) <- D_k^t psi_hat / |V|, BCC cosets mixed per cell.
+qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
+                                  const double* omega, int64_t t, void* psi_hat, cudaStream_t st);
+// (sum |psi^|^2, sum psi^dag G/sin(omega) psi^) over the zone into result[0..1].
+qw_status launch_particle_weights(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
+                                  const void* psi_hat, double* partials, double* result, cudaStream_t st);
 
 }  // namespace qw
 
@@ -93,6 +136,11 @@ struct qw_plan_s {
   int* dev_flags;       // [0] error word of bounded device waits, [1] work counter
   int4* tma_items;      // work-item table of the TMA stencil (device), or null
   int tma_nitems;
+  // spectral path (allocated by the first spectral call or qw_plan_prepare_spectral)
+  bool spec_ready;
+  qw::FftPlan fft;
+  double* omega;        // omega_k per stored wave vector (two per cell on the BCC lattice)
+  double* spec_partials;  // 2 * kObsBlocks doubles for the particle-weight reduction
   double* red_partials; // 4 * kObsBlocks doubles
   double* red_result;   // 4 doubles (device)
   double* red_host;     // 4 doubles (pinned host)

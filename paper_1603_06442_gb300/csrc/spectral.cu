@@ -1,0 +1,497 @@
+// Fourier form of the walk (Sec. 4): psi(t) = IDFT[ D_k^t DFT[psi(0)] ].
+//
+// D_k^t in closed form.  With D_k = n u_k I - i G_k (Sec. 3.2; the Dirac block
+// form gives G_k = [[n sigma.n~_k, -m I], [-m I, -n sigma.n~_k]], and in 1D
+// G_k = [[n sin k, -m], [-m, -n sin k]]), G_k is Hermitian with
+// G_k^2 = (m^2 + n^2 |n~_k|^2) I = sin^2(omega_k) I because u^2 + |n~|^2 = 1,
+// so D_k = exp(-i omega_k G^_k) with G^_k = G_k / sin(omega_k) and
+//     D_k^t = cos(omega_k t) I - i sin(omega_k t) G^_k ,
+// the Chebyshev form (sin(omega t)/sin(omega) = U_{t-1}(cos omega)).
+// omega_k = atan2(sin omega_k, n u_k) (the paper's arccos(n u_k), Sec. 3.2) is
+// tabulated once per plan in FP64; each call reduces omega_k t modulo 2 pi in
+// FP64 (exact product low part included), so the phase stays accurate for
+// t up to ~1e6 and beyond.  Where sin(omega_k) = 0 (m = 0 and n~_k = 0)
+// D_k = +-I and G^_k is taken as 0.
+//
+// BCC lattice (Eqs. bcc-dft, bcc-idft): the coset DFTs Psi^0, Psi^1 at the cell
+// wave vector kappa in [0, 2 pi)^3 hold the two BCC wave vectors
+// q0 = kappa/2 and q1 = kappa/2 + (pi, 0, 0); with a = exp(i (k1+k2+k3)/2),
+//     c0 = (Psi^0 + a* Psi^1)/2,  c1 = (Psi^0 - a* Psi^1)/2,
+// each evolves with its own D_q^t, and Psi^0 = c0 + c1, Psi^1 = a (c0 - c1).
+// This is the paper's two-rectangular-DFT reduction written for the
+// exp(-i k.x) forward convention.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "qw_internal.cuh"
+
+namespace qw {
+
+template <typename T> struct Cx2;
+template <> struct Cx2<float> { using t = float2; };
+template <> struct Cx2<double> { using t = double2; };
+
+template <typename V, typename T>
+__device__ __forceinline__ V make_vec(V v, T s) {
+  v.x *= s;
+  v.y *= s;
+  return v;
+}
+
+struct AxesDev {
+  int nparts[3];
+  int part[3][3];
+  int64_t len[3];
+};
+
+SpecAxes spec_axes(const Geometry& g, const FftPlan& f) {
+  SpecAxes a;
+  const int64_t ext[3] = {g.nx, g.ny, g.nz};
+  for (int ax = 0; ax < 3; ++ax) {
+    a.len[ax] = ext[ax];
+    a.nparts[ax] = 1;
+    a.part[ax][0] = (int)ext[ax];
+    a.part[ax][1] = a.part[ax][2] = 1;
+    if (ax < g.dim) {
+      a.nparts[ax] = f.axis[ax].nparts;
+      for (int q = 0; q < 3; ++q) a.part[ax][q] = q < f.axis[ax].nparts ? f.axis[ax].part[q] : 1;
+    }
+  }
+  return a;
+}
+
+static AxesDev to_dev(const SpecAxes& a) {
+  AxesDev d;
+  for (int ax = 0; ax < 3; ++ax) {
+    d.nparts[ax] = a.nparts[ax];
+    d.len[ax] = a.len[ax];
+    for (int q = 0; q < 3; ++q) d.part[ax][q] = a.part[ax][q];
+  }
+  return d;
+}
+
+// Frequency index of storage position p on an axis split into digits
+// (A), (A, B) or (A, B1, B2): the passes leave frequency k1 + A k2 at B k1 + k2
+// (and, recursively, k1 + A (k1' + B1 k2') at B k1 + B2 k1' + k2').
+__device__ __forceinline__ int64_t freq_of(int64_t p, const AxesDev& a, int ax) {
+  const int np = a.nparts[ax];
+  if (np == 1) return p;
+  const int64_t A = a.part[ax][0];
+  const int64_t B = a.len[ax] / A;
+  const int64_t k1 = p / B, r = p - k1 * B;
+  if (np == 2) return k1 + A * r;
+  const int64_t B1 = a.part[ax][1], B2 = a.part[ax][2];
+  const int64_t k1b = r / B2, k2b = r - k1b * B2;
+  return k1 + A * (k1b + B1 * k2b);
+}
+
+// ---------------------------------------------------------------- symbols (FP64)
+// u_k, n~_k of Eqs. weyl1d / weyl2d / weyl3d; 2D at k_x = (k1 + k2)/2, k_y = (k1 - k2)/2.
+__device__ __forceinline__ void symbol64(int dim, double k1, double k2, double k3, double& u, double& nx,
+                                         double& ny, double& nz) {
+  if (dim == 1) {
+    double s, c;
+    sincos(k1, &s, &c);
+    u = c;
+    nx = 0.0;
+    ny = 0.0;
+    nz = s;
+  } else if (dim == 2) {
+    double sx, cx, sy, cy;
+    sincos(0.5 * (k1 + k2), &sx, &cx);
+    sincos(0.5 * (k1 - k2), &sy, &cy);
+    u = cx * cy;
+    nx = sx * cy;
+    ny = cx * sy;
+    nz = sx * sy;
+  } else {
+    double sx, cx, sy, cy, sz, cz;
+    sincos(k1, &sx, &cx);
+    sincos(k2, &sy, &cy);
+    sincos(k3, &sz, &cz);
+    u = cx * cy * cz + sx * sy * sz;
+    nx = sx * cy * cz - cx * sy * sz;
+    ny = cx * sy * cz + sx * cy * sz;
+    nz = cx * cy * sz - sx * sy * cz;
+  }
+}
+
+__device__ __forceinline__ void symbol32(int dim, float k1, float k2, float k3, float& u, float& nx, float& ny,
+                                         float& nz) {
+  if (dim == 1) {
+    float s, c;
+    sincosf(k1, &s, &c);
+    u = c;
+    nx = 0.f;
+    ny = 0.f;
+    nz = s;
+  } else if (dim == 2) {
+    float sx, cx, sy, cy;
+    sincosf(0.5f * (k1 + k2), &sx, &cx);
+    sincosf(0.5f * (k1 - k2), &sy, &cy);
+    u = cx * cy;
+    nx = sx * cy;
+    ny = cx * sy;
+    nz = sx * sy;
+  } else {
+    float sx, cx, sy, cy, sz, cz;
+    sincosf(k1, &sx, &cx);
+    sincosf(k2, &sy, &cy);
+    sincosf(k3, &sz, &cz);
+    u = cx * cy * cz + sx * sy * sz;
+    nx = sx * cy * cz - cx * sy * sz;
+    ny = cx * sy * cz + sx * cy * sz;
+    nz = cx * cy * sz - sx * sy * cz;
+  }
+}
+
+// Wave vectors of storage index idx: 1D/2D one vector, BCC two (q0, q1).
+__device__ __forceinline__ void wave_vectors(int dim, int64_t idx, const AxesDev& a, double (&k)[3],
+                                             double& half_sum) {
+  const double TWO_PI = 6.283185307179586476925286766559;
+  const int64_t nx = a.len[0], ny = a.len[1];
+  const int64_t x = idx % nx, y = (idx / nx) % ny, z = idx / (nx * ny);
+  const int64_t fx = freq_of(x, a, 0);
+  const int64_t fy = dim >= 2 ? freq_of(y, a, 1) : 0;
+  const int64_t fz = dim >= 3 ? freq_of(z, a, 2) : 0;
+  k[0] = TWO_PI * (double)fx / (double)nx;
+  k[1] = dim >= 2 ? TWO_PI * (double)fy / (double)ny : 0.0;
+  k[2] = dim >= 3 ? TWO_PI * (double)fz / (double)a.len[2] : 0.0;
+  half_sum = 0.5 * (k[0] + k[1] + k[2]);
+}
+
+__global__ void omega_kernel(int dim, AxesDev a, int64_t count, double n, double m, double* __restrict__ omega) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double k[3], hs;
+    wave_vectors(dim, idx, a, k, hs);
+    const int nq = dim == 3 ? 2 : 1;
+    for (int q = 0; q < nq; ++q) {
+      double k1 = k[0], k2 = k[1], k3 = k[2];
+      if (dim == 3) {
+        k1 = 0.5 * k1 + (q ? 3.141592653589793238462643383279 : 0.0);
+        k2 *= 0.5;
+        k3 *= 0.5;
+      }
+      double u, nx, ny, nz;
+      symbol64(dim, k1, k2, k3, u, nx, ny, nz);
+      const double sw = sqrt(m * m + n * n * (nx * nx + ny * ny + nz * nz));
+      omega[idx * nq + q] = atan2(sw, n * u);
+    }
+  }
+}
+
+// (cos, sin) of omega t with omega t reduced modulo 2 pi in FP64.
+__device__ __forceinline__ void phase(double omega, double tt, double& c, double& s) {
+  const double TWO_PI_HI = 6.283185307179586232e+00;
+  const double TWO_PI_LO = 2.449293598294706e-16;
+  const double p = omega * tt;
+  const double e = fma(omega, tt, -p);  // exact low part of the product
+  const double kq = rint(p * 0.15915494309189533577);
+  double r = fma(-kq, TWO_PI_HI, p);
+  r = fma(-kq, TWO_PI_LO, r) + e;
+  sincos(r, &s, &c);
+}
+__device__ __forceinline__ void phase32(double omega, double tt, float& c, float& s) {
+  const double TWO_PI_HI = 6.283185307179586232e+00;
+  const double TWO_PI_LO = 2.449293598294706e-16;
+  const double p = omega * tt;
+  const double e = fma(omega, tt, -p);
+  const double kq = rint(p * 0.15915494309189533577);
+  double r = fma(-kq, TWO_PI_HI, p);
+  r = fma(-kq, TWO_PI_LO, r) + e;
+  sincosf((float)r, &s, &c);
+}
+
+// out = cos(phi) v - i sin(phi) G^ v for one wave vector, s = 2 or 4 components.
+template <typename T, int S>
+__device__ __forceinline__ void apply_dt(typename Cx2<T>::t (&v)[S], T c, T s, T gn, T gx, T gy, T gz, T gm) {
+  using V = typename Cx2<T>::t;
+  // G^ v: gn = n / sin(omega) scaled n~ components (gx, gy, gz), gm = m / sin(omega)
+  V w[S];
+  if (S == 2) {
+    // G^ = [[gz, -gm], [-gm, -gz]] (1D: gz = n sin k / sin omega)
+    w[0].x = gz * v[0].x - gm * v[1].x;
+    w[0].y = gz * v[0].y - gm * v[1].y;
+    w[1].x = -gm * v[0].x - gz * v[1].x;
+    w[1].y = -gm * v[0].y - gz * v[1].y;
+  } else {
+    // sigma.n v for the upper (0,1) and lower (2,3) pairs
+    V su0, su1, sl0, sl1;
+    su0.x = gz * v[0].x + gx * v[1].x + gy * v[1].y;
+    su0.y = gz * v[0].y + gx * v[1].y - gy * v[1].x;
+    su1.x = gx * v[0].x - gy * v[0].y - gz * v[1].x;
+    su1.y = gx * v[0].y + gy * v[0].x - gz * v[1].y;
+    sl0.x = gz * v[2].x + gx * v[3].x + gy * v[3].y;
+    sl0.y = gz * v[2].y + gx * v[3].y - gy * v[3].x;
+    sl1.x = gx * v[2].x - gy * v[2].y - gz * v[3].x;
+    sl1.y = gx * v[2].y + gy * v[2].x - gz * v[3].y;
+    w[0].x = su0.x - gm * v[2].x;
+    w[0].y = su0.y - gm * v[2].y;
+    w[1].x = su1.x - gm * v[3].x;
+    w[1].y = su1.y - gm * v[3].y;
+    w[2].x = -gm * v[0].x - sl0.x;
+    w[2].y = -gm * v[0].y - sl0.y;
+    w[3].x = -gm * v[1].x - sl1.x;
+    w[3].y = -gm * v[1].y - sl1.y;
+  }
+  (void)gn;
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    // cos v - i sin w
+    V r;
+    r.x = c * v[q].x + s * w[q].y;
+    r.y = c * v[q].y - s * w[q].x;
+    v[q] = r;
+  }
+}
+
+// G^ entries for one wave vector in precision T.
+template <typename T>
+__device__ __forceinline__ void ghat(int dim, double k1, double k2, double k3, double n, double m, T& gx, T& gy,
+                                     T& gz, T& gm) {
+  if (sizeof(T) == 8) {
+    double u, nx, ny, nz;
+    symbol64(dim, k1, k2, k3, u, nx, ny, nz);
+    const double sw = sqrt(m * m + n * n * (nx * nx + ny * ny + nz * nz));
+    const double inv = sw > 0.0 ? 1.0 / sw : 0.0;
+    gx = (T)(n * nx * inv);
+    gy = (T)(n * ny * inv);
+    gz = (T)(n * nz * inv);
+    gm = (T)(m * inv);
+  } else {
+    float u, nx, ny, nz;
+    symbol32(dim, (float)k1, (float)k2, (float)k3, u, nx, ny, nz);
+    const float nf = (float)n, mf = (float)m;
+    const float sw = sqrtf(mf * mf + nf * nf * (nx * nx + ny * ny + nz * nz));
+    const float inv = sw > 0.f ? 1.f / sw : 0.f;
+    gx = (T)(nf * nx * inv);
+    gy = (T)(nf * ny * inv);
+    gz = (T)(nf * nz * inv);
+    gm = (T)(mf * inv);
+  }
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void cs_of(double omega, double tt, T& c, T& s) {
+  if (sizeof(T) == 8) {
+    double cd, sd;
+    phase(omega, tt, cd, sd);
+    c = (T)cd;
+    s = (T)sd;
+  } else {
+    float cf, sf;
+    phase32(omega, tt, cf, sf);
+    c = (T)cf;
+    s = (T)sf;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t count, double n, double m,
+                                                     const double* __restrict__ omega, double tt, T scale,
+                                                     typename Cx2<T>::t* __restrict__ data) {
+  using V = typename Cx2<T>::t;
+  const double PI = 3.141592653589793238462643383279;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double k[3], hs;
+    wave_vectors(dim, idx, a, k, hs);
+    if (dim == 1) {
+      V v[2] = {data[idx], data[count + idx]};
+      T c, s, gx, gy, gz, gm;
+      cs_of<T, 2>(omega[idx], tt, c, s);
+      ghat<T>(1, k[0], 0.0, 0.0, n, m, gx, gy, gz, gm);
+      apply_dt<T, 2>(v, c, s, (T)0, gx, gy, gz, gm);
+      data[idx] = make_vec(v[0], scale);
+      data[count + idx] = make_vec(v[1], scale);
+    } else if (dim == 2) {
+      V v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = data[q * count + idx];
+      T c, s, gx, gy, gz, gm;
+      cs_of<T, 4>(omega[idx], tt, c, s);
+      ghat<T>(2, k[0], k[1], 0.0, n, m, gx, gy, gz, gm);
+      apply_dt<T, 4>(v, c, s, (T)0, gx, gy, gz, gm);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) data[q * count + idx] = make_vec(v[q], scale);
+    } else {
+      V p0[4], p1[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        p0[q] = data[q * count + idx];
+        p1[q] = data[(4 + q) * count + idx];
+      }
+      double sa, ca;
+      sincos(hs, &sa, &ca);  // a = exp(i (k1 + k2 + k3)/2)
+      const T ar = (T)ca, ai = (T)sa;
+      V c0[4], c1[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        // a* Psi1
+        V b;
+        b.x = ar * p1[q].x + ai * p1[q].y;
+        b.y = ar * p1[q].y - ai * p1[q].x;
+        c0[q].x = (T)0.5 * (p0[q].x + b.x);
+        c0[q].y = (T)0.5 * (p0[q].y + b.y);
+        c1[q].x = (T)0.5 * (p0[q].x - b.x);
+        c1[q].y = (T)0.5 * (p0[q].y - b.y);
+      }
+      {
+        T c, s, gx, gy, gz, gm;
+        cs_of<T, 4>(omega[2 * idx], tt, c, s);
+        ghat<T>(3, 0.5 * k[0], 0.5 * k[1], 0.5 * k[2], n, m, gx, gy, gz, gm);
+        apply_dt<T, 4>(c0, c, s, (T)0, gx, gy, gz, gm);
+      }
+      {
+        T c, s, gx, gy, gz, gm;
+        cs_of<T, 4>(omega[2 * idx + 1], tt, c, s);
+        ghat<T>(3, 0.5 * k[0] + PI, 0.5 * k[1], 0.5 * k[2], n, m, gx, gy, gz, gm);
+        apply_dt<T, 4>(c1, c, s, (T)0, gx, gy, gz, gm);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        V s0, d, s1;
+        s0.x = c0[q].x + c1[q].x;
+        s0.y = c0[q].y + c1[q].y;
+        d.x = c0[q].x - c1[q].x;
+        d.y = c0[q].y - c1[q].y;
+        s1.x = ar * d.x - ai * d.y;
+        s1.y = ar * d.y + ai * d.x;
+        data[q * count + idx] = make_vec(s0, scale);
+        data[(4 + q) * count + idx] = make_vec(s1, scale);
+      }
+    }
+  }
+}
+
+// Particle weight: sum |c|^2 and sum c^dag G^ c over every wave vector.
+template <typename T>
+__global__ void __launch_bounds__(256) weights_kernel(int dim, AxesDev a, int64_t count, double n, double m,
+                                                      const typename Cx2<T>::t* __restrict__ data,
+                                                      double* __restrict__ partials) {
+  using V = typename Cx2<T>::t;
+  const double PI = 3.141592653589793238462643383279;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double k[3], hs;
+    wave_vectors(dim, idx, a, k, hs);
+    const int S = dim == 1 ? 2 : 4;
+    const int nq = dim == 3 ? 2 : 1;
+    V vq[2][4];
+    if (dim == 3) {
+      double sa, ca;
+      sincos(hs, &sa, &ca);
+      const T ar = (T)ca, ai = (T)sa;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const V p0 = data[q * count + idx], p1 = data[(4 + q) * count + idx];
+        V b;
+        b.x = ar * p1.x + ai * p1.y;
+        b.y = ar * p1.y - ai * p1.x;
+        vq[0][q].x = p0.x + b.x;
+        vq[0][q].y = p0.y + b.y;
+        vq[1][q].x = p0.x - b.x;
+        vq[1][q].y = p0.y - b.y;
+      }
+    } else {
+      for (int q = 0; q < S; ++q) vq[0][q] = data[q * count + idx];
+    }
+    for (int j = 0; j < nq; ++j) {
+      T gx, gy, gz, gm;
+      if (dim == 3)
+        ghat<T>(3, 0.5 * k[0] + (j ? PI : 0.0), 0.5 * k[1], 0.5 * k[2], n, m, gx, gy, gz, gm);
+      else
+        ghat<T>(dim, k[0], k[1], 0.0, n, m, gx, gy, gz, gm);
+      // cos = 1, sin = 1 turns apply_dt into v - i G^ v; recover G^ v from it
+      T nrm = 0, gdot = 0;
+      if (S == 2) {
+        V v[2] = {vq[j][0], vq[j][1]};
+        V w[2] = {v[0], v[1]};
+        apply_dt<T, 2>(w, (T)0, (T)1, (T)0, gx, gy, gz, gm);  // w = -i G^ v
+        for (int q = 0; q < 2; ++q) {
+          nrm += v[q].x * v[q].x + v[q].y * v[q].y;
+          // v^dag (G^ v) = v^dag (i w)
+          gdot += -(v[q].x * w[q].y - v[q].y * w[q].x);
+        }
+      } else {
+        V v[4] = {vq[j][0], vq[j][1], vq[j][2], vq[j][3]};
+        V w[4] = {v[0], v[1], v[2], v[3]};
+        apply_dt<T, 4>(w, (T)0, (T)1, (T)0, gx, gy, gz, gm);
+        for (int q = 0; q < 4; ++q) {
+          nrm += v[q].x * v[q].x + v[q].y * v[q].y;
+          gdot += -(v[q].x * w[q].y - v[q].y * w[q].x);
+        }
+      }
+      acc[0] += (double)nrm;
+      acc[1] += (double)gdot;
+    }
+  }
+  block_sum<2, 256>(acc);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = acc[0];
+    partials[2 * blockIdx.x + 1] = acc[1];
+  }
+}
+
+__global__ void fold2_kernel(const double* __restrict__ partials, int nblk, double* __restrict__ result) {
+  double acc[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    acc[0] += partials[2 * b];
+    acc[1] += partials[2 * b + 1];
+  }
+  block_sum<2, 256>(acc);
+  if (threadIdx.x == 0) {
+    result[0] = acc[0];
+    result[1] = acc[1];
+  }
+}
+
+static int64_t kcount(const Geometry& g) { return g.vol; }
+
+static unsigned grid_for(int64_t count) {
+  int64_t b = (count + 255) / 256;
+  if (b > 4 * 152 * 8) b = 4 * 152 * 8;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,
+                             cudaStream_t st) {
+  omega_kernel<<<grid_for(kcount(g)), 256, 0, st>>>(g.dim, to_dev(ax), kcount(g), n, m, omega);
+  QW_CHECK_LAUNCH("omega table launch");
+  return QW_OK;
+}
+
+qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
+                                  const double* omega, int64_t t, void* psi_hat, cudaStream_t st) {
+  const int64_t count = kcount(g);
+  const double inv = 1.0 / (double)g.vol;
+  if (dt == QW_C64)
+    evolve_kernel<float><<<grid_for(count), 256, 0, st>>>(g.dim, to_dev(ax), count, n, m, omega, (double)t,
+                                                         (float)inv, static_cast<float2*>(psi_hat));
+  else
+    evolve_kernel<double><<<grid_for(count), 256, 0, st>>>(g.dim, to_dev(ax), count, n, m, omega, (double)t, inv,
+                                                          static_cast<double2*>(psi_hat));
+  QW_CHECK_LAUNCH("evolve launch");
+  return QW_OK;
+}
+
+qw_status launch_particle_weights(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
+                                  const void* psi_hat, double* partials, double* result, cudaStream_t st) {
+  const int64_t count = kcount(g);
+  const int nblk = kObsBlocks;
+  if (dt == QW_C64)
+    weights_kernel<float><<<nblk, 256, 0, st>>>(g.dim, to_dev(ax), count, n, m,
+                                                static_cast<const float2*>(psi_hat), partials);
+  else
+    weights_kernel<double><<<nblk, 256, 0, st>>>(g.dim, to_dev(ax), count, n, m,
+                                                 static_cast<const double2*>(psi_hat), partials);
+  QW_CHECK_LAUNCH("weights launch");
+  fold2_kernel<<<1, 256, 0, st>>>(partials, nblk, result);
+  QW_CHECK_LAUNCH("fold launch");
+  return QW_OK;
+}
+
+}  // namespace qw
