@@ -154,6 +154,27 @@ qw_status qw_sync(qw_plan plan, void* stream);
  * Errors: QW_EINVAL, QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
 qw_status qw_observables(qw_plan plan, const void* psi_dev, qw_obs* out, void* stream);
 
+/* qw_step without any device allocation, for callers that cannot call
+ * cudaMalloc where they step a walk: code whose device memory is owned and
+ * budgeted by another allocator (for example a framework's caching pool that
+ * already holds the GPU), or a latency-critical loop that must not pay for
+ * cudaMalloc's implicit device synchronisation.  The paper has no counterpart;
+ * this is a library-interface variant of qw_step.
+ * Same update and arguments as qw_plan_create + qw_step (dim, N, mass, dtype,
+ * psi_dev of qw_plan_field_elems elements, nsteps >= 0, stream), but the
+ * ping-pong partner field is a file-scope static device array of 64 MiB that
+ * every GPU loading libqw.so holds until the process exits; the kernel is the
+ * VEC variant where it applies, else PLAIN (never the TMA variant).
+ * The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.
+ * All calls on a device share the one array, and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.
+ * Errors: QW_EINVAL (bad arguments, or a field larger than 64 MiB -- use a
+ * plan for those), QW_ECUDA. */
+qw_status qw_step_static(int dim, int64_t N, double mass, qw_dtype dtype, void* psi_dev, int64_t nsteps,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

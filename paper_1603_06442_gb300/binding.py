@@ -51,6 +51,8 @@ _SIGS = {
     "qw_plan_get_stencil": (ctypes.c_int, [ctypes.c_void_p]),
     "qw_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "qw_plan_prepare_spectral": (ctypes.c_int, [ctypes.c_void_p]),
+    "qw_step_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.c_void_p]),
     "qw_evolve_spectral": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "qw_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(qw_obs),
                                       ctypes.c_void_p]),
@@ -143,6 +145,11 @@ def qw_plan_prepare_spectral(plan):
 
 def qw_evolve_spectral(plan, psi, t, stream=None):
     _check(load().qw_evolve_spectral(plan, _ptr(psi), int(t), _stream(stream)))
+
+
+def qw_step_static(dim, N, mass, dtype, psi, nsteps, stream=None):
+    dt = QW_C64 if dtype in ("c64", QW_C64) else QW_C128
+    _check(load().qw_step_static(int(dim), int(N), float(mass), dt, _ptr(psi), int(nsteps), _stream(stream)))
 
 
 def qw_sync(plan, stream=None):
