@@ -2,11 +2,13 @@
 
 Default workload: the BCC box N = 512 (33,554,432 sites, 1.07 GB complex64 field,
 larger than L2), m = 0.1, a Gaussian packet of width 32 sites.  One bench step =
-S stencil steps of the walk (qw_step, complex64) followed by the observables
-reduction (qw_observables, FP64 accumulation).  `value` = site-steps/s over the
+S = 100 stencil steps of the walk (qw_step, complex64) followed by the
+observables (qw_observables: norm and <x> in position space, particle weights
+through a forward DFT; FP64 accumulation).  `value` = site-steps/s over the
 timed steps; the roofline object reports the stencil kernel's achieved HBM
 bandwidth (algorithmic bytes: one read + one write of the field per launch)
-against the measured copy bandwidth.
+against the measured copy bandwidth.  The spectral form (qw_evolve_spectral)
+and the FP64 plain form are timed on the same box and reported in "extra".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -31,7 +33,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = {"name": "bcc_N512_stencil_c64", "dim": 3, "N": 512, "mass": 0.1, "sigma": 32.0,
-            "k0": (0.3, 0.2, 0.1), "substeps": 20}
+            "k0": (0.3, 0.2, 0.1), "substeps": 100}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -221,7 +223,8 @@ def run_ours(args, rank, world, local):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     value = sites * S * args.steps * world / (ms / 1e3)
-    launches_per_step = S + (1 if S % 2 else 0) + 2
+    # stencil launches (+ a final copy for odd S) + moments/fold + copy + 3 FFT passes + weights/fold
+    launches_per_step = S + 2 + 3 + 2
 
     # end-to-end through the public API with host buffers: H2D of the field,
     # S steps, observables read back to the host, every step.
@@ -315,7 +318,29 @@ def extra_measurements(qb, dev, stream):
         variants[name] = {"ms_per_step": ms, "site_steps_per_s": plan.sites / (ms / 1e3),
                           "hbm_GBps": 2 * plan.elems * 8 / (ms / 1e3) / 1e9}
     out["c64_stencil_variants"] = variants
-    plan.close()
+    # spectral form on the same box: the cost must not depend on t
+    spec = {}
+    for dt, tag in (("c64", "c64"), ("c128", "c128")):
+        plan = qb.Plan(3, W["N"], W["mass"], dt)
+        plan.prepare_spectral()
+        psi = torch.zeros(plan.elems, dtype=plan.torch_dtype, device=dev)
+        psi[::5] = 1e-3
+        for t in ((10 ** 4, 10 ** 6) if dt == "c64" else (10 ** 4,)):
+            plan.evolve_spectral(psi, t, stream)
+            torch.cuda.synchronize(dev)
+            reps = 5
+            s0.record(stream)
+            for _ in range(reps):
+                plan.evolve_spectral(psi, t, stream)
+            s1.record(stream)
+            plan.sync(stream)
+            ms = s0.elapsed_time(s1) / reps
+            bytes_min = 4 * plan.elems * (8 if dt == "c64" else 16)   # read+write field, forward and inverse
+            spec["%s_t%d" % (tag, t)] = {"ms_per_evolution": ms, "t": t,
+                                         "equivalent_site_steps_per_s": plan.sites * t / (ms / 1e3),
+                                         "effective_GBps_vs_4_field_passes": bytes_min / (ms / 1e3) / 1e9}
+        plan.close()
+    out["spectral"] = spec
     return out
 
 

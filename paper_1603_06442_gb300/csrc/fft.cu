@@ -272,6 +272,198 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __rest
   }
 }
 
+// ------------------------------------------------- two-factor register kernel
+// Lines of length L = R1 * R2 (R1, R2 in 4, 8, 16): n = n1 + R1 n2,
+//   Y[n1][k2] = omega_L^{n1 k2} sum_{n2} x[n1 + R1 n2] omega_{R2}^{n2 k2}   (step A, registers)
+//   X[k2 + R2 k1] = sum_{n1} Y[n1][k2] omega_{R1}^{n1 k1}                   (step B, registers)
+// with one shared-memory exchange between the steps; index maps are
+// compile-time, so the per-element cost is the butterflies, not the indexing.
+template <int R, bool INV, typename T, typename V> struct RegDFT;
+template <bool INV, typename T, typename V> struct RegDFT<2, INV, T, V> {
+  __device__ __forceinline__ static void run(V (&a)[2]) { dft2<INV>(a[0], a[1]); }
+};
+template <bool INV, typename T, typename V> struct RegDFT<4, INV, T, V> {
+  __device__ __forceinline__ static void run(V (&a)[4]) { dft4<INV>(a[0], a[1], a[2], a[3]); }
+};
+template <bool INV, typename T, typename V> struct RegDFT<8, INV, T, V> {
+  __device__ __forceinline__ static void run(V (&a)[8]) { dft8<INV, T>(a); }
+};
+template <bool INV, typename T, typename V> struct RegDFT<16, INV, T, V> {
+  __device__ __forceinline__ static void run(V (&a)[16]) {
+    // even / odd halves, then X_k = E_k + w16^k O_k, X_{k+8} = E_k - w16^k O_k
+    V e[8], o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      e[j] = a[2 * j];
+      o[j] = a[2 * j + 1];
+    }
+    dft8<INV, T>(e);
+    dft8<INV, T>(o);
+    const T cs[8] = {(T)1.0, (T)0.92387953251128675613, (T)0.70710678118654752440, (T)0.38268343236508977173,
+                     (T)0.0, (T)-0.38268343236508977173, (T)-0.70710678118654752440, (T)-0.92387953251128675613};
+    const T sn[8] = {(T)0.0, (T)0.38268343236508977173, (T)0.70710678118654752440, (T)0.92387953251128675613,
+                     (T)1.0, (T)0.92387953251128675613, (T)0.70710678118654752440, (T)0.38268343236508977173};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      V w;  // w16^k = cos - i sin (forward), cos + i sin (inverse)
+      w.x = cs[k];
+      w.y = INV ? sn[k] : -sn[k];
+      const V t = (k == 0) ? o[0] : cmul(o[k], w);
+      a[k] = cadd(e[k], t);
+      a[k + 8] = csub(e[k], t);
+    }
+  }
+};
+
+template <typename T, bool INV, int R1, int R2, bool CONTIG>
+__global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restrict__ data, FftPass p,
+                                                    const typename Cx<T>::t* __restrict__ tw_line,
+                                                    const typename Cx<T>::t* __restrict__ tw_hi,
+                                                    const typename Cx<T>::t* __restrict__ tw_lo) {
+  using V = typename Cx<T>::t;
+  constexpr int L = R1 * R2;
+  constexpr int TPL = R1 > R2 ? R1 : R2;  // threads per line
+  constexpr int C = 256 / TPL;            // lines per CTA
+  constexpr int CP = C + 1;               // padded line-minor pitch
+  extern __shared__ __align__(16) unsigned char f2_smem[];
+  V* sm = reinterpret_cast<V*>(f2_smem);
+  const int tid = threadIdx.x;
+  const int64_t S = p.S;
+  const int64_t nlines = p.O * S;
+  const int64_t l0 = (int64_t)blockIdx.x * C;
+  const int c = tid % C, r = tid / C;
+  const int64_t l = l0 + c;
+  const bool live = l < nlines;
+  int64_t base = 0, tw_b = 0;
+  if (live) {
+    const int64_t o = l / S, i = l - o * S;
+    base = o * (int64_t)L * S + i;
+    tw_b = i / p.tw_div;
+  }
+  // ---- load into shared memory, element n of line c at sm[c + CP n]
+  if (CONTIG) {  // S == 1: the CTA's lines are one contiguous run
+#pragma unroll 4
+    for (int e = tid; e < C * L; e += 256) {
+      const int cc = e / L, n = e - cc * L;
+      const int64_t ll = l0 + cc;
+      V v;
+      v.x = 0;
+      v.y = 0;
+      if (ll < nlines) v = data[ll * L + n];
+      sm[cc + CP * n] = v;
+    }
+  } else {
+#pragma unroll 4
+    for (int n = r; n < L; n += TPL) {
+      V v;
+      v.x = 0;
+      v.y = 0;
+      if (live) {
+        v = data[base + (int64_t)n * S];
+        if (INV && p.twiddle) v = cmulc(v, twiddle_big(tw_hi, tw_lo, (int64_t)n * tw_b, p.tlo_bits));
+      }
+      sm[c + CP * n] = v;
+    }
+  }
+  __syncthreads();
+  // ---- step A: thread r = n1 < R1
+  V a[R2];
+  if (r < R1) {
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) a[n2] = sm[c + CP * (r + R1 * n2)];
+    RegDFT<R2, INV, T, V>::run(a);
+#pragma unroll
+    for (int k2 = 1; k2 < R2; ++k2) {
+      const V w = tw_line[r * k2];  // omega_L^{n1 k2}
+      a[k2] = INV ? cmulc(a[k2], w) : cmul(a[k2], w);
+    }
+  }
+  __syncthreads();
+  if (r < R1) {
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) sm[c + CP * (r * R2 + k2)] = a[k2];
+  }
+  __syncthreads();
+  // ---- step B: thread r = k2 < R2
+  V b[R1];
+  if (r < R2) {
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) b[n1] = sm[c + CP * (n1 * R2 + r)];
+    RegDFT<R1, INV, T, V>::run(b);
+  }
+  __syncthreads();
+  if (r < R2) {
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) sm[c + CP * (r + R2 * k1)] = b[k1];
+  }
+  __syncthreads();
+  // ---- store
+  if (CONTIG) {
+#pragma unroll 4
+    for (int e = tid; e < C * L; e += 256) {
+      const int cc = e / L, n = e - cc * L;
+      const int64_t ll = l0 + cc;
+      if (ll < nlines) data[ll * L + n] = sm[cc + CP * n];
+    }
+  } else {
+#pragma unroll 4
+    for (int n = r; n < L; n += TPL) {
+      if (!live) break;
+      V v = sm[c + CP * n];
+      if (!INV && p.twiddle) v = cmul(v, twiddle_big(tw_hi, tw_lo, (int64_t)n * tw_b, p.tlo_bits));
+      data[base + (int64_t)n * S] = v;
+    }
+  }
+}
+
+template <typename T, bool INV, int R1, int R2>
+static qw_status launch_2f(const FftPass& p, void* data, cudaStream_t st) {
+  using V = typename Cx<T>::t;
+  constexpr int L = R1 * R2, TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
+  const size_t smem = (size_t)L * (C + 1) * sizeof(V);
+  static bool attr[2] = {false, false};
+  const int64_t nlines = p.O * p.S;
+  const int64_t grid = (nlines + C - 1) / C;
+  if (grid > 0x7fffffff) {
+    set_error("FFT grid too large");
+    return QW_EINVAL;
+  }
+  if (p.S == 1) {
+    if (!attr[0]) {
+      QW_CHECK_CUDA(cudaFuncSetAttribute(fft2f_kernel<T, INV, R1, R2, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr[0] = true;
+    }
+    fft2f_kernel<T, INV, R1, R2, true><<<(unsigned)grid, 256, smem, st>>>(
+        static_cast<V*>(data), p, static_cast<const V*>(p.tw_line), static_cast<const V*>(p.tw_hi),
+        static_cast<const V*>(p.tw_lo));
+  } else {
+    if (!attr[1]) {
+      QW_CHECK_CUDA(cudaFuncSetAttribute(fft2f_kernel<T, INV, R1, R2, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr[1] = true;
+    }
+    fft2f_kernel<T, INV, R1, R2, false><<<(unsigned)grid, 256, smem, st>>>(
+        static_cast<V*>(data), p, static_cast<const V*>(p.tw_line), static_cast<const V*>(p.tw_hi),
+        static_cast<const V*>(p.tw_lo));
+  }
+  QW_CHECK_LAUNCH("fft two-factor pass launch");
+  return QW_OK;
+}
+
+// Lengths with a two-factor register kernel; returns false for the generic path.
+template <typename T, bool INV>
+static bool run_2f(const FftPass& p, void* data, cudaStream_t st, qw_status* out) {
+  switch (p.L) {
+    case 16: *out = launch_2f<T, INV, 4, 4>(p, data, st); return true;
+    case 32: *out = launch_2f<T, INV, 8, 4>(p, data, st); return true;
+    case 64: *out = launch_2f<T, INV, 8, 8>(p, data, st); return true;
+    case 128: *out = launch_2f<T, INV, 16, 8>(p, data, st); return true;
+    case 256: *out = launch_2f<T, INV, 16, 16>(p, data, st); return true;
+    default: return false;
+  }
+}
+
 // ---------------------------------------------------------------- planning
 static bool radix_plan(int L, int* radix, int* n) {
   int k = 0;
@@ -344,14 +536,17 @@ static qw_status build_pass(FftPass* p, int L, int64_t S, int64_t O, int64_t tw_
     return QW_EINVAL;
   }
   const int esz = (int)sizeof(typename Cx<T>::t);
-  const int budget = kFftSmemBytes / (2 * esz);  // elements per ping-pong buffer
-  int C = budget / L;
-  C = C > 16 ? 16 : (C < 1 ? 1 : C);
-  int64_t nlines = O * S;
-  if (C > nlines) C = (int)nlines;
+  // widest tile (<= 16 lines) whose two padded buffers fit the shared-memory budget
+  const int64_t nlines = O * S;
+  int C = 16;
+  while (C > 1 && (C > nlines || 2 * (size_t)L * ((C % 2 == 0) ? C + 1 : C) * esz > (size_t)kFftSmemBytes)) --C;
   p->C = C;
   p->pitch = (C % 2 == 0) ? C + 1 : C;
   p->smem = 2 * (size_t)L * p->pitch * esz;
+  if (p->smem > (size_t)kFftSmemBytes) {
+    set_error("FFT line of %d elements does not fit shared memory", L);
+    return QW_EINVAL;
+  }
   p->twiddle = twiddle ? 1 : 0;
   p->tw_N = tw_N;
   p->tw_div = tw_div;
@@ -436,6 +631,8 @@ void fft_plan_destroy(FftPlan* f) {
 template <typename T, bool INV>
 static qw_status run_pass(const FftPass& p, void* data, cudaStream_t st) {
   using V = typename Cx<T>::t;
+  qw_status s2;
+  if (run_2f<T, INV>(p, data, st, &s2)) return s2;
   static bool attr[2] = {false, false};
   if (!attr[INV]) {
     QW_CHECK_CUDA(cudaFuncSetAttribute(fft_pass_kernel<T, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,

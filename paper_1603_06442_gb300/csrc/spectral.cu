@@ -146,26 +146,52 @@ __device__ __forceinline__ void symbol32(int dim, float k1, float k2, float k3, 
   }
 }
 
-// Wave vectors of storage index idx: 1D/2D one vector, BCC two (q0, q1).
-__device__ __forceinline__ void wave_vectors(int dim, int64_t idx, const AxesDev& a, double (&k)[3],
-                                             double& half_sum) {
+// Wave vector(s) of storage position (x, y, z): k_j = 2 pi f_j / len_j with f the
+// frequency index of the position; fsum = fx + fy + fz (BCC coset phase).
+__device__ __forceinline__ void wave_vectors(int dim, int64_t x, int64_t y, int64_t z, const AxesDev& a,
+                                             double (&k)[3], int64_t& fsum) {
   const double TWO_PI = 6.283185307179586476925286766559;
-  const int64_t nx = a.len[0], ny = a.len[1];
-  const int64_t x = idx % nx, y = (idx / nx) % ny, z = idx / (nx * ny);
   const int64_t fx = freq_of(x, a, 0);
   const int64_t fy = dim >= 2 ? freq_of(y, a, 1) : 0;
   const int64_t fz = dim >= 3 ? freq_of(z, a, 2) : 0;
-  k[0] = TWO_PI * (double)fx / (double)nx;
-  k[1] = dim >= 2 ? TWO_PI * (double)fy / (double)ny : 0.0;
+  k[0] = TWO_PI * (double)fx / (double)a.len[0];
+  k[1] = dim >= 2 ? TWO_PI * (double)fy / (double)a.len[1] : 0.0;
   k[2] = dim >= 3 ? TWO_PI * (double)fz / (double)a.len[2] : 0.0;
-  half_sum = 0.5 * (k[0] + k[1] + k[2]);
+  fsum = fx + fy + fz;
+}
+
+// a = exp(i (k1 + k2 + k3)/2) = exp(i pi fsum / M) on the cubic coset grid.
+template <typename T>
+__device__ __forceinline__ void coset_phase(int64_t fsum, int64_t M, T& ar, T& ai) {
+  const int64_t q = fsum % (2 * M);
+  if (sizeof(T) == 8) {
+    double s, c;
+    sincospi((double)q / (double)M, &s, &c);
+    ar = (T)c;
+    ai = (T)s;
+  } else {
+    float s, c;
+    sincospif((float)q / (float)M, &s, &c);
+    ar = (T)c;
+    ai = (T)s;
+  }
+}
+
+// Position of the thread in a 3D launch over (nx, ny, nz); false when outside.
+__device__ __forceinline__ bool grid_pos(const AxesDev& a, int64_t& x, int64_t& y, int64_t& z) {
+  x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  y = blockIdx.y;
+  z = blockIdx.z;
+  return x < a.len[0];
 }
 
 __global__ void omega_kernel(int dim, AxesDev a, int64_t count, double n, double m, double* __restrict__ omega) {
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    double k[3], hs;
-    wave_vectors(dim, idx, a, k, hs);
+  int64_t x, y, z;
+  if (grid_pos(a, x, y, z)) {
+    const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
+    double k[3];
+    int64_t fs;
+    wave_vectors(dim, x, y, z, a, k, fs);
     const int nq = dim == 3 ? 2 : 1;
     for (int q = 0; q < nq; ++q) {
       double k1 = k[0], k2 = k[1], k3 = k[2];
@@ -294,10 +320,12 @@ __global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t
                                                      typename Cx2<T>::t* __restrict__ data) {
   using V = typename Cx2<T>::t;
   const double PI = 3.141592653589793238462643383279;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    double k[3], hs;
-    wave_vectors(dim, idx, a, k, hs);
+  int64_t x, y, z;
+  if (grid_pos(a, x, y, z)) {
+    const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
+    double k[3];
+    int64_t fs;
+    wave_vectors(dim, x, y, z, a, k, fs);
     if (dim == 1) {
       V v[2] = {data[idx], data[count + idx]};
       T c, s, gx, gy, gz, gm;
@@ -323,9 +351,8 @@ __global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t
         p0[q] = data[q * count + idx];
         p1[q] = data[(4 + q) * count + idx];
       }
-      double sa, ca;
-      sincos(hs, &sa, &ca);  // a = exp(i (k1 + k2 + k3)/2)
-      const T ar = (T)ca, ai = (T)sa;
+      T ar, ai;
+      coset_phase<T>(fs, a.len[0], ar, ai);  // a = exp(i (k1 + k2 + k3)/2)
       V c0[4], c1[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -374,17 +401,19 @@ __global__ void __launch_bounds__(256) weights_kernel(int dim, AxesDev a, int64_
   using V = typename Cx2<T>::t;
   const double PI = 3.141592653589793238462643383279;
   double acc[2] = {0.0, 0.0};
+  const int64_t nx = a.len[0], ny = a.len[1];
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    double k[3], hs;
-    wave_vectors(dim, idx, a, k, hs);
+    const int64_t x = idx % nx, y = (idx / nx) % ny, z = idx / (nx * ny);
+    double k[3];
+    int64_t fs;
+    wave_vectors(dim, x, y, z, a, k, fs);
     const int S = dim == 1 ? 2 : 4;
     const int nq = dim == 3 ? 2 : 1;
     V vq[2][4];
     if (dim == 3) {
-      double sa, ca;
-      sincos(hs, &sa, &ca);
-      const T ar = (T)ca, ai = (T)sa;
+      T ar, ai;
+      coset_phase<T>(fs, nx, ar, ai);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const V p0 = data[q * count + idx], p1 = data[(4 + q) * count + idx];
@@ -451,15 +480,14 @@ __global__ void fold2_kernel(const double* __restrict__ partials, int nblk, doub
 
 static int64_t kcount(const Geometry& g) { return g.vol; }
 
-static unsigned grid_for(int64_t count) {
-  int64_t b = (count + 255) / 256;
-  if (b > 4 * 152 * 8) b = 4 * 152 * 8;
-  return (unsigned)(b < 1 ? 1 : b);
+
+static dim3 grid3(const Geometry& g) {
+  return dim3((unsigned)((g.nx + 255) / 256), (unsigned)g.ny, (unsigned)g.nz);
 }
 
 qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,
                              cudaStream_t st) {
-  omega_kernel<<<grid_for(kcount(g)), 256, 0, st>>>(g.dim, to_dev(ax), kcount(g), n, m, omega);
+  omega_kernel<<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), kcount(g), n, m, omega);
   QW_CHECK_LAUNCH("omega table launch");
   return QW_OK;
 }
@@ -469,10 +497,10 @@ qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtyp
   const int64_t count = kcount(g);
   const double inv = 1.0 / (double)g.vol;
   if (dt == QW_C64)
-    evolve_kernel<float><<<grid_for(count), 256, 0, st>>>(g.dim, to_dev(ax), count, n, m, omega, (double)t,
+    evolve_kernel<float><<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), count, n, m, omega, (double)t,
                                                          (float)inv, static_cast<float2*>(psi_hat));
   else
-    evolve_kernel<double><<<grid_for(count), 256, 0, st>>>(g.dim, to_dev(ax), count, n, m, omega, (double)t, inv,
+    evolve_kernel<double><<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), count, n, m, omega, (double)t, inv,
                                                           static_cast<double2*>(psi_hat));
   QW_CHECK_LAUNCH("evolve launch");
   return QW_OK;

@@ -91,6 +91,23 @@ def test_spectral_long_chain_multipass(qb, dtype, N):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("dim,N", [(3, 512), (2, 1024), (1, 4096)])
+def test_spectral_large_boxes_vs_stencil(qb, dtype, dim, N):
+    """Largest single-pass lines (FFT tiles at the shared-memory limit): spectral t = 4 equals 4 steps."""
+    m, t = 0.2, 4
+    a = inputs.random_field(dim, N, seed=N)
+    plan = qb.Plan(dim, N, m, dtype)
+    x1, x2 = to_dev(a, dtype), to_dev(a, dtype)
+    plan.set_stencil("plain")
+    plan.step(x1, t)
+    plan.evolve_spectral(x2, t)
+    plan.sync()
+    e = rel_l2(x2.cpu().numpy(), x1.cpu().numpy())
+    plan.close()
+    assert e <= TOL[dtype], e
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_spectral_matches_stencil_on_gpu(qb, dtype):
     for dim, N, t in ((1, 512, 300), (2, 64, 50), (3, 128, 40)):
         m = 0.07
