@@ -154,6 +154,54 @@ qw_status qw_sync(qw_plan plan, void* stream);
  * Errors: QW_EINVAL, QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
 qw_status qw_observables(qw_plan plan, const void* psi_dev, qw_obs* out, void* stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent walks of uneven size advanced together by one persistent
+ * kernel launch, replayed from a CUDA graph (complex64 only).  Each walk is the
+ * update rule (Eq. upd-rule) applied t times to its own field, exactly as
+ * qw_step with the PLAIN kernel would. */
+typedef struct {
+  int dim;          /* 1, 2 or 3 */
+  int64_t N;        /* box side (even for dim 3) */
+  double mass;      /* m in [0, 1] */
+  int64_t t;        /* steps per qw_batch_run, 0 <= t < 2^30 */
+  void* psi_dev;    /* the walk's complex64 field (device layout), caller-owned */
+} qw_walk;
+
+typedef struct qw_batch_s* qw_batch;
+
+/* Create a batch over n walks (descriptors copied).  Allocates a partner
+ * field per walk, the schedule tables and counters on the current device.
+ * Errors: QW_EINVAL (bad descriptor), QW_ENOMEM, QW_ECUDA. */
+qw_status qw_batch_create(const qw_walk* walks, int n, qw_batch* out);
+qw_status qw_batch_destroy(qw_batch batch);
+
+/* Tile size (sites per work item) and the L2 share a group of walks may
+ * occupy (two buffers per walk); rebuilds the schedule.  Errors: QW_EINVAL. */
+qw_status qw_batch_set_tiling(qw_batch batch, int64_t tile_sites, int64_t l2_budget_bytes);
+qw_status qw_batch_get_tiling(qw_batch batch, int64_t* tile_sites, int64_t* l2_budget_bytes, int64_t* items);
+
+/* Autotuner: times the batch kernel for every tile size in {1K, 2K, 4K, 8K,
+ * 16K} sites and L2 share in {24, 48, 96} MiB on stand-in fields of the same
+ * sizes (zero-filled scratch, allocated and freed here; the walks' fields are
+ * not touched), with every walk's step count capped at rounds_cap, and keeps
+ * the fastest setting.  Optional outputs: chosen tile, budget and the measured
+ * site-steps/s.  Synchronous.  Errors: QW_EINVAL, QW_ENOMEM, QW_ECUDA. */
+qw_status qw_batch_autotune(qw_batch batch, int64_t rounds_cap, void* stream, int64_t* best_tile,
+                            int64_t* best_budget, double* best_rate);
+
+/* Advance every walk by its t steps, in place, in one persistent launch
+ * (captured into a CUDA graph on the first call, replayed afterwards).
+ * Asynchronous on `stream`.  Dependency waits inside the kernel are bounded;
+ * a wait that gives up is reported by qw_batch_sync.  Errors: QW_EINVAL, QW_ECUDA. */
+qw_status qw_batch_run(qw_batch batch, void* stream);
+
+/* Wait for the batch's work on `stream`; QW_ETIMEOUT if a dependency wait gave up. */
+qw_status qw_batch_sync(qw_batch batch, void* stream);
+
+/* Norm and <x> of every walk (out[i] for walk i, original order); particle
+ * weights are NaN here (use a plan's qw_observables).  Synchronous. */
+qw_status qw_batch_observables(qw_batch batch, qw_obs* out, void* stream);
+
 /* qw_step without any device allocation, for callers that cannot call
  * cudaMalloc where they step a walk: code whose device memory is owned and
  * budgeted by another allocator (for example a framework's caching pool that

@@ -35,6 +35,11 @@ class qw_obs(ctypes.Structure):
                 "w_antiparticle": self.w_antiparticle}
 
 
+class qw_walk(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("N", ctypes.c_int64), ("mass", ctypes.c_double), ("t", ctypes.c_int64),
+                ("psi_dev", ctypes.c_void_p)]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -51,6 +56,17 @@ _SIGS = {
     "qw_plan_get_stencil": (ctypes.c_int, [ctypes.c_void_p]),
     "qw_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "qw_plan_prepare_spectral": (ctypes.c_int, [ctypes.c_void_p]),
+    "qw_batch_create": (ctypes.c_int, [ctypes.POINTER(qw_walk), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "qw_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "qw_batch_set_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
+    "qw_batch_get_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "qw_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "qw_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_double)]),
+    "qw_batch_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "qw_batch_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qw_obs), ctypes.c_void_p]),
     "qw_step_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_void_p]),
     "qw_evolve_spectral": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -160,6 +176,88 @@ def qw_observables(plan, psi, stream=None):
     out = qw_obs()
     _check(load().qw_observables(plan, _ptr(psi), ctypes.byref(out), _stream(stream)))
     return out.as_dict()
+
+
+def qw_batch_create(walks):
+    """walks: list of (dim, N, mass, t, field tensor or device address)."""
+    arr = (qw_walk * len(walks))()
+    for i, (dim, N, mass, t, psi) in enumerate(walks):
+        arr[i] = qw_walk(int(dim), int(N), float(mass), int(t), _ptr(psi))
+    h = ctypes.c_void_p()
+    _check(load().qw_batch_create(arr, len(walks), ctypes.byref(h)))
+    return h.value
+
+
+def qw_batch_destroy(batch):
+    _check(load().qw_batch_destroy(batch))
+
+
+def qw_batch_set_tiling(batch, tile_sites, l2_budget_bytes):
+    _check(load().qw_batch_set_tiling(batch, int(tile_sites), int(l2_budget_bytes)))
+
+
+def qw_batch_get_tiling(batch):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().qw_batch_get_tiling(batch, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def qw_batch_run(batch, stream=None):
+    _check(load().qw_batch_run(batch, _stream(stream)))
+
+
+def qw_batch_autotune(batch, rounds_cap=32, stream=None):
+    a, b, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(load().qw_batch_autotune(batch, int(rounds_cap), _stream(stream), ctypes.byref(a), ctypes.byref(b),
+                                    ctypes.byref(r)))
+    return a.value, b.value, r.value
+
+
+def qw_batch_sync(batch, stream=None):
+    _check(load().qw_batch_sync(batch, _stream(stream)))
+
+
+def qw_batch_observables(batch, n, stream=None):
+    out = (qw_obs * n)()
+    _check(load().qw_batch_observables(batch, out, _stream(stream)))
+    return [o.as_dict() for o in out]
+
+
+class Batch:
+    """Owning wrapper of a qw_batch over (dim, N, mass, t, field) walks (complex64)."""
+
+    def __init__(self, walks):
+        self.walks = list(walks)
+        self.handle = qw_batch_create(self.walks)
+
+    def run(self, stream=None):
+        qw_batch_run(self.handle, stream)
+
+    def sync(self, stream=None):
+        qw_batch_sync(self.handle, stream)
+
+    def autotune(self, rounds_cap=32, stream=None):
+        return qw_batch_autotune(self.handle, rounds_cap, stream)
+
+    def set_tiling(self, tile_sites, l2_budget_bytes):
+        qw_batch_set_tiling(self.handle, tile_sites, l2_budget_bytes)
+
+    def tiling(self):
+        return qw_batch_get_tiling(self.handle)
+
+    def observables(self, stream=None):
+        return qw_batch_observables(self.handle, len(self.walks), stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            qw_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

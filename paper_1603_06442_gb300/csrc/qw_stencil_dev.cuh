@@ -1,0 +1,165 @@
+// Per-site update of the Dirac walk shared by the plain and batched stencil
+// kernels (derivation of the transition matrices at the top of stencil.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qw_internal.cuh"
+
+namespace qw {
+
+template <typename R> struct CplxOf;
+template <> struct CplxOf<float> { using T = float2; };
+template <> struct CplxOf<double> { using T = double2; };
+
+// Loads of the field.  The read-only path (__ldg) is only valid while nothing
+// in the same launch writes the field; the batched kernel, whose CTAs read what
+// other CTAs wrote earlier in the launch (after an acquire), passes NC = false
+// and reads through L2.
+template <bool NC = true, typename C>
+__device__ __forceinline__ C ldg(const C* p) {
+  if constexpr (NC) return __ldg(p);
+  else return __ldcg(p);  // L2 only: never a stale L1 line of another CTA's write
+}
+
+// acc += (A + i B) * v  for A, B in {-1, 0, 1}: additions only.
+template <int A, int B, typename C>
+__device__ __forceinline__ void cmac(C& acc, const C& v) {
+  if constexpr (A == 1) { acc.x += v.x; acc.y += v.y; }
+  if constexpr (A == -1) { acc.x -= v.x; acc.y -= v.y; }
+  if constexpr (B == 1) { acc.x -= v.y; acc.y += v.x; }
+  if constexpr (B == -1) { acc.x += v.y; acc.y -= v.x; }
+}
+
+// nq * S + i m * o  (FP32: hi/lo split coefficients through FMA chains).
+__device__ __forceinline__ float2 finish(const Coef32& c, float2 S, float2 o) {
+  float rx = -c.m_lo * o.y;
+  rx = fmaf(c.nq_lo, S.x, rx);
+  rx = fmaf(-c.m_hi, o.y, rx);
+  rx = fmaf(c.nq_hi, S.x, rx);
+  float ry = c.m_lo * o.x;
+  ry = fmaf(c.nq_lo, S.y, ry);
+  ry = fmaf(c.m_hi, o.x, ry);
+  ry = fmaf(c.nq_hi, S.y, ry);
+  return make_float2(rx, ry);
+}
+__device__ __forceinline__ double2 finish(const Coef64& c, double2 S, double2 o) {
+  return make_double2(fma(c.nq, S.x, -c.m * o.y), fma(c.nq, S.y, c.m * o.x));
+}
+
+template <typename R> struct CoefOf;
+template <> struct CoefOf<float> { using T = Coef32; };
+template <> struct CoefOf<double> { using T = Coef64; };
+
+__device__ __forceinline__ int64_t wrapm(int64_t v, int64_t M) { return v < 0 ? v + M : (v >= M ? v - M : v); }
+
+
+// ------------------------------------------------------------ per-site updates
+// chain, s = 2: psi'_0(x) = n psi_0(x-1) + i m psi_1(x), psi'_1(x) = i m psi_0(x) + n psi_1(x+1)
+template <typename R, bool NC = true>
+__device__ __forceinline__ void site_update_1d(const typename CplxOf<R>::T* __restrict__ in,
+                                               typename CplxOf<R>::T* __restrict__ out, int64_t N, int64_t x,
+                                               const typename CoefOf<R>::T& cf) {
+  using C = typename CplxOf<R>::T;
+  const C* p0 = in;
+  const C* p1 = in + N;
+  C a = ldg<NC>(p0 + wrapm(x - 1, N));   // psi_0(x - 1)
+  C b = ldg<NC>(p1 + wrapm(x + 1, N));   // psi_1(x + 1)
+  C o0 = ldg<NC>(p0 + x), o1 = ldg<NC>(p1 + x);
+  out[x] = finish(cf, a, o1);
+  out[N + x] = finish(cf, b, o0);
+}
+
+// square lattice, s = 4 (tables above), site (x, y) of the N x N box
+template <typename R, bool NC = true>
+__device__ __forceinline__ void site_update_2d(const typename CplxOf<R>::T* __restrict__ in,
+                                               typename CplxOf<R>::T* __restrict__ out, int64_t N, int64_t x,
+                                               int64_t y, const typename CoefOf<R>::T& cf) {
+  using C = typename CplxOf<R>::T;
+  const int64_t vol = N * N;
+  const int64_t xm = wrapm(x - 1, N), xp = wrapm(x + 1, N);
+  const int64_t ym = wrapm(y - 1, N), yp = wrapm(y + 1, N);
+  C S0 = {0, 0}, S1 = {0, 0}, S2 = {0, 0}, S3 = {0, 0};
+  {  // h = +e1: source (x - 1, y)
+    const int64_t i = y * N + xm;
+    C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
+    cmac<1, 1>(S0, a); cmac<1, -1>(S0, b); cmac<1, 1>(S1, a); cmac<1, -1>(S1, b);
+    cmac<1, -1>(S2, c); cmac<-1, 1>(S2, d); cmac<-1, -1>(S3, c); cmac<1, 1>(S3, d);
+  }
+  {  // h = -e1: source (x + 1, y)
+    const int64_t i = y * N + xp;
+    C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
+    cmac<1, 1>(S0, a); cmac<-1, 1>(S0, b); cmac<-1, -1>(S1, a); cmac<1, -1>(S1, b);
+    cmac<1, -1>(S2, c); cmac<1, -1>(S2, d); cmac<1, 1>(S3, c); cmac<1, 1>(S3, d);
+  }
+  {  // h = +e2: source (x, y - 1)
+    const int64_t i = ym * N + x;
+    C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
+    cmac<1, -1>(S0, a); cmac<1, 1>(S0, b); cmac<1, -1>(S1, a); cmac<1, 1>(S1, b);
+    cmac<1, 1>(S2, c); cmac<-1, -1>(S2, d); cmac<-1, 1>(S3, c); cmac<1, -1>(S3, d);
+  }
+  {  // h = -e2: source (x, y + 1)
+    const int64_t i = yp * N + x;
+    C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
+    cmac<1, -1>(S0, a); cmac<-1, -1>(S0, b); cmac<-1, 1>(S1, a); cmac<1, 1>(S1, b);
+    cmac<1, 1>(S2, c); cmac<1, 1>(S2, d); cmac<1, -1>(S3, c); cmac<1, -1>(S3, d);
+  }
+  const int64_t i = y * N + x;
+  C o0 = ldg<NC>(in + i), o1 = ldg<NC>(in + vol + i), o2 = ldg<NC>(in + 2 * vol + i), o3 = ldg<NC>(in + 3 * vol + i);
+  out[i] = finish(cf, S0, o2);
+  out[vol + i] = finish(cf, S1, o3);
+  out[2 * vol + i] = finish(cf, S2, o0);
+  out[3 * vol + i] = finish(cf, S3, o1);
+}
+
+// BCC, s = 4: output coset c at cell (x, y, z) reads coset 1-c at (per axis)
+// m - 1 + c for h = +1 and m + c for h = -1 (the site x - h of the other sublattice).
+template <int HX, int HY, int HZ, bool NC = true, typename C>
+__device__ __forceinline__ void bcc_term(C& S0, C& S1, C& S2, C& S3, const C* __restrict__ src, int64_t vol) {
+  constexpr int P = HX * HY * HZ;
+  if constexpr (HZ == 1) {
+    C a = ldg<NC>(src), b = ldg<NC>(src + vol), d = ldg<NC>(src + 3 * vol);
+    cmac<1, -P>(S0, a);
+    cmac<HX, -HY>(S0, b);
+    cmac<-HX, HY>(S2, d);
+    cmac<1, -P>(S3, d);
+  } else {
+    C a = ldg<NC>(src), b = ldg<NC>(src + vol), c = ldg<NC>(src + 2 * vol);
+    cmac<HX, HY>(S1, a);
+    cmac<1, -P>(S1, b);
+    cmac<1, -P>(S2, c);
+    cmac<-HX, -HY>(S3, c);
+  }
+}
+
+template <typename R, bool NC = true>
+__device__ __forceinline__ void site_update_3d(const typename CplxOf<R>::T* __restrict__ in,
+                                               typename CplxOf<R>::T* __restrict__ out, int64_t M, int c,
+                                               int64_t z, int64_t y, int64_t x, const typename CoefOf<R>::T& cf) {
+  using C = typename CplxOf<R>::T;
+  const int64_t plane = M * M, vol = plane * M;
+  const int64_t xa = wrapm(x - 1 + c, M), xb = wrapm(x + c, M);
+  const int64_t ya = wrapm(y - 1 + c, M), yb = wrapm(y + c, M);
+  const int64_t za = wrapm(z - 1 + c, M), zb = wrapm(z + c, M);
+  const C* src = in + (int64_t)(1 - c) * 4 * vol;
+  C S0 = {0, 0}, S1 = {0, 0}, S2 = {0, 0}, S3 = {0, 0};
+  bcc_term<+1, +1, +1, NC>(S0, S1, S2, S3, src + za * plane + ya * M + xa, vol);
+  bcc_term<+1, -1, +1, NC>(S0, S1, S2, S3, src + za * plane + yb * M + xa, vol);
+  bcc_term<-1, +1, +1, NC>(S0, S1, S2, S3, src + za * plane + ya * M + xb, vol);
+  bcc_term<-1, -1, +1, NC>(S0, S1, S2, S3, src + za * plane + yb * M + xb, vol);
+  bcc_term<+1, +1, -1, NC>(S0, S1, S2, S3, src + zb * plane + ya * M + xa, vol);
+  bcc_term<+1, -1, -1, NC>(S0, S1, S2, S3, src + zb * plane + yb * M + xa, vol);
+  bcc_term<-1, +1, -1, NC>(S0, S1, S2, S3, src + zb * plane + ya * M + xb, vol);
+  bcc_term<-1, -1, -1, NC>(S0, S1, S2, S3, src + zb * plane + yb * M + xb, vol);
+  const int64_t i = z * plane + y * M + x;
+  const C* own = in + (int64_t)c * 4 * vol + i;
+  C o0 = ldg<NC>(own), o1 = ldg<NC>(own + vol), o2 = ldg<NC>(own + 2 * vol), o3 = ldg<NC>(own + 3 * vol);
+  C* dst = out + (int64_t)c * 4 * vol + i;
+  dst[0] = finish(cf, S0, o2);
+  dst[vol] = finish(cf, S1, o3);
+  dst[2 * vol] = finish(cf, S2, o0);
+  dst[3 * vol] = finish(cf, S3, o1);
+}
+
+}  // namespace qw
