@@ -202,6 +202,66 @@ qw_status qw_batch_sync(qw_batch batch, void* stream);
  * weights are NaN here (use a plan's qw_observables).  Synchronous. */
 qw_status qw_batch_observables(qw_batch batch, qw_obs* out, void* stream);
 
+/* Fill psi_dev with the Gaussian packet
+ *     psi(x) = exp(-|d|^2 / (4 sigma^2)) exp(i k0.d) chi,   d = minimum-image (x - x0),
+ * on the plan's box (physical coordinates on the BCC lattice, lattice
+ * coordinates (a, b) in 2D): the position-space shape of the particle states of
+ * Sec. 5 (Definition 1).  chi: s complex values as (re, im) pairs (s = 2 in 1D,
+ * 4 otherwise; 8 doubles are read).  Not normalised.  Asynchronous.
+ * Errors: QW_EINVAL (null pointer, sigma <= 0), QW_ECUDA. */
+qw_status qw_prepare_packet(qw_plan plan, void* psi_dev, const double* x0, double sigma, const double* k0,
+                            const double* chi, void* stream);
+
+/* ---------------------------------------------------------------- serving
+ * Walk requests evolved in the Fourier form (Sec. 4, complex64 fields, FP64
+ * phase and reductions) by one scheduler thread with continuous batching:
+ * requests wait in a FIFO, the head is admitted when one of `slots` CUDA
+ * streams is free and its fields (8 B per complex value + 8 B per site for the
+ * omega table) fit in the device pool of `hbm_budget_bytes` (allocated once at
+ * creation); finished requests return their slot and memory, so requests that
+ * arrived meanwhile start while others are still running, and requests in
+ * different slots overlap on the device.  The initial state is normalised. */
+typedef struct {
+  int dim;                 /* 1, 2 or 3 */
+  int64_t N;               /* box side; every axis length (N, or N/2 in 3D) 2^a 3^b */
+  double mass;             /* m in [0, 1] */
+  int64_t t;               /* time, >= 0 */
+  const void* psi0_host;   /* complex64 initial field (device layout), copied at submit; or NULL ... */
+  double x0[3];            /* ... for the packet of qw_prepare_packet with these parameters */
+  double sigma;
+  double k0[3];
+  double chi[8];
+} qw_request;
+
+typedef struct qw_server_s* qw_server;
+
+typedef struct {
+  int64_t pending, running, admitted, completed;
+  int64_t bytes_in_use, peak_bytes, budget_bytes;
+} qw_server_stats_t;
+
+/* Start a server on the current device with a device pool of hbm_budget_bytes,
+ * `slots` concurrent streams (1..64) and at most max_pending queued requests.
+ * Errors: QW_EINVAL, QW_ENOMEM, QW_ECUDA. */
+qw_status qw_server_create(size_t hbm_budget_bytes, int slots, int max_pending, qw_server* out);
+
+/* Queue a request; *ticket identifies it.  Does not block on the GPU.
+ * Errors: QW_EINVAL (bad request, axis not 2^a 3^b, larger than the whole
+ * budget), QW_EAGAIN (pending queue full: retry later). */
+qw_status qw_submit(qw_server server, const qw_request* req, uint64_t* ticket);
+
+/* Non-blocking: *done = 0 while the request waits or runs; once done, *done = 1,
+ * *out holds its norm, <x> and particle weights, *latency_s the time from
+ * qw_submit to completion, and the ticket is retired.
+ * Errors: QW_ENOTFOUND (unknown or retired ticket), QW_ECUDA (the request failed). */
+qw_status qw_poll(qw_server server, uint64_t ticket, qw_obs* out, int* done, double* latency_s);
+
+/* Queue and pool occupancy counters. */
+qw_status qw_server_stats(qw_server server, qw_server_stats_t* out);
+
+/* Stop the scheduler (queued requests are dropped, running ones finish) and free everything. */
+qw_status qw_server_destroy(qw_server server);
+
 /* qw_step without any device allocation, for callers that cannot call
  * cudaMalloc where they step a walk: code whose device memory is owned and
  * budgeted by another allocator (for example a framework's caching pool that

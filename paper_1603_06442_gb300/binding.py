@@ -40,6 +40,17 @@ class qw_walk(ctypes.Structure):
                 ("psi_dev", ctypes.c_void_p)]
 
 
+class qw_request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("N", ctypes.c_int64), ("mass", ctypes.c_double), ("t", ctypes.c_int64),
+                ("psi0_host", ctypes.c_void_p), ("x0", ctypes.c_double * 3), ("sigma", ctypes.c_double),
+                ("k0", ctypes.c_double * 3), ("chi", ctypes.c_double * 8)]
+
+
+class qw_server_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("pending", "running", "admitted", "completed", "bytes_in_use",
+                                              "peak_bytes", "budget_bytes")]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -56,6 +67,15 @@ _SIGS = {
     "qw_plan_get_stencil": (ctypes.c_int, [ctypes.c_void_p]),
     "qw_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "qw_plan_prepare_spectral": (ctypes.c_int, [ctypes.c_void_p]),
+    "qw_prepare_packet": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "qw_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "qw_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qw_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "qw_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(qw_obs), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_double)]),
+    "qw_server_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qw_server_stats_t)]),
+    "qw_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "qw_batch_create": (ctypes.c_int, [ctypes.POINTER(qw_walk), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "qw_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "qw_batch_set_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
@@ -161,6 +181,74 @@ def qw_plan_prepare_spectral(plan):
 
 def qw_evolve_spectral(plan, psi, t, stream=None):
     _check(load().qw_evolve_spectral(plan, _ptr(psi), int(t), _stream(stream)))
+
+
+def _darr(vals, n):
+    a = (ctypes.c_double * n)()
+    for i, v in enumerate(list(vals)[:n]):
+        a[i] = float(v)
+    return a
+
+
+def _chi8(chi):
+    flat = []
+    for c in chi:
+        c = complex(c)
+        flat += [c.real, c.imag]
+    return _darr(flat + [0.0] * (8 - len(flat)), 8)
+
+
+def qw_prepare_packet(plan, psi, x0, sigma, k0, chi, stream=None):
+    _check(load().qw_prepare_packet(plan, _ptr(psi), _darr(list(x0) + [0, 0, 0], 3), float(sigma),
+                                    _darr(list(k0) + [0, 0, 0], 3), _chi8(chi), _stream(stream)))
+
+
+def qw_server_create(hbm_budget_bytes, slots=8, max_pending=4096):
+    h = ctypes.c_void_p()
+    _check(load().qw_server_create(int(hbm_budget_bytes), int(slots), int(max_pending), ctypes.byref(h)))
+    return h.value
+
+
+def make_request(dim, N, mass, t, psi0_host=None, x0=(0, 0, 0), sigma=1.0, k0=(0, 0, 0), chi=(1, 0, 0, 0)):
+    r = qw_request()
+    r.dim, r.N, r.mass, r.t = int(dim), int(N), float(mass), int(t)
+    r.psi0_host = None if psi0_host is None else psi0_host.ctypes.data
+    for i, v in enumerate((list(x0) + [0, 0, 0])[:3]):
+        r.x0[i] = float(v)
+    r.sigma = float(sigma)
+    for i, v in enumerate((list(k0) + [0, 0, 0])[:3]):
+        r.k0[i] = float(v)
+    ch = _chi8(chi)
+    for i in range(8):
+        r.chi[i] = ch[i]
+    return r
+
+
+def qw_submit(server, req):
+    """Returns the ticket, or None when the queue is full (QW_EAGAIN)."""
+    t = ctypes.c_uint64()
+    st = load().qw_submit(server, ctypes.byref(req), ctypes.byref(t))
+    if st == QW_EAGAIN:
+        return None
+    _check(st)
+    return t.value
+
+
+def qw_poll(server, ticket):
+    """(done, obs dict or None, latency seconds or None)."""
+    o, d, lat = qw_obs(), ctypes.c_int(), ctypes.c_double()
+    _check(load().qw_poll(server, int(ticket), ctypes.byref(o), ctypes.byref(d), ctypes.byref(lat)))
+    return (True, o.as_dict(), lat.value) if d.value else (False, None, None)
+
+
+def qw_server_stats(server):
+    s = qw_server_stats_t()
+    _check(load().qw_server_stats(server, ctypes.byref(s)))
+    return {n: getattr(s, n) for n, _ in qw_server_stats_t._fields_}
+
+
+def qw_server_destroy(server):
+    _check(load().qw_server_destroy(server))
 
 
 def qw_step_static(dim, N, mass, dtype, psi, nsteps, stream=None):
@@ -310,6 +398,10 @@ class Plan:
 
     def sync(self, stream=None):
         qw_sync(self.handle, stream)
+
+    def prepare_packet(self, psi, x0, sigma, k0, chi, stream=None):
+        self.check_field(psi)
+        qw_prepare_packet(self.handle, psi, x0, sigma, k0, chi, stream)
 
     def observables(self, psi, stream=None):
         self.check_field(psi)

@@ -261,6 +261,17 @@ qw_status qw_evolve_spectral(qw_plan p, void* psi, int64_t t, void* stream) {
   return fft_inverse(p->fft, p->g.dim, psi, s);
 }
 
+qw_status qw_prepare_packet(qw_plan p, void* psi, const double* x0, double sigma, const double* k0,
+                            const double* chi, void* stream) {
+  if (!p || !psi || !x0 || !k0 || !chi) {
+    set_error("qw_prepare_packet: null argument");
+    return QW_EINVAL;
+  }
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  return launch_packet(p->g, p->dtype, x0, sigma, k0, chi, psi, static_cast<cudaStream_t>(stream));
+}
+
 qw_status qw_sync(qw_plan p, void* stream) {
   if (!p) {
     set_error("qw_sync: null plan");

@@ -27,6 +27,10 @@ qw_status cuda_fail(cudaError_t e, const char* what);
     if (qw_e_ != cudaSuccess) return ::qw::cuda_fail(qw_e_, what);  \
   } while (0)
 
+template <typename T> struct CplxOf2;
+template <> struct CplxOf2<float> { using t = float2; };
+template <> struct CplxOf2<double> { using t = double2; };
+
 // ---- geometry -------------------------------------------------------------
 // One field in the device layout: ncoset x s planes of `vol` complex values,
 // each plane [z][y][x] with extents (nz, ny, nx).  1D: nx = N, ny = nz = 1;
@@ -114,9 +118,18 @@ struct SpecAxes {  // digit split of each axis (storage order -> frequency)
 SpecAxes spec_axes(const Geometry& g, const FftPlan& f);
 qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,
                              cudaStream_t st);
-// psi_hat (forward DFT, storage order) <- D_k^t psi_hat / |V|, BCC cosets mixed per cell.
+// psi_hat (forward DFT, storage order) <- D_k^t psi_hat / |V|, BCC cosets mixed per cell;
+// with norm0 (device, optional) the result is also divided by sqrt(norm0[0]).
 qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
-                                  const double* omega, int64_t t, void* psi_hat, cudaStream_t st);
+                                  const double* omega, int64_t t, void* psi_hat, cudaStream_t st,
+                                  const double* norm0 = nullptr);
+
+// ---- state preparation (packet.cu) ---------------------------------------------
+// psi(x) = exp(-|d|^2 / (4 sigma^2)) exp(i k0.d) chi with d the minimum-image
+// displacement from x0 on the periodic box (physical BCC coordinates, lattice
+// coordinates in 2D); chi = s complex values (re, im interleaved).  Not normalised.
+qw_status launch_packet(const Geometry& g, qw_dtype dt, const double* x0, double sigma, const double* k0,
+                        const double* chi, void* psi, cudaStream_t st);
 // (sum |psi^|^2, sum psi^dag G/sin(omega) psi^) over the zone into result[0..1].
 qw_status launch_particle_weights(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
                                   const void* psi_hat, double* partials, double* result, cudaStream_t st);

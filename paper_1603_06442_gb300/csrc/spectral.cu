@@ -316,10 +316,13 @@ __device__ __forceinline__ void cs_of(double omega, double tt, T& c, T& s) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t count, double n, double m,
-                                                     const double* __restrict__ omega, double tt, T scale,
+                                                     const double* __restrict__ omega, double tt, T scale_in,
+                                                     const double* __restrict__ norm0,
                                                      typename Cx2<T>::t* __restrict__ data) {
   using V = typename Cx2<T>::t;
   const double PI = 3.141592653589793238462643383279;
+  // optional normalisation of the initial state, folded into the 1/|V| scale
+  const T scale = norm0 ? (T)((double)scale_in / sqrt(norm0[0])) : scale_in;
   int64_t x, y, z;
   if (grid_pos(a, x, y, z)) {
     const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
@@ -493,15 +496,16 @@ qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, do
 }
 
 qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
-                                  const double* omega, int64_t t, void* psi_hat, cudaStream_t st) {
+                                  const double* omega, int64_t t, void* psi_hat, cudaStream_t st,
+                                  const double* norm0) {
   const int64_t count = kcount(g);
   const double inv = 1.0 / (double)g.vol;
   if (dt == QW_C64)
     evolve_kernel<float><<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), count, n, m, omega, (double)t,
-                                                         (float)inv, static_cast<float2*>(psi_hat));
+                                                         (float)inv, norm0, static_cast<float2*>(psi_hat));
   else
     evolve_kernel<double><<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), count, n, m, omega, (double)t, inv,
-                                                          static_cast<double2*>(psi_hat));
+                                                          norm0, static_cast<double2*>(psi_hat));
   QW_CHECK_LAUNCH("evolve launch");
   return QW_OK;
 }
