@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--N", type=int, default=None, help="override the box side (profiling runs)")
     ap.add_argument("--stencil", default=None, help="force a stencil variant (plain, vec, tma)")
+    ap.add_argument("--only", default=None, choices=["spectral", "batched", "served"],
+                    help="run one secondary workload alone and print its JSON (profiling runs)")
+    ap.add_argument("--requests", type=int, default=1000, help="served workload: number of requests")
+    ap.add_argument("--walks", type=int, default=256, help="batched workload: number of walks")
     ap.add_argument("--substeps", type=int, default=None, help="override stencil steps per bench step")
     args = ap.parse_args()
     if args.N is not None:
@@ -318,7 +322,17 @@ def extra_measurements(qb, dev, stream):
         variants[name] = {"ms_per_step": ms, "site_steps_per_s": plan.sites / (ms / 1e3),
                           "hbm_GBps": 2 * plan.elems * 8 / (ms / 1e3) / 1e9}
     out["c64_stencil_variants"] = variants
-    # spectral form on the same box: the cost must not depend on t
+    out["spectral"] = spectral_measurement(qb, dev, stream)
+    out["batched"] = batched_measurement(qb, dev, stream)
+    out["served"] = served_measurement(qb, dev, stream)
+    return out
+
+
+def spectral_measurement(qb, dev, stream):
+    """Spectral form on the bench box (complex64 at t = 1e4 and 1e6, complex128 at 1e4): flat in t."""
+    import torch
+    W = WORKLOAD
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     spec = {}
     for dt, tag in (("c64", "c64"), ("c128", "c128")):
         plan = qb.Plan(3, W["N"], W["mass"], dt)
@@ -340,17 +354,110 @@ def extra_measurements(qb, dev, stream):
                                          "equivalent_site_steps_per_s": plan.sites * t / (ms / 1e3),
                                          "effective_GBps_vs_4_field_passes": bytes_min / (ms / 1e3) / 1e9}
         plan.close()
-    out["spectral"] = spec
-    out["batched"] = batched_measurement(qb, dev, stream)
-    return out
+    return spec
 
 
-def batched_measurement(qb, dev, stream, runs=3):
+def fp64_plain_rates(qb, dev, stream):
+    """FP64 plain-form (complex128 stencil) site-steps/s per dimension on this GPU."""
+    import torch
+    rates = {}
+    for dim, N in ((1, 1 << 22), (2, 1024), (3, 256)):
+        plan = qb.Plan(dim, N, 0.1, "c128")
+        x = torch.zeros(plan.elems, dtype=torch.complex128, device=dev)
+        x[::3] = 1e-3
+        plan.step(x, 2, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.step(x, 6, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        rates[dim] = plan.sites * 6 / (e0.elapsed_time(e1) / 1e3)
+        plan.close()
+    return rates
+
+
+def served_measurement(qb, dev, stream, n_req=1000, rate=200.0, budget_gb=150, slots=8):
+    """Poisson arrivals (200/s) of walk requests: dim U{1,2,3}, sites log-U[1e4, 1e8] snapped to
+    2^a 3^b boxes, m U[0, 0.5], t log-U[10, 1e5]; packets of width N/16 at the box centre; each asks
+    for norm, <x> and particle weight.  Spectral path, complex64 with FP64 phase and reductions."""
+    import time as _t
+    from paper_1603_06442_gb300 import inputs
+    stream_reqs = inputs.sample_served_stream(n_req, rate, seed=0)
+    srv = qb.qw_server_create(int(budget_gb) << 30, slots=slots, max_pending=1 << 16)
+    chi = {1: [1, 0], 2: [0.5, 0.5, 0.5j, -0.5j], 3: [0.5, 0.5, 0.5j, -0.5j]}
+    reqs = []
+    for r in stream_reqs:
+        d, N = r["dim"], r["N"]
+        reqs.append(qb.make_request(d, N, r["mass"], r["t"], x0=[N / 2] * d, sigma=max(N / 16, 1.0),
+                                    k0=[0.2] * d, chi=chi[d]))
+    # warm the per-geometry FFT plans outside the measurement
+    warm = set()
+    wt = []
+    for r, req in zip(stream_reqs, reqs):
+        key = (r["dim"], r["N"])
+        if key not in warm:
+            warm.add(key)
+            wt.append(qb.qw_submit(srv, req))
+    _drain(qb, srv, wt)
+    lat, out, pend = [], [], {}
+    t0 = _t.perf_counter()
+    i = 0
+    while i < len(reqs) or pend:
+        now = _t.perf_counter() - t0
+        while i < len(reqs) and stream_reqs[i]["arrival"] <= now:
+            tk = qb.qw_submit(srv, reqs[i])
+            if tk is None:
+                break
+            pend[tk] = i
+            i += 1
+        for tk in list(pend):
+            done, obs, l = qb.qw_poll(srv, tk)
+            if done:
+                lat.append(l)
+                out.append(obs)
+                del pend[tk]
+        _t.sleep(0.0002)
+    wall = _t.perf_counter() - t0
+    st = qb.qw_server_stats(srv)
+    qb.qw_server_destroy(srv)
+    site_t = 0.0
+    fp64 = fp64_plain_rates(qb, dev, stream)
+    est = []
+    for r in stream_reqs:
+        d, N = r["dim"], r["N"]
+        sites = N if d == 1 else (N * N if d == 2 else N ** 3 // 4)
+        site_t += sites * r["t"]
+        est.append(sites * r["t"] / fp64[d])
+    lat = np.array(lat)
+    est = np.array(est)
+    return {"requests": len(reqs), "arrival_rate_per_s": rate, "slots": slots, "budget_GB": budget_gb,
+            "latency_p50_ms": float(np.percentile(lat, 50) * 1e3), "latency_p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "latency_mean_ms": float(lat.mean() * 1e3), "wall_s": wall, "completed_per_s": len(lat) / wall,
+            "equivalent_site_steps_per_s": site_t / wall, "peak_pool_GB": st["peak_bytes"] / 2 ** 30,
+            "max_norm_drift": float(max(abs(o["norm"] - 1) for o in out)),
+            "fp64_plain_unbatched": {"service_p50_ms": float(np.percentile(est, 50) * 1e3),
+                                     "service_p99_ms": float(np.percentile(est, 99) * 1e3),
+                                     "rates_site_steps_per_s": {str(k): v for k, v in fp64.items()},
+                                     "note": "per-request service time of the FP64 stencil (sites*t / measured "
+                                             "FP64 rate on this GPU), no queueing: extrapolated, not run"}}
+
+
+def _drain(qb, srv, tickets):
+    import time as _t
+    left = set(t for t in tickets if t is not None)
+    while left:
+        for t in list(left):
+            if qb.qw_poll(srv, t)[0]:
+                left.discard(t)
+        _t.sleep(0.0005)
+
+
+def batched_measurement(qb, dev, stream, runs=3, n_walks=256):
     """256 uneven walks (2D N log-U[64,1024], BCC N log-U[32,128], m U[0,0.5], t U{100..5000},
     packets of width N/16) in one persistent launch replayed from a CUDA graph; tiling autotuned."""
     import torch
     from paper_1603_06442_gb300 import inputs
-    mix = inputs.sample_batch_mix(256, seed=0)
+    mix = inputs.sample_batch_mix(n_walks, seed=0)
     fields = []
     for w in mix:
         N = w["N"]
@@ -386,9 +493,29 @@ def batched_measurement(qb, dev, stream, runs=3):
             "launches_per_run": 1, "graph": True}
 
 
+def run_only(args, local):
+    import torch
+    from paper_1603_06442_gb300 import binding as qb
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    if args.only == "served":
+        out = served_measurement(qb, dev, stream, n_req=args.requests)
+    elif args.only == "batched":
+        out = batched_measurement(qb, dev, stream, n_walks=args.walks)
+    else:
+        out = spectral_measurement(qb, dev, stream)
+    print(json.dumps({"only": args.only, "config": {"workload": WORKLOAD["name"], "N": WORKLOAD["N"]},
+                      "result": out}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.only:
+        if rank == 0:
+            run_only(args, local)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

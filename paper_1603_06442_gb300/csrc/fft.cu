@@ -168,20 +168,29 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __rest
   const int total = L * ncol;
 
   // ---- load (and undo the inter-pass twiddle on the inverse) ----
-  for (int e = tid; e < total; e += nthr) {
-    int j, c;
-    if (S == 1) {
-      c = e / L;
-      j = e - c * L;
-    } else {
-      j = e / ncol;
-      c = e - j * ncol;
+  // C divides the block, so for S > 1 every thread keeps one column c and its
+  // line base; for S == 1 the CTA's lines are one contiguous run.
+  const int cfix = tid % C;
+  int64_t base_c = 0, twb_c = 0;
+  {
+    const int64_t l = l0 + cfix;
+    if (l < nlines) {
+      const int64_t o = l / S, i = l - o * S;
+      base_c = o * (int64_t)L * S + i;
+      twb_c = i / p.tw_div;
     }
-    const int64_t l = l0 + c;
-    const int64_t o = l / S, i = l - o * S;
-    V v = data[o * (int64_t)L * S + (int64_t)j * S + i];
-    if (INV && p.twiddle) v = cmulc(v, twiddle_big(tw_hi, tw_lo, (int64_t)j * (i / p.tw_div), p.tlo_bits));
-    bufA[j * pitch + c] = v;
+  }
+  if (S == 1) {
+    for (int e = tid; e < total; e += nthr) {
+      const int c = e / L, j = e - c * L;
+      bufA[j * pitch + c] = data[l0 * L + e];
+    }
+  } else if (cfix < ncol) {
+    for (int j = tid / C; j < L; j += nthr / C) {
+      V v = data[base_c + (int64_t)j * S];
+      if (INV && p.twiddle) v = cmulc(v, twiddle_big(tw_hi, tw_lo, (int64_t)j * twb_c, p.tlo_bits));
+      bufA[j * pitch + cfix] = v;
+    }
   }
   __syncthreads();
 
@@ -193,8 +202,9 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __rest
     const int R = p.radix[s];
     const int nb = L / R;
     const int tstep = L / (Ns * R);  // table stride of omega_{Ns R}
-    for (int b = tid; b < nb * ncol; b += nthr) {
-      const int jb = b / ncol, c = b - jb * ncol;
+    for (int b = tid; b < nb * C; b += nthr) {
+      const int jb = b >> p.cshift, c = b & (C - 1);
+      if (c >= ncol) continue;
       const int k = jb % Ns;
       const int idxD = (jb / Ns) * Ns * R + k;
       if (R == 8) {
@@ -255,20 +265,17 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __rest
   }
 
   // ---- store (apply the inter-pass twiddle on the forward) ----
-  for (int e = tid; e < total; e += nthr) {
-    int j, c;
-    if (S == 1) {
-      c = e / L;
-      j = e - c * L;
-    } else {
-      j = e / ncol;
-      c = e - j * ncol;
+  if (S == 1) {
+    for (int e = tid; e < total; e += nthr) {
+      const int c = e / L, j = e - c * L;
+      data[l0 * L + e] = in[j * pitch + c];
     }
-    const int64_t l = l0 + c;
-    const int64_t o = l / S, i = l - o * S;
-    V v = in[j * pitch + c];
-    if (!INV && p.twiddle) v = cmul(v, twiddle_big(tw_hi, tw_lo, (int64_t)j * (i / p.tw_div), p.tlo_bits));
-    data[o * (int64_t)L * S + (int64_t)j * S + i] = v;
+  } else if (cfix < ncol) {
+    for (int j = tid / C; j < L; j += nthr / C) {
+      V v = in[j * pitch + cfix];
+      if (!INV && p.twiddle) v = cmul(v, twiddle_big(tw_hi, tw_lo, (int64_t)j * twb_c, p.tlo_bits));
+      data[base_c + (int64_t)j * S] = v;
+    }
   }
 }
 
@@ -538,9 +545,11 @@ static qw_status build_pass(FftPass* p, int L, int64_t S, int64_t O, int64_t tw_
   const int esz = (int)sizeof(typename Cx<T>::t);
   // widest tile (<= 16 lines) whose two padded buffers fit the shared-memory budget
   const int64_t nlines = O * S;
-  int C = 16;
-  while (C > 1 && (C > nlines || 2 * (size_t)L * ((C % 2 == 0) ? C + 1 : C) * esz > (size_t)kFftSmemBytes)) --C;
+  int C = 16;  // a power of two, so it divides the 256-thread block
+  while (C > 1 && (C > nlines || 2 * (size_t)L * ((C % 2 == 0) ? C + 1 : C) * esz > (size_t)kFftSmemBytes)) C >>= 1;
   p->C = C;
+  p->cshift = 0;
+  while ((1 << p->cshift) < C) ++p->cshift;
   p->pitch = (C % 2 == 0) ? C + 1 : C;
   p->smem = 2 * (size_t)L * p->pitch * esz;
   if (p->smem > (size_t)kFftSmemBytes) {
@@ -613,13 +622,46 @@ static qw_status fft_plan_t(FftPlan* f, const Geometry& g) {
   return QW_OK;
 }
 
+static qw_status trig_tables(FftPlan* f, const Geometry& g) {
+  const int64_t ext[3] = {g.nx, g.ny, g.nz};
+  for (int ax = 0; ax < g.dim; ++ax) {
+    int64_t len, period;  // angle = 2 pi q / period for q < len
+    if (g.dim == 1) {
+      len = g.nx;
+      period = g.nx;
+    } else if (g.dim == 2) {
+      if (ax > 0) break;  // one table serves both halves
+      len = 2 * g.nx;
+      period = 2 * g.nx;
+    } else {
+      len = ext[ax];
+      period = 2 * ext[ax];
+    }
+    std::vector<double2> h(len);
+    for (int64_t q = 0; q < len; ++q) {
+      const double ang = 2.0 * M_PI * (double)(q % period) / (double)period;
+      h[q].x = std::cos(ang);
+      h[q].y = std::sin(ang);
+    }
+    QW_CHECK_CUDA(cudaMalloc(&f->trig[ax], len * sizeof(double2)));
+    QW_CHECK_CUDA(cudaMemcpy(f->trig[ax], h.data(), len * sizeof(double2), cudaMemcpyHostToDevice));
+  }
+  return QW_OK;
+}
+
 qw_status fft_plan_create(FftPlan* f, const Geometry& g, qw_dtype dt) {
   *f = FftPlan();
   f->dtype = dt;
-  return dt == QW_C64 ? fft_plan_t<float>(f, g) : fft_plan_t<double>(f, g);
+  qw_status st = dt == QW_C64 ? fft_plan_t<float>(f, g) : fft_plan_t<double>(f, g);
+  if (st != QW_OK) return st;
+  return trig_tables(f, g);
 }
 
 void fft_plan_destroy(FftPlan* f) {
+  for (int a = 0; a < 3; ++a) {
+    if (f->trig[a]) cudaFree(f->trig[a]);
+    f->trig[a] = nullptr;
+  }
   for (int i = 0; i < f->npass; ++i) {
     if (f->pass[i].tw_line) cudaFree(f->pass[i].tw_line);
     if (f->pass[i].tw_hi) cudaFree(f->pass[i].tw_hi);

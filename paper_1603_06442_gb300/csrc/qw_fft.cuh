@@ -20,7 +20,8 @@ struct FftPass {
   int L;
   int64_t S;
   int64_t O;
-  int C;            // lines per CTA
+  int C;            // lines per CTA (a power of two)
+  int cshift;       // log2(C)
   int pitch;        // shared-memory line pitch (elements)
   size_t smem;      // dynamic shared memory bytes
   int nstages;
@@ -46,6 +47,10 @@ struct FftPlan {
   int npass = 0;
   FftPass pass[9];
   FftAxis axis[3];
+  // (cos, sin) tables of the symbol's angles, FP64 (double2), per axis:
+  //   dim 1: 2 pi f / N (f < N);  dim 2: pi q / N (q < 2N, for k1 +- k2 halves);
+  //   dim 3: pi f / M (f < M, the half wave vector kappa / 2 of each axis)
+  void* trig[3] = {nullptr, nullptr, nullptr};
 };
 
 bool fft_size_ok(int64_t L);

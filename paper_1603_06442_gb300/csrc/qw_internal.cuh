@@ -110,10 +110,11 @@ qw_status launch_position_moments(const Geometry& g, qw_dtype dt, const void* ps
                                   double* result, cudaStream_t st);
 
 // ---- spectral path (spectral.cu) ---------------------------------------------
-struct SpecAxes {  // digit split of each axis (storage order -> frequency)
+struct SpecAxes {  // digit split of each axis (storage order -> frequency) and trig tables
   int nparts[3];
   int part[3][3];
   int64_t len[3];
+  const double2* trig[3];
 };
 SpecAxes spec_axes(const Geometry& g, const FftPlan& f);
 qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,

@@ -13,14 +13,15 @@ template <typename R> struct CplxOf;
 template <> struct CplxOf<float> { using T = float2; };
 template <> struct CplxOf<double> { using T = double2; };
 
-// Loads of the field.  The read-only path (__ldg) is only valid while nothing
-// in the same launch writes the field; the batched kernel, whose CTAs read what
-// other CTAs wrote earlier in the launch (after an acquire), passes NC = false
-// and reads through L2.
+// Loads of the field.  The read-only path (__ldg, ld.global.nc) is only valid
+// while nothing in the same launch writes the field; the batched kernel, whose
+// CTAs read what other CTAs wrote earlier in the launch, passes NC = false and
+// uses ordinary loads, which the PTX memory model orders after the CTA's
+// acquire (thread 0's ld.acquire.gpu, then bar.sync).
 template <bool NC = true, typename C>
 __device__ __forceinline__ C ldg(const C* p) {
   if constexpr (NC) return __ldg(p);
-  else return __ldcg(p);  // L2 only: never a stale L1 line of another CTA's write
+  else return *p;  // ordinary load: ordered after the CTA's acquire by the memory model
 }
 
 // acc += (A + i B) * v  for A, B in {-1, 0, 1}: additions only.

@@ -43,6 +43,7 @@ struct AxesDev {
   int nparts[3];
   int part[3][3];
   int64_t len[3];
+  const double2* trig[3];
 };
 
 SpecAxes spec_axes(const Geometry& g, const FftPlan& f) {
@@ -57,6 +58,7 @@ SpecAxes spec_axes(const Geometry& g, const FftPlan& f) {
       a.nparts[ax] = f.axis[ax].nparts;
       for (int q = 0; q < 3; ++q) a.part[ax][q] = q < f.axis[ax].nparts ? f.axis[ax].part[q] : 1;
     }
+    a.trig[ax] = static_cast<const double2*>(f.trig[ax]);
   }
   return a;
 }
@@ -67,6 +69,7 @@ static AxesDev to_dev(const SpecAxes& a) {
     d.nparts[ax] = a.nparts[ax];
     d.len[ax] = a.len[ax];
     for (int q = 0; q < 3; ++q) d.part[ax][q] = a.part[ax][q];
+    d.trig[ax] = a.trig[ax];
   }
   return d;
 }
@@ -86,59 +89,36 @@ __device__ __forceinline__ int64_t freq_of(int64_t p, const AxesDev& a, int ax) 
   return k1 + A * (k1b + B1 * k2b);
 }
 
-// ---------------------------------------------------------------- symbols (FP64)
-// u_k, n~_k of Eqs. weyl1d / weyl2d / weyl3d; 2D at k_x = (k1 + k2)/2, k_y = (k1 - k2)/2.
-__device__ __forceinline__ void symbol64(int dim, double k1, double k2, double k3, double& u, double& nx,
-                                         double& ny, double& nz) {
+// ---------------------------------------------------------------- symbols
+// u_k, n~_k from the per-axis (cos, sin) tables: the frequency indices select
+// exact table angles (q = 1 adds pi to the x half-angle: the BCC wave vector q1).
+template <typename T>
+__device__ __forceinline__ void symbol_tab(int dim, const AxesDev& a, int64_t fx, int64_t fy, int64_t fz, int q,
+                                           T& u, T& nx, T& ny, T& nz) {
   if (dim == 1) {
-    double s, c;
-    sincos(k1, &s, &c);
-    u = c;
-    nx = 0.0;
-    ny = 0.0;
-    nz = s;
+    const double2 e = a.trig[0][fx];
+    u = (T)e.x;
+    nx = (T)0;
+    ny = (T)0;
+    nz = (T)e.y;
   } else if (dim == 2) {
-    double sx, cx, sy, cy;
-    sincos(0.5 * (k1 + k2), &sx, &cx);
-    sincos(0.5 * (k1 - k2), &sy, &cy);
+    const int64_t N2 = 2 * a.len[0];
+    int64_t dm = fx - fy;
+    if (dm < 0) dm += N2;
+    const double2 e1 = a.trig[0][fx + fy], e2 = a.trig[0][dm];
+    const T cx = (T)e1.x, sx = (T)e1.y, cy = (T)e2.x, sy = (T)e2.y;
     u = cx * cy;
     nx = sx * cy;
     ny = cx * sy;
     nz = sx * sy;
   } else {
-    double sx, cx, sy, cy, sz, cz;
-    sincos(k1, &sx, &cx);
-    sincos(k2, &sy, &cy);
-    sincos(k3, &sz, &cz);
-    u = cx * cy * cz + sx * sy * sz;
-    nx = sx * cy * cz - cx * sy * sz;
-    ny = cx * sy * cz + sx * cy * sz;
-    nz = cx * cy * sz - sx * sy * cz;
-  }
-}
-
-__device__ __forceinline__ void symbol32(int dim, float k1, float k2, float k3, float& u, float& nx, float& ny,
-                                         float& nz) {
-  if (dim == 1) {
-    float s, c;
-    sincosf(k1, &s, &c);
-    u = c;
-    nx = 0.f;
-    ny = 0.f;
-    nz = s;
-  } else if (dim == 2) {
-    float sx, cx, sy, cy;
-    sincosf(0.5f * (k1 + k2), &sx, &cx);
-    sincosf(0.5f * (k1 - k2), &sy, &cy);
-    u = cx * cy;
-    nx = sx * cy;
-    ny = cx * sy;
-    nz = sx * sy;
-  } else {
-    float sx, cx, sy, cy, sz, cz;
-    sincosf(k1, &sx, &cx);
-    sincosf(k2, &sy, &cy);
-    sincosf(k3, &sz, &cz);
+    const double2 ex = a.trig[0][fx], ey = a.trig[1][fy], ez = a.trig[2][fz];
+    T cx = (T)ex.x, sx = (T)ex.y;
+    if (q) {
+      cx = -cx;
+      sx = -sx;
+    }
+    const T cy = (T)ey.x, sy = (T)ey.y, cz = (T)ez.x, sz = (T)ez.y;
     u = cx * cy * cz + sx * sy * sz;
     nx = sx * cy * cz - cx * sy * sz;
     ny = cx * sy * cz + sx * cy * sz;
@@ -149,15 +129,11 @@ __device__ __forceinline__ void symbol32(int dim, float k1, float k2, float k3, 
 // Wave vector(s) of storage position (x, y, z): k_j = 2 pi f_j / len_j with f the
 // frequency index of the position; fsum = fx + fy + fz (BCC coset phase).
 __device__ __forceinline__ void wave_vectors(int dim, int64_t x, int64_t y, int64_t z, const AxesDev& a,
-                                             double (&k)[3], int64_t& fsum) {
-  const double TWO_PI = 6.283185307179586476925286766559;
-  const int64_t fx = freq_of(x, a, 0);
-  const int64_t fy = dim >= 2 ? freq_of(y, a, 1) : 0;
-  const int64_t fz = dim >= 3 ? freq_of(z, a, 2) : 0;
-  k[0] = TWO_PI * (double)fx / (double)a.len[0];
-  k[1] = dim >= 2 ? TWO_PI * (double)fy / (double)a.len[1] : 0.0;
-  k[2] = dim >= 3 ? TWO_PI * (double)fz / (double)a.len[2] : 0.0;
-  fsum = fx + fy + fz;
+                                             int64_t (&f)[3], int64_t& fsum) {
+  f[0] = freq_of(x, a, 0);
+  f[1] = dim >= 2 ? freq_of(y, a, 1) : 0;
+  f[2] = dim >= 3 ? freq_of(z, a, 2) : 0;
+  fsum = f[0] + f[1] + f[2];
 }
 
 // a = exp(i (k1 + k2 + k3)/2) = exp(i pi fsum / M) on the cubic coset grid.
@@ -189,19 +165,12 @@ __global__ void omega_kernel(int dim, AxesDev a, int64_t count, double n, double
   int64_t x, y, z;
   if (grid_pos(a, x, y, z)) {
     const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
-    double k[3];
-    int64_t fs;
-    wave_vectors(dim, x, y, z, a, k, fs);
+    int64_t f[3], fs;
+    wave_vectors(dim, x, y, z, a, f, fs);
     const int nq = dim == 3 ? 2 : 1;
     for (int q = 0; q < nq; ++q) {
-      double k1 = k[0], k2 = k[1], k3 = k[2];
-      if (dim == 3) {
-        k1 = 0.5 * k1 + (q ? 3.141592653589793238462643383279 : 0.0);
-        k2 *= 0.5;
-        k3 *= 0.5;
-      }
       double u, nx, ny, nz;
-      symbol64(dim, k1, k2, k3, u, nx, ny, nz);
+      symbol_tab<double>(dim, a, f[0], f[1], f[2], q, u, nx, ny, nz);
       const double sw = sqrt(m * m + n * n * (nx * nx + ny * ny + nz * nz));
       omega[idx * nq + q] = atan2(sw, n * u);
     }
@@ -275,28 +244,17 @@ __device__ __forceinline__ void apply_dt(typename Cx2<T>::t (&v)[S], T c, T s, T
 
 // G^ entries for one wave vector in precision T.
 template <typename T>
-__device__ __forceinline__ void ghat(int dim, double k1, double k2, double k3, double n, double m, T& gx, T& gy,
-                                     T& gz, T& gm) {
-  if (sizeof(T) == 8) {
-    double u, nx, ny, nz;
-    symbol64(dim, k1, k2, k3, u, nx, ny, nz);
-    const double sw = sqrt(m * m + n * n * (nx * nx + ny * ny + nz * nz));
-    const double inv = sw > 0.0 ? 1.0 / sw : 0.0;
-    gx = (T)(n * nx * inv);
-    gy = (T)(n * ny * inv);
-    gz = (T)(n * nz * inv);
-    gm = (T)(m * inv);
-  } else {
-    float u, nx, ny, nz;
-    symbol32(dim, (float)k1, (float)k2, (float)k3, u, nx, ny, nz);
-    const float nf = (float)n, mf = (float)m;
-    const float sw = sqrtf(mf * mf + nf * nf * (nx * nx + ny * ny + nz * nz));
-    const float inv = sw > 0.f ? 1.f / sw : 0.f;
-    gx = (T)(nf * nx * inv);
-    gy = (T)(nf * ny * inv);
-    gz = (T)(nf * nz * inv);
-    gm = (T)(mf * inv);
-  }
+__device__ __forceinline__ void ghat(int dim, const AxesDev& a, const int64_t (&f)[3], int q, double n, double m,
+                                     T& gx, T& gy, T& gz, T& gm) {
+  T u, nx, ny, nz;
+  symbol_tab<T>(dim, a, f[0], f[1], f[2], q, u, nx, ny, nz);
+  const T nf = (T)n, mf = (T)m;
+  const T sw = sqrt(mf * mf + nf * nf * (nx * nx + ny * ny + nz * nz));
+  const T inv = sw > (T)0 ? (T)1 / sw : (T)0;
+  gx = nf * nx * inv;
+  gy = nf * ny * inv;
+  gz = nf * nz * inv;
+  gm = mf * inv;
 }
 
 template <typename T, int S>
@@ -320,20 +278,18 @@ __global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t
                                                      const double* __restrict__ norm0,
                                                      typename Cx2<T>::t* __restrict__ data) {
   using V = typename Cx2<T>::t;
-  const double PI = 3.141592653589793238462643383279;
   // optional normalisation of the initial state, folded into the 1/|V| scale
   const T scale = norm0 ? (T)((double)scale_in / sqrt(norm0[0])) : scale_in;
   int64_t x, y, z;
   if (grid_pos(a, x, y, z)) {
     const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
-    double k[3];
-    int64_t fs;
-    wave_vectors(dim, x, y, z, a, k, fs);
+    int64_t f[3], fs;
+    wave_vectors(dim, x, y, z, a, f, fs);
     if (dim == 1) {
       V v[2] = {data[idx], data[count + idx]};
       T c, s, gx, gy, gz, gm;
       cs_of<T, 2>(omega[idx], tt, c, s);
-      ghat<T>(1, k[0], 0.0, 0.0, n, m, gx, gy, gz, gm);
+      ghat<T>(1, a, f, 0, n, m, gx, gy, gz, gm);
       apply_dt<T, 2>(v, c, s, (T)0, gx, gy, gz, gm);
       data[idx] = make_vec(v[0], scale);
       data[count + idx] = make_vec(v[1], scale);
@@ -343,7 +299,7 @@ __global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t
       for (int q = 0; q < 4; ++q) v[q] = data[q * count + idx];
       T c, s, gx, gy, gz, gm;
       cs_of<T, 4>(omega[idx], tt, c, s);
-      ghat<T>(2, k[0], k[1], 0.0, n, m, gx, gy, gz, gm);
+      ghat<T>(2, a, f, 0, n, m, gx, gy, gz, gm);
       apply_dt<T, 4>(v, c, s, (T)0, gx, gy, gz, gm);
 #pragma unroll
       for (int q = 0; q < 4; ++q) data[q * count + idx] = make_vec(v[q], scale);
@@ -371,13 +327,13 @@ __global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t
       {
         T c, s, gx, gy, gz, gm;
         cs_of<T, 4>(omega[2 * idx], tt, c, s);
-        ghat<T>(3, 0.5 * k[0], 0.5 * k[1], 0.5 * k[2], n, m, gx, gy, gz, gm);
+        ghat<T>(3, a, f, 0, n, m, gx, gy, gz, gm);
         apply_dt<T, 4>(c0, c, s, (T)0, gx, gy, gz, gm);
       }
       {
         T c, s, gx, gy, gz, gm;
         cs_of<T, 4>(omega[2 * idx + 1], tt, c, s);
-        ghat<T>(3, 0.5 * k[0] + PI, 0.5 * k[1], 0.5 * k[2], n, m, gx, gy, gz, gm);
+        ghat<T>(3, a, f, 1, n, m, gx, gy, gz, gm);
         apply_dt<T, 4>(c1, c, s, (T)0, gx, gy, gz, gm);
       }
 #pragma unroll
@@ -402,15 +358,13 @@ __global__ void __launch_bounds__(256) weights_kernel(int dim, AxesDev a, int64_
                                                       const typename Cx2<T>::t* __restrict__ data,
                                                       double* __restrict__ partials) {
   using V = typename Cx2<T>::t;
-  const double PI = 3.141592653589793238462643383279;
   double acc[2] = {0.0, 0.0};
   const int64_t nx = a.len[0], ny = a.len[1];
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x = idx % nx, y = (idx / nx) % ny, z = idx / (nx * ny);
-    double k[3];
-    int64_t fs;
-    wave_vectors(dim, x, y, z, a, k, fs);
+    int64_t f[3], fs;
+    wave_vectors(dim, x, y, z, a, f, fs);
     const int S = dim == 1 ? 2 : 4;
     const int nq = dim == 3 ? 2 : 1;
     V vq[2][4];
@@ -433,10 +387,7 @@ __global__ void __launch_bounds__(256) weights_kernel(int dim, AxesDev a, int64_
     }
     for (int j = 0; j < nq; ++j) {
       T gx, gy, gz, gm;
-      if (dim == 3)
-        ghat<T>(3, 0.5 * k[0] + (j ? PI : 0.0), 0.5 * k[1], 0.5 * k[2], n, m, gx, gy, gz, gm);
-      else
-        ghat<T>(dim, k[0], k[1], 0.0, n, m, gx, gy, gz, gm);
+      ghat<T>(dim, a, f, dim == 3 ? j : 0, n, m, gx, gy, gz, gm);
       // cos = 1, sin = 1 turns apply_dt into v - i G^ v; recover G^ v from it
       T nrm = 0, gdot = 0;
       if (S == 2) {
