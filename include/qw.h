@@ -57,13 +57,15 @@ typedef enum { QW_C64 = 0, QW_C128 = 1 } qw_dtype;
  * data movement.  PLAIN: any geometry and dtype, one thread per site.  VEC: BCC,
  * complex64, N/2 % 64 == 0; two cells per thread, 16-byte loads.  TMA: BCC,
  * complex64, N/2 % 64 == 0; z-marching CTAs with TMA-staged shared-memory tiles.
- * AUTO picks, at plan creation, the fastest variant measured by
- * qw_plan_autotune, else the default order TMA > VEC > PLAIN. */
+ * TMA2: as TMA with two steps fused per pass over HBM (temporal fusion; an odd
+ * remaining step runs as TMA).  AUTO restores the default order
+ * TMA2 > TMA > VEC > PLAIN; qw_plan_autotune measures and keeps the fastest. */
 typedef enum {
   QW_STENCIL_AUTO = 0,
   QW_STENCIL_PLAIN = 1,
   QW_STENCIL_VEC = 2,
-  QW_STENCIL_TMA = 3
+  QW_STENCIL_TMA = 3,
+  QW_STENCIL_TMA2 = 4
 } qw_stencil_variant;
 
 typedef struct qw_plan_s* qw_plan;
@@ -112,6 +114,13 @@ qw_status qw_plan_set_stencil(qw_plan plan, int variant);
 
 /* The stencil variant qw_step currently uses (never QW_STENCIL_AUTO); -1 for null. */
 int qw_plan_get_stencil(qw_plan plan);
+
+/* Autotuner of the stencil: times every variant that supports the plan (fusion
+ * depth 1 or 2, data movement PLAIN / VEC / TMA) for 8 steps on a temporary
+ * field (allocated and freed here; the caller's fields are not touched) and keeps
+ * the fastest; *best_rate (optional) receives its site-steps/s.  Synchronous.
+ * Errors: QW_EINVAL, QW_ENOMEM, QW_ECUDA, QW_ETIMEOUT. */
+qw_status qw_plan_autotune(qw_plan plan, void* stream, double* best_rate);
 
 /* Advance psi_dev in place by `nsteps` >= 0 applications of the update rule
  * (Eq. upd-rule; the plain position-space form of Sec. 4) with the plan's

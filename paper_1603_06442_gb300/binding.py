@@ -14,8 +14,8 @@ LIB_PATH = os.path.join(PKG, "libqw.so")
 
 QW_OK, QW_EINVAL, QW_ENOMEM, QW_ECUDA, QW_ETIMEOUT, QW_EAGAIN, QW_EBUSY, QW_ENOTFOUND = range(8)
 QW_C64, QW_C128 = 0, 1
-QW_STENCIL_AUTO, QW_STENCIL_PLAIN, QW_STENCIL_VEC, QW_STENCIL_TMA = 0, 1, 2, 3
-STENCILS = {"auto": 0, "plain": 1, "vec": 2, "tma": 3}
+QW_STENCIL_AUTO, QW_STENCIL_PLAIN, QW_STENCIL_VEC, QW_STENCIL_TMA, QW_STENCIL_TMA2 = 0, 1, 2, 3, 4
+STENCILS = {"auto": 0, "plain": 1, "vec": 2, "tma": 3, "tma2": 4}
 STATUS_NAMES = {0: "QW_OK", 1: "QW_EINVAL", 2: "QW_ENOMEM", 3: "QW_ECUDA", 4: "QW_ETIMEOUT",
                 5: "QW_EAGAIN", 6: "QW_EBUSY", 7: "QW_ENOTFOUND"}
 
@@ -65,6 +65,7 @@ _SIGS = {
     "qw_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "qw_plan_set_stencil": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "qw_plan_get_stencil": (ctypes.c_int, [ctypes.c_void_p]),
+    "qw_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "qw_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "qw_plan_prepare_spectral": (ctypes.c_int, [ctypes.c_void_p]),
     "qw_prepare_packet": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -256,6 +257,12 @@ def qw_step_static(dim, N, mass, dtype, psi, nsteps, stream=None):
     _check(load().qw_step_static(int(dim), int(N), float(mass), dt, _ptr(psi), int(nsteps), _stream(stream)))
 
 
+def qw_plan_autotune(plan, stream=None):
+    r = ctypes.c_double()
+    _check(load().qw_plan_autotune(plan, _stream(stream), ctypes.byref(r)))
+    return r.value
+
+
 def qw_sync(plan, stream=None):
     _check(load().qw_sync(plan, _stream(stream)))
 
@@ -381,6 +388,9 @@ class Plan:
     def step(self, psi, nsteps, stream=None):
         self.check_field(psi)
         qw_step(self.handle, psi, nsteps, stream)
+
+    def autotune(self, stream=None):
+        return qw_plan_autotune(self.handle, stream)
 
     def set_stencil(self, variant):
         qw_plan_set_stencil(self.handle, variant)

@@ -53,6 +53,7 @@ bool make_geometry(int dim, int64_t N, Geometry* g) {
 }
 
 static int default_stencil(const qw_plan_s* p) {
+  if (stencil_supported(p->g, p->dtype, QW_STENCIL_TMA2)) return QW_STENCIL_TMA2;
   if (stencil_supported(p->g, p->dtype, QW_STENCIL_TMA)) return QW_STENCIL_TMA;
   if (stencil_supported(p->g, p->dtype, QW_STENCIL_VEC)) return QW_STENCIL_VEC;
   return QW_STENCIL_PLAIN;
@@ -151,16 +152,23 @@ qw_status qw_plan_create(int dim, int64_t N, double mass, qw_dtype dtype, qw_pla
   if (tma_step_supported(g) && dtype == QW_C64) {
     int nsm = 0;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
-    std::vector<int4> items = tma_item_table(g, 2 * nsm);
+    std::vector<int4> items = tma_item_table(g, 2 * nsm, 4);
     if (e == cudaSuccess) e = cudaMalloc(&p->tma_items, items.size() * sizeof(int4));
     if (e == cudaSuccess)
       e = cudaMemcpy(p->tma_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    p->tma_nitems = (int)items.size();
+    if (e == cudaSuccess && tma2_step_supported(g)) {
+      std::vector<int4> items2 = tma_item_table(g, nsm, 8);
+      e = cudaMalloc(&p->tma2_items, items2.size() * sizeof(int4));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(p->tma2_items, items2.data(), items2.size() * sizeof(int4), cudaMemcpyHostToDevice);
+      p->tma2_nitems = (int)items2.size();
+    }
     if (e != cudaSuccess) {
-      st = cuda_fail(e, "qw_plan_create: TMA item table");
+      st = cuda_fail(e, "qw_plan_create: TMA item tables");
       qw_plan_destroy(p);
       return st;
     }
-    p->tma_nitems = (int)items.size();
   }
   p->stencil = default_stencil(p);
   *out = p;
@@ -176,6 +184,7 @@ qw_status qw_plan_destroy(qw_plan p) {
   if (p->red_host) cudaFreeHost(p->red_host);
   if (p->dev_flags) cudaFree(p->dev_flags);
   if (p->tma_items) cudaFree(p->tma_items);
+  if (p->tma2_items) cudaFree(p->tma2_items);
   fft_plan_destroy(&p->fft);
   if (p->omega) cudaFree(p->omega);
   if (p->spec_partials) cudaFree(p->spec_partials);
@@ -198,16 +207,23 @@ qw_status qw_step(qw_plan p, void* psi, int64_t nsteps, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* cur = psi;
   void* nxt = p->scratch;
-  for (int64_t i = 0; i < nsteps; ++i) {
-    if (p->stencil == QW_STENCIL_TMA)
+  for (int64_t i = 0; i < nsteps;) {
+    int done = 1;
+    if (p->stencil == QW_STENCIL_TMA2 && nsteps - i >= 2) {
+      st = launch_step_tma2(p->g, p->n, p->mass, cur, nxt, p->tma2_items, p->tma2_nitems, p->dev_flags,
+                            p->dev_flags + 1, s);
+      done = 2;
+    } else if (p->stencil == QW_STENCIL_TMA || p->stencil == QW_STENCIL_TMA2) {
       st = launch_step_tma(p->g, p->n, p->mass, cur, nxt, p->tma_items, p->tma_nitems, p->dev_flags,
                            p->dev_flags + 1, s);
-    else
+    } else {
       st = launch_step(p->g, p->dtype, p->stencil, p->n, p->mass, cur, nxt, s);
+    }
     if (st != QW_OK) return st;
     void* t = cur;
     cur = nxt;
     nxt = t;
+    i += done;
   }
   if (cur != psi)
     QW_CHECK_CUDA(cudaMemcpyAsync(psi, cur, (size_t)p->g.elems * p->elem_bytes, cudaMemcpyDeviceToDevice, s));
@@ -270,6 +286,54 @@ qw_status qw_prepare_packet(qw_plan p, void* psi, const double* x0, double sigma
   qw_status st = use_device(p);
   if (st != QW_OK) return st;
   return launch_packet(p->g, p->dtype, x0, sigma, k0, chi, psi, static_cast<cudaStream_t>(stream));
+}
+
+qw_status qw_plan_autotune(qw_plan p, void* stream, double* best_rate) {
+  if (!p) {
+    set_error("qw_plan_autotune: null plan");
+    return QW_EINVAL;
+  }
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* tmp = nullptr;
+  const size_t bytes = (size_t)p->g.elems * p->elem_bytes;
+  QW_CHECK_CUDA(cudaMalloc(&tmp, bytes));
+  QW_CHECK_CUDA(cudaMemsetAsync(tmp, 0, bytes, s));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int saved = p->stencil;
+  int best = saved;
+  double best_r = -1.0;
+  const int variants[] = {QW_STENCIL_PLAIN, QW_STENCIL_VEC, QW_STENCIL_TMA, QW_STENCIL_TMA2};
+  const int64_t steps = 8;
+  for (int v : variants) {
+    if (!stencil_supported(p->g, p->dtype, v)) continue;
+    p->stencil = v;
+    st = qw_step(p, tmp, 2, s);  // warm-up
+    if (st != QW_OK) break;
+    cudaEventRecord(e0, s);
+    st = qw_step(p, tmp, steps, s);
+    cudaEventRecord(e1, s);
+    if (st != QW_OK) break;
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double r = (double)p->g.sites * steps / (ms * 1e-3);
+    if (r > best_r) {
+      best_r = r;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  p->stencil = (st == QW_OK) ? best : saved;
+  if (best_rate) *best_rate = best_r;
+  if (st != QW_OK) return st;
+  return check_flags(p, s);
 }
 
 qw_status qw_sync(qw_plan p, void* stream) {

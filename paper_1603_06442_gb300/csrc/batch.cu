@@ -9,10 +9,14 @@
 //     groups follow one another, so a group's walks are evolved while cached;
 //   * inside a group, rounds come in order and each round lists the tiles of
 //     every walk still running (walks sorted by length, so that set is a prefix).
-// Before working on round s of walk w a CTA waits (bounded) until all tiles of
-// round s-1 of that walk are counted done (release/acquire on a per-walk
-// counter).  Every item waits only on items earlier in the order, and an item
-// is only claimed by a running CTA, so the launch always makes progress.
+// Before working on round s of tile i of walk w a CTA waits (bounded) until the
+// tiles within the stencil's reach of tile i (cyclically, the box is periodic)
+// have finished round s-1: per-tile round counters, release/acquire.  That
+// covers both the data tile i reads (written in round s-1) and the buffer it
+// overwrites (read by its neighbours in round s-1), and lets consecutive rounds
+// of a walk overlap as a wavefront instead of meeting at a barrier.  Every item
+// waits only on items earlier in the order, and an item is only claimed by a
+// running CTA, so the launch always makes progress.
 // The launch (counter resets + kernel) is captured once into a CUDA graph and
 // replayed by every qw_batch_run.
 #include <cuda/atomic>
@@ -31,6 +35,8 @@ namespace qw {
 struct BatchWalk {
   int dim;
   int ntiles;
+  int reach;              // tiles on each side a tile depends on (cyclic)
+  int64_t tile_base;      // first entry of this walk in the per-tile round counters
   int64_t nx;             // row length (N in 1D/2D, M = N/2 on the BCC lattice)
   int64_t ny;             // rows per plane layer (1 in 1D, N in 2D, M in 3D)
   int64_t rows;           // rows of one step (1, N, 2 M^2)
@@ -74,7 +80,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchWalk* __restrict_
                                                     const BatchGroup* __restrict__ groups, int ngroups,
                                                     const int64_t* __restrict__ tile_prefix,
                                                     const int64_t* __restrict__ round_prefix, int64_t total_items,
-                                                    unsigned long long* __restrict__ done, BatchCtl* __restrict__ ctl) {
+                                                    unsigned int* __restrict__ done, BatchCtl* __restrict__ ctl) {
   __shared__ int64_t s_item;
   __shared__ int s_abort;
   const int tid = threadIdx.x;
@@ -99,20 +105,25 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchWalk* __restrict_
     const int tile = (int)(off - tp[wl]);
     const int wi = G.first + wl;
     const BatchWalk W = walks[wi];
-    // ---- wait for round s-1 of this walk
+    // ---- wait for round s-1 of the tiles within reach
     if (tid == 0 && s > 0) {
-      cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> d(done[wi]);
-      const unsigned long long target = (unsigned long long)s * (unsigned long long)W.ntiles;
+      const int span = 2 * W.reach + 1 >= W.ntiles ? W.ntiles : 2 * W.reach + 1;
+      const int first = 2 * W.reach + 1 >= W.ntiles ? 0 : tile - W.reach;
       long long spins = 0;
-      while (d.load(cuda::memory_order_acquire) < target) {
-        if (++spins > kBatchSpin ||
-            cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).load(cuda::memory_order_relaxed)) {
-          cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).store(1, cuda::memory_order_relaxed);
-          atomicExch(&ctl->err, 1);
-          s_abort = 1;
-          break;
+      for (int d = 0; d < span && !s_abort; ++d) {
+        int j = first + d;
+        j = j < 0 ? j + W.ntiles : (j >= W.ntiles ? j - W.ntiles : j);
+        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> c(done[W.tile_base + j]);
+        while (c.load(cuda::memory_order_acquire) < (unsigned int)s) {
+          if (++spins > kBatchSpin ||
+              cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).load(cuda::memory_order_relaxed)) {
+            cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).store(1, cuda::memory_order_relaxed);
+            atomicExch(&ctl->err, 1);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(64);
         }
-        __nanosleep(64);
       }
     }
     __syncthreads();
@@ -156,8 +167,8 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchWalk* __restrict_
     }
     __syncthreads();
     if (tid == 0)
-      cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>(done[wi]).fetch_add(1ull,
-                                                                                      cuda::memory_order_release);
+      cuda::atomic_ref<unsigned int, cuda::thread_scope_device>(done[W.tile_base + tile])
+          .store((unsigned int)(s + 1), cuda::memory_order_release);
   }
 }
 
@@ -175,7 +186,8 @@ struct qw_batch_s {
   BatchGroup* d_groups = nullptr;
   int64_t* d_tiles = nullptr;
   int64_t* d_rounds = nullptr;
-  unsigned long long* d_done = nullptr;
+  unsigned int* d_done = nullptr;
+  int64_t ndone = 0;
   BatchCtl* d_ctl = nullptr;
   int ngroups = 0;
   int64_t total_items = 0;
@@ -241,6 +253,7 @@ static qw_status build_schedule(qw_batch_s* b) {
   std::vector<int64_t> tiles, rounds;
   b->order.clear();
   int64_t item0 = 0;
+  int64_t ndone_acc = 0;
   for (auto& gw : grp) {
     // inside a group: longest walks first, so the walks alive at round s are a prefix
     std::stable_sort(gw.begin(), gw.end(), [&](int a, int c) { return b->desc[a].t > b->desc[c].t; });
@@ -263,6 +276,12 @@ static qw_status build_schedule(qw_batch_s* b) {
       W.rows = g.dim == 1 ? 1 : (g.dim == 2 ? g.ny : 2 * g.ny * g.nz);
       W.rows_per_tile = std::max<int64_t>(1, b->tile_sites / g.nx);
       W.ntiles = (int)((W.rows + W.rows_per_tile - 1) / W.rows_per_tile);
+      // rows a site update reaches: 1 (2D), 2M + 3 (BCC rows interleave the cosets), 0 (1D: one row)
+      const int64_t reach_rows = g.dim == 1 ? 0 : (g.dim == 2 ? 1 : 2 * g.nx + 3);
+      // (+1 when the last tile is short: a cyclic neighbour window then needs one more tile)
+      W.reach = (int)((reach_rows + W.rows_per_tile - 1) / W.rows_per_tile) + (W.rows % W.rows_per_tile ? 1 : 0);
+      W.tile_base = ndone_acc;
+      ndone_acc += W.ntiles;
       W.t = d.t;
       W.rounds = d.t + (d.t & 1);
       W.vol = g.vol;
@@ -304,7 +323,8 @@ static qw_status build_schedule(qw_batch_s* b) {
   QW_CHECK_CUDA(cudaMalloc(&b->d_groups, groups.size() * sizeof(BatchGroup)));
   QW_CHECK_CUDA(cudaMalloc(&b->d_tiles, tiles.size() * sizeof(int64_t)));
   QW_CHECK_CUDA(cudaMalloc(&b->d_rounds, rounds.size() * sizeof(int64_t)));
-  QW_CHECK_CUDA(cudaMalloc(&b->d_done, n * sizeof(unsigned long long)));
+  b->ndone = ndone_acc;
+  QW_CHECK_CUDA(cudaMalloc(&b->d_done, std::max<int64_t>(1, ndone_acc) * sizeof(unsigned int)));
   QW_CHECK_CUDA(cudaMemcpy(b->d_walks, walks.data(), walks.size() * sizeof(BatchWalk), cudaMemcpyHostToDevice));
   QW_CHECK_CUDA(cudaMemcpy(b->d_groups, groups.data(), groups.size() * sizeof(BatchGroup), cudaMemcpyHostToDevice));
   QW_CHECK_CUDA(cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
@@ -317,7 +337,7 @@ static qw_status build_schedule(qw_batch_s* b) {
 }
 
 static qw_status launch_batch(qw_batch_s* b, cudaStream_t s) {
-  QW_CHECK_CUDA(cudaMemsetAsync(b->d_done, 0, b->n * sizeof(unsigned long long), s));
+  QW_CHECK_CUDA(cudaMemsetAsync(b->d_done, 0, std::max<int64_t>(1, b->ndone) * sizeof(unsigned int), s));
   QW_CHECK_CUDA(cudaMemsetAsync(b->d_ctl, 0, sizeof(BatchCtl), s));
   batch_kernel<<<b->grid, 256, 0, s>>>(b->d_walks, b->d_groups, b->ngroups, b->d_tiles, b->d_rounds,
                                        b->total_items, b->d_done, b->d_ctl);

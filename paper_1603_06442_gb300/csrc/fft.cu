@@ -638,13 +638,18 @@ static qw_status trig_tables(FftPlan* f, const Geometry& g) {
       period = 2 * ext[ax];
     }
     std::vector<double2> h(len);
+    std::vector<float2> h32(len);
     for (int64_t q = 0; q < len; ++q) {
       const double ang = 2.0 * M_PI * (double)(q % period) / (double)period;
       h[q].x = std::cos(ang);
       h[q].y = std::sin(ang);
+      h32[q].x = (float)h[q].x;
+      h32[q].y = (float)h[q].y;
     }
     QW_CHECK_CUDA(cudaMalloc(&f->trig[ax], len * sizeof(double2)));
     QW_CHECK_CUDA(cudaMemcpy(f->trig[ax], h.data(), len * sizeof(double2), cudaMemcpyHostToDevice));
+    QW_CHECK_CUDA(cudaMalloc(&f->trig32[ax], len * sizeof(float2)));
+    QW_CHECK_CUDA(cudaMemcpy(f->trig32[ax], h32.data(), len * sizeof(float2), cudaMemcpyHostToDevice));
   }
   return QW_OK;
 }
@@ -660,7 +665,9 @@ qw_status fft_plan_create(FftPlan* f, const Geometry& g, qw_dtype dt) {
 void fft_plan_destroy(FftPlan* f) {
   for (int a = 0; a < 3; ++a) {
     if (f->trig[a]) cudaFree(f->trig[a]);
+    if (f->trig32[a]) cudaFree(f->trig32[a]);
     f->trig[a] = nullptr;
+    f->trig32[a] = nullptr;
   }
   for (int i = 0; i < f->npass; ++i) {
     if (f->pass[i].tw_line) cudaFree(f->pass[i].tw_line);

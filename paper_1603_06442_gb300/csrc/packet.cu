@@ -24,22 +24,35 @@ __global__ void __launch_bounds__(256) packet_kernel(Geometry g, PacketArgs pa, 
   const double N = (double)g.N;
   const double scale = g.dim == 3 ? 2.0 : 1.0;
   const double pos[3] = {scale * (double)x + c, scale * (double)y + c, scale * (double)z + c};
-  double r2 = 0.0, ph = 0.0;
+  // displacements are exact in T (integers and half-integers below 2^24);
+  // the envelope and phase are evaluated in the field's precision
+  T r2 = 0, ph = 0;
   for (int j = 0; j < g.dim; ++j) {
     double d = pos[j] - pa.x0[j] + 0.5 * N;
     d = d - N * floor(d / N) - 0.5 * N;  // minimum image in [-N/2, N/2)
-    r2 += d * d;
-    ph += pa.k0[j] * d;
+    const T dt = (T)d;
+    r2 += dt * dt;
+    ph += (T)pa.k0[j] * dt;
   }
-  double sp, cp;
-  sincos(ph, &sp, &cp);
-  const double env = exp(-r2 * pa.inv4s2);
+  T sp, cp;
+  if (sizeof(T) == 8) {
+    double a, b;
+    sincos((double)ph, &a, &b);
+    sp = (T)a;
+    cp = (T)b;
+  } else {
+    float a, b;
+    sincosf((float)ph, &a, &b);
+    sp = (T)a;
+    cp = (T)b;
+  }
+  const T env = (sizeof(T) == 8) ? (T)exp(-(double)r2 * pa.inv4s2) : (T)expf(-(float)r2 * (float)pa.inv4s2);
   const int64_t cell = (z * g.ny + y) * g.nx + x;
   for (int q = 0; q < g.s; ++q) {
-    const double cr = pa.chi[2 * q], ci = pa.chi[2 * q + 1];
+    const T cr = (T)pa.chi[2 * q], ci = (T)pa.chi[2 * q + 1];
     V v;
-    v.x = (T)(env * (cp * cr - sp * ci));
-    v.y = (T)(env * (cp * ci + sp * cr));
+    v.x = env * (cp * cr - sp * ci);
+    v.y = env * (cp * ci + sp * cr);
     psi[((int64_t)c * g.s + q) * g.vol + cell] = v;
   }
 }

@@ -51,6 +51,7 @@ struct FftPlan {
   //   dim 1: 2 pi f / N (f < N);  dim 2: pi q / N (q < 2N, for k1 +- k2 halves);
   //   dim 3: pi f / M (f < M, the half wave vector kappa / 2 of each axis)
   void* trig[3] = {nullptr, nullptr, nullptr};
+  void* trig32[3] = {nullptr, nullptr, nullptr};  // the same tables as float2 (complex64 kernels)
 };
 
 bool fft_size_ok(int64_t L);

@@ -69,8 +69,13 @@ bool stencil_supported(const Geometry& g, qw_dtype dt, int variant);
 qw_status launch_step(const Geometry& g, qw_dtype dt, int variant, double n, double m, const void* in, void* out,
                       cudaStream_t st);
 bool tma_step_supported(const Geometry& g);
-// Work items {tile, z_begin, z_end, 0} of the TMA stencil for `resident` CTAs.
-std::vector<int4> tma_item_table(const Geometry& g, int resident);
+// Work items {tile, z_begin, z_end, 0} of the TMA stencils (tiles of 64 x ty cells)
+// for `resident` CTAs.
+std::vector<int4> tma_item_table(const Geometry& g, int resident, int ty);
+bool tma2_step_supported(const Geometry& g);
+// Two fused steps out = U^2 in (TMA, tiles of 64 x 8 cells).
+qw_status launch_step_tma2(const Geometry& g, double n, double m, const void* in, void* out, const int4* items,
+                           int nitems, int* err, int* next_item, cudaStream_t st);
 qw_status launch_step_tma(const Geometry& g, double n, double m, const void* in, void* out, const int4* items,
                           int nitems, int* err, int* next_item, cudaStream_t st);
 
@@ -115,6 +120,7 @@ struct SpecAxes {  // digit split of each axis (storage order -> frequency) and 
   int part[3][3];
   int64_t len[3];
   const double2* trig[3];
+  const float2* trig32[3];
 };
 SpecAxes spec_axes(const Geometry& g, const FftPlan& f);
 qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,
@@ -150,6 +156,8 @@ struct qw_plan_s {
   int* dev_flags;       // [0] error word of bounded device waits, [1] work counter
   int4* tma_items;      // work-item table of the TMA stencil (device), or null
   int tma_nitems;
+  int4* tma2_items;     // work-item table of the two-step TMA stencil, or null
+  int tma2_nitems;
   // spectral path (allocated by the first spectral call or qw_plan_prepare_spectral)
   bool spec_ready;
   qw::FftPlan fft;

@@ -44,6 +44,7 @@ struct AxesDev {
   int part[3][3];
   int64_t len[3];
   const double2* trig[3];
+  const float2* trig32[3];
 };
 
 SpecAxes spec_axes(const Geometry& g, const FftPlan& f) {
@@ -59,6 +60,7 @@ SpecAxes spec_axes(const Geometry& g, const FftPlan& f) {
       for (int q = 0; q < 3; ++q) a.part[ax][q] = q < f.axis[ax].nparts ? f.axis[ax].part[q] : 1;
     }
     a.trig[ax] = static_cast<const double2*>(f.trig[ax]);
+    a.trig32[ax] = static_cast<const float2*>(f.trig32[ax]);
   }
   return a;
 }
@@ -70,6 +72,7 @@ static AxesDev to_dev(const SpecAxes& a) {
     d.len[ax] = a.len[ax];
     for (int q = 0; q < 3; ++q) d.part[ax][q] = a.part[ax][q];
     d.trig[ax] = a.trig[ax];
+    d.trig32[ax] = a.trig32[ax];
   }
   return d;
 }
@@ -93,32 +96,48 @@ __device__ __forceinline__ int64_t freq_of(int64_t p, const AxesDev& a, int ax) 
 // u_k, n~_k from the per-axis (cos, sin) tables: the frequency indices select
 // exact table angles (q = 1 adds pi to the x half-angle: the BCC wave vector q1).
 template <typename T>
+__device__ __forceinline__ void tab(const AxesDev& a, int ax, int64_t i, T& c, T& s) {
+  if (sizeof(T) == 8) {
+    const double2 e = a.trig[ax][i];
+    c = (T)e.x;
+    s = (T)e.y;
+  } else {
+    const float2 e = a.trig32[ax][i];
+    c = (T)e.x;
+    s = (T)e.y;
+  }
+}
+
+template <typename T>
 __device__ __forceinline__ void symbol_tab(int dim, const AxesDev& a, int64_t fx, int64_t fy, int64_t fz, int q,
                                            T& u, T& nx, T& ny, T& nz) {
   if (dim == 1) {
-    const double2 e = a.trig[0][fx];
-    u = (T)e.x;
+    T ec, es;
+    tab<T>(a, 0, fx, ec, es);
+    u = ec;
     nx = (T)0;
     ny = (T)0;
-    nz = (T)e.y;
+    nz = es;
   } else if (dim == 2) {
     const int64_t N2 = 2 * a.len[0];
     int64_t dm = fx - fy;
     if (dm < 0) dm += N2;
-    const double2 e1 = a.trig[0][fx + fy], e2 = a.trig[0][dm];
-    const T cx = (T)e1.x, sx = (T)e1.y, cy = (T)e2.x, sy = (T)e2.y;
+    T cx, sx, cy, sy;
+    tab<T>(a, 0, fx + fy, cx, sx);
+    tab<T>(a, 0, dm, cy, sy);
     u = cx * cy;
     nx = sx * cy;
     ny = cx * sy;
     nz = sx * sy;
   } else {
-    const double2 ex = a.trig[0][fx], ey = a.trig[1][fy], ez = a.trig[2][fz];
-    T cx = (T)ex.x, sx = (T)ex.y;
+    T cx, sx, cy, sy, cz, sz;
+    tab<T>(a, 0, fx, cx, sx);
+    tab<T>(a, 1, fy, cy, sy);
+    tab<T>(a, 2, fz, cz, sz);
     if (q) {
       cx = -cx;
       sx = -sx;
     }
-    const T cy = (T)ey.x, sy = (T)ey.y, cz = (T)ez.x, sz = (T)ez.y;
     u = cx * cy * cz + sx * sy * sz;
     nx = sx * cy * cz - cx * sy * sz;
     ny = cx * sy * cz + sx * cy * sz;
@@ -188,14 +207,15 @@ __device__ __forceinline__ void phase(double omega, double tt, double& c, double
   r = fma(-kq, TWO_PI_LO, r) + e;
   sincos(r, &s, &c);
 }
+// complex64 path: same FP64 reduction without the product's low part (about
+// 1e-16 * omega t, far below the FP32 resolution of the reduced phase)
 __device__ __forceinline__ void phase32(double omega, double tt, float& c, float& s) {
   const double TWO_PI_HI = 6.283185307179586232e+00;
   const double TWO_PI_LO = 2.449293598294706e-16;
   const double p = omega * tt;
-  const double e = fma(omega, tt, -p);
   const double kq = rint(p * 0.15915494309189533577);
   double r = fma(-kq, TWO_PI_HI, p);
-  r = fma(-kq, TWO_PI_LO, r) + e;
+  r = fma(-kq, TWO_PI_LO, r);
   sincosf((float)r, &s, &c);
 }
 

@@ -231,6 +231,7 @@ bool stencil_supported(const Geometry& g, qw_dtype dt, int variant) {
     case QW_STENCIL_PLAIN: return true;
     case QW_STENCIL_VEC: return g.dim == 3 && dt == QW_C64 && g.nx % 64 == 0;
     case QW_STENCIL_TMA: return dt == QW_C64 && tma_step_supported(g);  // item table built at plan creation
+    case QW_STENCIL_TMA2: return dt == QW_C64 && tma2_step_supported(g);
     default: return false;
   }
 }

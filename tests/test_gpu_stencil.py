@@ -69,8 +69,8 @@ def test_stencil_parity(qb, dim, N, dtype, t):
     assert rel_l2(got, exp) <= tol(dtype, t)
 
 
-@pytest.mark.parametrize("variant", ["plain", "vec", "tma"])
-@pytest.mark.parametrize("N,t", [(128, 1), (128, 6), (256, 3)])
+@pytest.mark.parametrize("variant", ["plain", "vec", "tma", "tma2"])
+@pytest.mark.parametrize("N,t", [(128, 1), (128, 6), (128, 7), (256, 3), (256, 10)])
 def test_bcc_c64_variants(qb, variant, N, t):
     """Every complex64 BCC kernel variant against the oracle (N/2 % 64 == 0 boxes)."""
     m = 0.37
@@ -150,7 +150,8 @@ def _subbox_oracle(a_dev_layout, N, m, t, centre):
     return psi[:, L // 2, L // 2, L // 2]
 
 
-@pytest.mark.parametrize("dtype,variant", [("c64", "tma"), ("c64", "vec"), ("c64", "plain"), ("c128", "plain")])
+@pytest.mark.parametrize("dtype,variant", [("c64", "tma2"), ("c64", "tma"), ("c64", "vec"), ("c64", "plain"),
+                                           ("c128", "plain")])
 def test_bcc512_sampled(qb, dtype, variant):
     """Full-size BCC box N = 512 (33,554,432 sites): sampled sites against sub-box oracle runs."""
     N, m, t = 512, 0.3, 6
@@ -187,6 +188,19 @@ def test_position_observables(qb, dim, N, dtype):
         assert abs(obs["x_mean"][j] - exp[j]) <= rtol * N, (j, obs["x_mean"][j], exp[j])
     for j in range(dim, 3):
         assert obs["x_mean"][j] == 0.0
+
+
+def test_autotune_picks_a_supported_variant(qb):
+    plan = qb.Plan(3, 128, 0.1, "c64")
+    rate = plan.autotune()
+    assert rate > 0 and plan.stencil in (1, 2, 3, 4)
+    a = inputs.random_field(3, 128, seed=8)
+    x = to_dev(a, "c64")
+    plan.step(x, 5)
+    plan.sync()
+    exp = walk.to_device(3, 128, walk.step(3, 0.1, walk.from_device(3, 128, a), 5))
+    assert rel_l2(x.cpu().numpy().astype(np.complex128), exp) <= tol("c64", 5)
+    plan.close()
 
 
 def test_step_rejects_bad_arguments(qb):
