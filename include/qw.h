@@ -59,7 +59,7 @@ typedef enum { QW_C64 = 0, QW_C128 = 1 } qw_dtype;
  * complex64, N/2 % 64 == 0; z-marching CTAs with TMA-staged shared-memory tiles.
  * TMA2: as TMA with two steps fused per pass over HBM (temporal fusion; an odd
  * remaining step runs as TMA).  AUTO restores the default order
- * TMA2 > TMA > VEC > PLAIN; qw_plan_autotune measures and keeps the fastest. */
+ * TMA > TMA2 > VEC > PLAIN; qw_plan_autotune measures and keeps the fastest. */
 typedef enum {
   QW_STENCIL_AUTO = 0,
   QW_STENCIL_PLAIN = 1,
@@ -225,9 +225,8 @@ qw_status qw_prepare_packet(qw_plan plan, void* psi_dev, const double* x0, doubl
  * Walk requests evolved in the Fourier form (Sec. 4, complex64 fields, FP64
  * phase and reductions) by one scheduler thread with continuous batching:
  * requests wait in a FIFO, the head is admitted when one of `slots` CUDA
- * streams is free and its fields (8 B per complex value + 8 B per site for the
- * omega table) fit in the device pool of `hbm_budget_bytes` (allocated once at
- * creation); finished requests return their slot and memory, so requests that
+ * streams is free and its field (8 B per complex value) fits in the device pool
+ * of `hbm_budget_bytes` (allocated once at creation); finished requests return their slot and memory, so requests that
  * arrived meanwhile start while others are still running, and requests in
  * different slots overlap on the device.  The initial state is normalised. */
 typedef struct {

@@ -131,12 +131,14 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchWalk* __restrict_
     // ---- the tile's rows
     const int64_t r0 = (int64_t)tile * W.rows_per_tile;
     const int64_t r1 = min(W.rows, r0 + W.rows_per_tile);
-    const int64_t nsite = (r1 - r0) * W.nx;
+    const int nx32 = (int)W.nx, ny32 = (int)W.ny;   // tiles and rows fit 32-bit indices
+    const int nsite = (int)((r1 - r0) * W.nx);
     if (s < W.t) {
       const float2* in = W.buf[s & 1];
       float2* out = W.buf[(s + 1) & 1];
-      for (int64_t k = tid; k < nsite; k += blockDim.x) {
-        const int64_t row = r0 + k / W.nx, x = k - (k / W.nx) * W.nx;
+      for (int k = tid; k < nsite; k += blockDim.x) {
+        const int kr = k / nx32;
+        const int64_t row = r0 + kr, x = k - kr * nx32;
         if (W.dim == 1) {
           site_update_1d<float, false>(in, out, W.nx, x, W.cf);
         } else if (W.dim == 2) {
@@ -144,8 +146,9 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchWalk* __restrict_
         } else {
           // rows interleave the cosets: row = 2 (z M + y) + c
           const int c = (int)(row & 1);
-          const int64_t zy = row >> 1;
-          site_update_3d<float, false>(in, out, W.nx, c, zy / W.ny, zy - (zy / W.ny) * W.ny, x, W.cf);
+          const int zy = (int)(row >> 1);
+          const int z = zy / ny32;
+          site_update_3d<float, false>(in, out, W.nx, c, z, zy - z * ny32, x, W.cf);
         }
       }
     } else {
@@ -153,8 +156,9 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchWalk* __restrict_
       const float2* src = W.buf[1];
       float2* dst = W.buf[0];
       const int s_comp = W.dim == 1 ? 2 : 4;
-      for (int64_t k = tid; k < nsite; k += blockDim.x) {
-        const int64_t row = r0 + k / W.nx, x = k - (k / W.nx) * W.nx;
+      for (int k = tid; k < nsite; k += blockDim.x) {
+        const int kr = k / nx32;
+        const int64_t row = r0 + kr, x = k - kr * nx32;
         int64_t base;
         if (W.dim == 3) {
           const int c = (int)(row & 1);

@@ -202,11 +202,16 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __rest
     const int R = p.radix[s];
     const int nb = L / R;
     const int tstep = L / (Ns * R);  // table stride of omega_{Ns R}
-    for (int b = tid; b < nb * C; b += nthr) {
-      const int jb = b >> p.cshift, c = b & (C - 1);
-      if (c >= ncol) continue;
-      const int k = jb % Ns;
-      const int idxD = (jb / Ns) * Ns * R + k;
+    // butterfly b = tid + i * nthr: column c is fixed, jb advances by nthr / C;
+    // k = jb % Ns and jq = jb / Ns advance by precomputed quotient/remainder
+    const int jstep = nthr >> p.cshift;
+    const int sq = jstep / Ns, sr = jstep - sq * Ns;
+    const int c = tid & (C - 1);
+    int jb = tid >> p.cshift;
+    int jq = jb / Ns, k = jb - jq * Ns;
+    for (; jb < nb; jb += jstep) {
+      if (c < ncol) {
+      const int idxD = jq * Ns * R + k;
       if (R == 8) {
         V a[8];
 #pragma unroll
@@ -255,6 +260,13 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __rest
         dft2<INV>(a0, a1);
         out[idxD * pitch + c] = a0;
         out[(idxD + Ns) * pitch + c] = a1;
+      }
+      }
+      k += sr;
+      jq += sq;
+      if (k >= Ns) {
+        k -= Ns;
+        ++jq;
       }
     }
     __syncthreads();
@@ -322,6 +334,112 @@ template <bool INV, typename T, typename V> struct RegDFT<16, INV, T, V> {
   }
 };
 
+// Compile-time twiddles exp(-2 pi i m / R) for the composite register DFTs:
+// cos and sin of 2 pi m / R by a Taylor series after reduction to [-pi/4, pi/4]
+// (double precision; the values become immediates).
+constexpr double ce_pi = 3.14159265358979323846264338327950288;
+constexpr double ce_taylor_sin(double x) {
+  double term = x, sum = x;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double ce_taylor_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+    sum += term;
+  }
+  return sum;
+}
+// angle 2 pi m / R, m in [0, R): octant reduction with exact rational arithmetic
+constexpr double ce_trig(int m, int R, bool want_sin) {
+  const int num = 8 * m, q = num / R;                  // octant
+  const double f = (double)(num - q * R) / (double)R;  // fraction of an octant
+  const double x = f * ce_pi / 4.0;
+  const double sx = ce_taylor_sin(x), cx = ce_taylor_cos(x);
+  const double sy = ce_taylor_sin(ce_pi / 4.0 - x), cy = ce_taylor_cos(ce_pi / 4.0 - x);
+  double s = 0.0, c = 0.0;
+  switch (q & 7) {
+    case 0: s = sx; c = cx; break;
+    case 1: s = cy; c = sy; break;
+    case 2: s = cx; c = -sx; break;
+    case 3: s = sy; c = -cy; break;
+    case 4: s = -sx; c = -cx; break;
+    case 5: s = -cy; c = -sy; break;
+    case 6: s = -cx; c = sx; break;
+    default: s = -sy; c = cy; break;
+  }
+  return want_sin ? s : c;
+}
+
+constexpr int reg_first_factor(int R) {
+  // split R = P * Q with Q the factor transformed first
+  return (R % 16 == 0 && R > 16) ? 16 : (R % 8 == 0 && R > 8) ? 8 : (R % 4 == 0 && R > 4) ? 4
+       : (R % 3 == 0 && R > 3) ? R / 3 : (R % 2 == 0 && R > 2) ? 2 : R;
+}
+
+template <bool INV, typename T, typename V> struct RegDFT<3, INV, T, V> {
+  __device__ __forceinline__ static void run(V (&a)[3]) { dft3<INV, T>(a[0], a[1], a[2]); }
+};
+
+// Composite R = P * Q (P = reg_first_factor(R)): Q-point DFTs over a[p + P q],
+// twiddle exp(-+2 pi i p k2 / R), P-point DFTs over p; output index k2 + Q k1.
+// The (p, k2) loops are template recursions so every twiddle is a constant.
+template <int R, int Q, int p, int k2, bool INV, typename T, typename V>
+struct TwApply {
+  __device__ __forceinline__ static void run(const V (&b)[Q], V (&t)[R]) {
+    if constexpr (k2 < Q) {
+      constexpr int m = (p * k2) % R;
+      if constexpr (m == 0) {
+        t[p * Q + k2] = b[k2];
+      } else {
+        constexpr double c = ce_trig(m, R, false), sn = ce_trig(m, R, true);
+        V w;
+        w.x = (T)c;
+        w.y = INV ? (T)sn : (T)-sn;
+        t[p * Q + k2] = cmul(b[k2], w);
+      }
+      TwApply<R, Q, p, k2 + 1, INV, T, V>::run(b, t);
+    }
+  }
+};
+
+template <int R, int P, int Q, int p, bool INV, typename T, typename V>
+struct StepA {
+  __device__ __forceinline__ static void run(const V (&a)[R], V (&t)[R]) {
+    if constexpr (p < P) {
+      V b[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) b[q] = a[p + P * q];
+      RegDFT<Q, INV, T, V>::run(b);
+      TwApply<R, Q, p, 0, INV, T, V>::run(b, t);
+      StepA<R, P, Q, p + 1, INV, T, V>::run(a, t);
+    }
+  }
+};
+
+template <int R, bool INV, typename T, typename V>
+struct RegDFT {
+  static constexpr int P = reg_first_factor(R);
+  static constexpr int Q = R / P;
+  __device__ __forceinline__ static void run(V (&a)[R]) {
+    V t[R];
+    StepA<R, P, Q, 0, INV, T, V>::run(a, t);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) {
+      V c[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) c[p] = t[p * Q + k2];
+      RegDFT<P, INV, T, V>::run(c);
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) a[k2 + Q * k1] = c[k1];
+    }
+  }
+};
+
 template <typename T, bool INV, int R1, int R2, bool CONTIG>
 __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restrict__ data, FftPass p,
                                                     const typename Cx<T>::t* __restrict__ tw_line,
@@ -330,17 +448,17 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restric
   using V = typename Cx<T>::t;
   constexpr int L = R1 * R2;
   constexpr int TPL = R1 > R2 ? R1 : R2;  // threads per line
-  constexpr int C = 256 / TPL;            // lines per CTA
-  constexpr int CP = C + 1;               // padded line-minor pitch
+  constexpr int C = 256 / TPL;            // lines per CTA (C * TPL <= 256 threads work)
+  constexpr int CP = (C % 2 == 0) ? C + 1 : C;  // odd line-minor pitch
   extern __shared__ __align__(16) unsigned char f2_smem[];
   V* sm = reinterpret_cast<V*>(f2_smem);
   const int tid = threadIdx.x;
   const int64_t S = p.S;
   const int64_t nlines = p.O * S;
   const int64_t l0 = (int64_t)blockIdx.x * C;
-  const int c = tid % C, r = tid / C;
+  const int c = tid % C, r = tid / C;   // r >= TPL: idle in the butterfly steps
   const int64_t l = l0 + c;
-  const bool live = l < nlines;
+  const bool live = l < nlines && r < TPL;
   int64_t base = 0, tw_b = 0;
   if (live) {
     const int64_t o = l / S, i = l - o * S;
@@ -359,7 +477,7 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restric
       if (ll < nlines) v = data[ll * L + n];
       sm[cc + CP * n] = v;
     }
-  } else {
+  } else if (r < TPL) {
 #pragma unroll 4
     for (int n = r; n < L; n += TPL) {
       V v;
@@ -412,7 +530,7 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restric
       const int64_t ll = l0 + cc;
       if (ll < nlines) data[ll * L + n] = sm[cc + CP * n];
     }
-  } else {
+  } else if (r < TPL) {
 #pragma unroll 4
     for (int n = r; n < L; n += TPL) {
       if (!live) break;
@@ -427,7 +545,7 @@ template <typename T, bool INV, int R1, int R2>
 static qw_status launch_2f(const FftPass& p, void* data, cudaStream_t st) {
   using V = typename Cx<T>::t;
   constexpr int L = R1 * R2, TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
-  const size_t smem = (size_t)L * (C + 1) * sizeof(V);
+  const size_t smem = (size_t)L * ((C % 2 == 0) ? C + 1 : C) * sizeof(V);
   static bool attr[2] = {false, false};
   const int64_t nlines = p.O * p.S;
   const int64_t grid = (nlines + C - 1) / C;
@@ -467,6 +585,32 @@ static bool run_2f(const FftPass& p, void* data, cudaStream_t st, qw_status* out
     case 64: *out = launch_2f<T, INV, 8, 8>(p, data, st); return true;
     case 128: *out = launch_2f<T, INV, 16, 8>(p, data, st); return true;
     case 256: *out = launch_2f<T, INV, 16, 16>(p, data, st); return true;
+    default: break;
+  }
+  if (sizeof(T) != 4) return false;
+  // lengths with a factor 3 (complex64; complex128 uses the Stockham kernel)
+  switch (p.L) {
+    case 12: *out = launch_2f<T, INV, 4, 3>(p, data, st); return true;
+    case 18: *out = launch_2f<T, INV, 6, 3>(p, data, st); return true;
+    case 24: *out = launch_2f<T, INV, 8, 3>(p, data, st); return true;
+    case 27: *out = launch_2f<T, INV, 9, 3>(p, data, st); return true;
+    case 36: *out = launch_2f<T, INV, 6, 6>(p, data, st); return true;
+    case 48: *out = launch_2f<T, INV, 8, 6>(p, data, st); return true;
+    case 54: *out = launch_2f<T, INV, 9, 6>(p, data, st); return true;
+    case 72: *out = launch_2f<T, INV, 9, 8>(p, data, st); return true;
+    case 81: *out = launch_2f<T, INV, 9, 9>(p, data, st); return true;
+    case 96: *out = launch_2f<T, INV, 12, 8>(p, data, st); return true;
+    case 108: *out = launch_2f<T, INV, 12, 9>(p, data, st); return true;
+    case 144: *out = launch_2f<T, INV, 12, 12>(p, data, st); return true;
+    case 162: *out = launch_2f<T, INV, 18, 9>(p, data, st); return true;
+    case 192: *out = launch_2f<T, INV, 16, 12>(p, data, st); return true;
+    case 216: *out = launch_2f<T, INV, 18, 12>(p, data, st); return true;
+    case 243: *out = launch_2f<T, INV, 27, 9>(p, data, st); return true;
+    case 288: *out = launch_2f<T, INV, 18, 16>(p, data, st); return true;
+    case 324: *out = launch_2f<T, INV, 18, 18>(p, data, st); return true;
+    case 384: *out = launch_2f<T, INV, 24, 16>(p, data, st); return true;
+    case 432: *out = launch_2f<T, INV, 24, 18>(p, data, st); return true;
+    case 512: *out = launch_2f<T, INV, 32, 16>(p, data, st); return true;
     default: return false;
   }
 }

@@ -126,7 +126,8 @@ SpecAxes spec_axes(const Geometry& g, const FftPlan& f);
 qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,
                              cudaStream_t st);
 // psi_hat (forward DFT, storage order) <- D_k^t psi_hat / |V|, BCC cosets mixed per cell;
-// with norm0 (device, optional) the result is also divided by sqrt(norm0[0]).
+// with norm0 (device, optional) the result is also divided by sqrt(norm0[0]);
+// omega == nullptr computes omega_k in the kernel (FP64) instead of reading a table.
 qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
                                   const double* omega, int64_t t, void* psi_hat, cudaStream_t st,
                                   const double* norm0 = nullptr);

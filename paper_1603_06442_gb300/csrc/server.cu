@@ -8,9 +8,9 @@
 //     is the server's HBM budget (allocated once: the loop never calls cudaMalloc);
 //   * an admitted request runs on its slot's stream: initial state (Gaussian
 //     packet built on the device, or the caller's field copied at submit), its
-//     norm, the FP64 omega table, forward FFT, D_k^t (normalised), inverse FFT,
-//     then <x> and norm, an in-place forward FFT and the particle weight;
-//     six doubles come back into pinned host memory and an event marks the end;
+//     norm, forward FFT, D_k^t (normalised; omega_k in FP64 inside the kernel),
+//     the particle weights on the evolved spectrum, inverse FFT, then <x> and
+//     norm; ten doubles come back into pinned host memory and an event marks the end;
 //   * completion: finished slots give their memory and stream back, so requests
 //     that arrived meanwhile are admitted while others are still on the GPU.
 // Requests in different slots overlap on the device.  qw_poll reads a ticket's
@@ -141,7 +141,7 @@ namespace qw {
 
 static size_t request_bytes(const Geometry& g, size_t* field, size_t* omega) {
   *field = (size_t)g.elems * 8;  // complex64
-  *omega = (size_t)g.vol * (g.dim == 3 ? 2 : 1) * sizeof(double);
+  *omega = 0;                    // omega_k is computed inside the evolve kernel
   return ((*field + 255) & ~size_t(255)) + ((*omega + 255) & ~size_t(255));
 }
 
@@ -170,7 +170,6 @@ static qw_status launch_request(qw_server_s* S, Slot& sl) {
   cudaStream_t s = sl.stream;
   char* base = static_cast<char*>(S->pool_base) + sl.off;
   void* psi = base;
-  double* omega = reinterpret_cast<double*>(base + ((R.bytes_field + 255) & ~size_t(255)));
   const double m = R.req.mass, n = std::sqrt(1.0 - m * m);
   qw_status st;
   FftPlan* f = fft_for(S, g, &st);
@@ -184,13 +183,14 @@ static qw_status launch_request(qw_server_s* S, Slot& sl) {
   }
   // norm of the initial state (its first moment slot), used to normalise
   if ((st = launch_position_moments(g, QW_C64, psi, sl.d_part, sl.d_res, s)) != QW_OK) return st;
-  if ((st = launch_omega_table(g, ax, n, m, omega, s)) != QW_OK) return st;
   if ((st = fft_forward(*f, g.dim, psi, s)) != QW_OK) return st;
-  if ((st = launch_evolve_pointwise(g, ax, QW_C64, n, m, omega, R.req.t, psi, s, sl.d_res)) != QW_OK) return st;
+  // D_k^t with omega_k computed in the kernel (a request's table would be used once)
+  if ((st = launch_evolve_pointwise(g, ax, QW_C64, n, m, nullptr, R.req.t, psi, s, sl.d_res)) != QW_OK) return st;
+  // particle weights from the evolved spectrum: |P(+-) psi^_k|^2 is what a forward
+  // DFT of psi(t) would give (the ratio does not depend on the DFT's scale)
+  if ((st = launch_particle_weights(g, ax, QW_C64, n, m, psi, sl.d_part, sl.d_res + 8, s)) != QW_OK) return st;
   if ((st = fft_inverse(*f, g.dim, psi, s)) != QW_OK) return st;
   if ((st = launch_position_moments(g, QW_C64, psi, sl.d_part, sl.d_res + 4, s)) != QW_OK) return st;
-  if ((st = fft_forward(*f, g.dim, psi, s)) != QW_OK) return st;
-  if ((st = launch_particle_weights(g, ax, QW_C64, n, m, psi, sl.d_part, sl.d_res + 8, s)) != QW_OK) return st;
   QW_CHECK_CUDA(cudaMemcpyAsync(sl.h_res, sl.d_res, 10 * sizeof(double), cudaMemcpyDeviceToHost, s));
   QW_CHECK_CUDA(cudaEventRecord(sl.done, s));
   return QW_OK;

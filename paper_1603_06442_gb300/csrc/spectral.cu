@@ -277,6 +277,14 @@ __device__ __forceinline__ void ghat(int dim, const AxesDev& a, const int64_t (&
   gm = mf * inv;
 }
 
+// omega_k = atan2(sin omega, n u) in FP64 from the FP64 tables (served path: no table)
+__device__ __forceinline__ double omega_of(int dim, const AxesDev& a, const int64_t (&f)[3], int q, double n,
+                                          double m) {
+  double u, nx, ny, nz;
+  symbol_tab<double>(dim, a, f[0], f[1], f[2], q, u, nx, ny, nz);
+  return atan2(sqrt(m * m + n * n * (nx * nx + ny * ny + nz * nz)), n * u);
+}
+
 template <typename T, int S>
 __device__ __forceinline__ void cs_of(double omega, double tt, T& c, T& s) {
   if (sizeof(T) == 8) {
@@ -308,7 +316,7 @@ __global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t
     if (dim == 1) {
       V v[2] = {data[idx], data[count + idx]};
       T c, s, gx, gy, gz, gm;
-      cs_of<T, 2>(omega[idx], tt, c, s);
+      cs_of<T, 2>(omega ? omega[idx] : omega_of(1, a, f, 0, n, m), tt, c, s);
       ghat<T>(1, a, f, 0, n, m, gx, gy, gz, gm);
       apply_dt<T, 2>(v, c, s, (T)0, gx, gy, gz, gm);
       data[idx] = make_vec(v[0], scale);
@@ -318,7 +326,7 @@ __global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t
 #pragma unroll
       for (int q = 0; q < 4; ++q) v[q] = data[q * count + idx];
       T c, s, gx, gy, gz, gm;
-      cs_of<T, 4>(omega[idx], tt, c, s);
+      cs_of<T, 4>(omega ? omega[idx] : omega_of(2, a, f, 0, n, m), tt, c, s);
       ghat<T>(2, a, f, 0, n, m, gx, gy, gz, gm);
       apply_dt<T, 4>(v, c, s, (T)0, gx, gy, gz, gm);
 #pragma unroll
@@ -346,13 +354,13 @@ __global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t
       }
       {
         T c, s, gx, gy, gz, gm;
-        cs_of<T, 4>(omega[2 * idx], tt, c, s);
+        cs_of<T, 4>(omega ? omega[2 * idx] : omega_of(3, a, f, 0, n, m), tt, c, s);
         ghat<T>(3, a, f, 0, n, m, gx, gy, gz, gm);
         apply_dt<T, 4>(c0, c, s, (T)0, gx, gy, gz, gm);
       }
       {
         T c, s, gx, gy, gz, gm;
-        cs_of<T, 4>(omega[2 * idx + 1], tt, c, s);
+        cs_of<T, 4>(omega ? omega[2 * idx + 1] : omega_of(3, a, f, 1, n, m), tt, c, s);
         ghat<T>(3, a, f, 1, n, m, gx, gy, gz, gm);
         apply_dt<T, 4>(c1, c, s, (T)0, gx, gy, gz, gm);
       }

@@ -67,6 +67,27 @@ def test_spectral_parity(qb, dim, N, dtype, t):
     assert err <= tol(dtype, t), err
 
 
+@pytest.mark.parametrize("N", [12, 18, 24, 27, 36, 48, 54, 72, 81, 96, 108, 144, 162, 192, 216, 243, 288, 324,
+                               384, 432, 512])
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_spectral_line_lengths(qb, N, dtype):
+    """Every register-kernel line length (2^a 3^b), forward and inverse, against 5 oracle steps."""
+    m, t = 0.31, 5
+    a = inputs.random_field(1, N, seed=N)
+    got = run_spectral(qb, 1, N, m, dtype, a, t)
+    exp = walk.step(1, m, a, t)
+    assert rel_l2(got, exp) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dim,N", [(2, 54), (2, 162), (3, 36), (3, 108)])
+def test_spectral_factor3_boxes(qb, dim, N):
+    m, t = 0.12, 4
+    a = inputs.random_field(dim, N, seed=N + dim)
+    got = run_spectral(qb, dim, N, m, "c64", a, t)
+    exp = walk.to_device(dim, N, walk.step(dim, m, walk.from_device(dim, N, a), t))
+    assert rel_l2(got, exp) <= TOL["c64"]
+
+
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("m", [0.0, 1.0])
 def test_spectral_degenerate_masses(qb, dtype, m):
