@@ -35,6 +35,10 @@ if ROOT not in sys.path:
 WORKLOAD = {"name": "bcc_N512_stencil_c64", "dim": 3, "N": 512, "mass": 0.1, "sigma": 32.0,
             "k0": (0.3, 0.2, 0.1), "substeps": 100}
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per launch of a stencil kernel from one ncu capture of it, per site:
+# step3d_c64_tma_kernel at BCC N=384 moved 470.5 MB + 409.9 MB for 14,155,776 sites.  Traffic grows in
+# proportion to the sites, so bench.py reports sites x this figure; kernels without a capture get null.
+NCU_TRAFFIC_BYTES_PER_SITE = {"step3d_c64_tma_kernel": (470507520 + 409899264) / 14155776}
 
 
 def parse():
@@ -66,6 +70,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(ms, world, device):
+    """Slowest rank's time: all-reduce MAX over the process group (no data-path collective)."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(sites, substeps, steps, world, ms):
+    """Whole-job site-steps/s: every rank advances its own replica by steps x substeps updates."""
+    return sites * substeps * steps * world / (ms / 1e3)
 
 
 def measured_peaks():
@@ -223,12 +243,8 @@ def run_ours(args, rank, world, local):
         barrier()
     total_ms = t_start.elapsed_time(t_end)
     stencil_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
-    ms = total_ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = sites * S * args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(total_ms, world, dev)
+    value = job_value(sites, S, args.steps, world, ms)
     # stencil launches (S / fused, S even) + moments/fold + 3 FFT passes + weights/fold
     stencil_launches = (S + fused - 1) // fused
     launches_per_step = stencil_launches + 2 + 3 + 2
@@ -266,7 +282,11 @@ def run_ours(args, rank, world, local):
                    "l2": "no flush: the %.2f GB field is larger than L2 (129 MB)" % (field_bytes / 1e9),
                    "input": "Gaussian packet sigma=%g sites, k0=%s" % (W["sigma"], list(W["k0"]))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (NCU_TRAFFIC_BYTES_PER_SITE[kernel_name] * sites
+                                 if kernel_name in NCU_TRAFFIC_BYTES_PER_SITE else None),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at BCC N=384, "
+                                       "scaled by sites (profiles/step3d_c64_tma_kernel_bcc_N384.txt)",
                      "kernel": kernel_name, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": 2 * field_bytes,
                      "steps_per_launch": fused,

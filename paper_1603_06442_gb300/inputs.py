@@ -17,7 +17,7 @@ Recipes (shaped like the paper's runs, Sec. 5, Figs. 2-6):
 
 import numpy as np
 
-__all__ = ["field_shape", "n_components", "site_positions", "gaussian_packet", "random_field",
+__all__ = ["field_shape", "n_components", "site_positions", "gaussian_packet", "random_packets", "random_field",
            "localized", "sample_batch_mix", "sample_served_stream", "snap_fft_size"]
 
 
@@ -77,6 +77,25 @@ def gaussian_packet(dim, N, x0, sigma, k0, spinor):
     else:
         out = chi.reshape((s,) + (1,) * dim) * env[None]
     return _normalise(out.astype(complex))
+
+
+def random_packets(dim, N, n_packets, sigma, kmax, seed, spinor=None):
+    """Superposition of Gaussian packets: centres uniform in the box, wave-vector
+    directions uniform, |k0| ~ U[0, kmax], phases U[0, 2 pi), fixed spinor."""
+    rng = np.random.default_rng(seed)
+    s = n_components(dim)
+    chi = np.asarray(spinor if spinor is not None else ([1, 0] if dim == 1 else [0.5, 0.5, 0.5, 0.5]), complex)
+    out = np.zeros(field_shape(dim, N), dtype=complex)
+    for _ in range(n_packets):
+        x0 = rng.uniform(0, N, size=dim)
+        if dim == 3:
+            x0 = 2.0 * np.round(x0 / 2.0)          # a BCC site of coset 0
+        d = rng.normal(size=dim)
+        d /= np.linalg.norm(d)
+        k0 = d * rng.uniform(0.0, kmax)
+        ph = np.exp(1j * rng.uniform(0, 2 * np.pi))
+        out = out + ph * gaussian_packet(dim, N, x0, sigma, k0, chi)
+    return _normalise(out)
 
 
 def random_field(dim, N, seed):

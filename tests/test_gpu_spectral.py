@@ -166,6 +166,70 @@ def test_config_bcc128_spectral_t1000(qb, dtype):
     assert err <= TOL[dtype]
 
 
+@pytest.mark.parametrize("m", [0.01, 0.1, 0.3])
+@pytest.mark.parametrize("t", [10 ** 4, 10 ** 6])
+def test_config3_like_long_times_vs_oracle(qb, m, t):
+    """Random-phase Gaussian packets (|k0| ~ U[0, 0.5]) on a BCC box the oracle can transform
+    (N = 64): complex64 (FP64 phase) against the FP64 oracle at t = 1e4 and 1e6."""
+    N = 64
+    a = inputs.random_packets(3, N, 4, 4.0, 0.5, seed=int(100 * m))
+    got = run_spectral(qb, 3, N, m, "c64", a, t)
+    exp = walk.to_device(3, N, spectral.evolve(3, m, walk.from_device(3, N, a.astype(np.complex64).astype(complex)), t))
+    err = rel_l2(got, exp)
+    print("BCC64 m=%g t=%d c64 rel-L2 %.3e" % (m, t, err))
+    assert err <= TOL["c64"]
+
+
+def device_packets(qb, plan, N, n_packets, sigma, kmax, seed):
+    """A superposition of Gaussian packets built by the device packet builder (pinned against
+    the seeded generator in the serving tests); centres, directions and phases seeded."""
+    rng = np.random.default_rng(seed)
+    out = torch.zeros(plan.elems, dtype=plan.torch_dtype, device="cuda")
+    one = torch.empty_like(out)
+    for _ in range(n_packets):
+        x0 = 2.0 * np.round(rng.uniform(0, N, size=3) / 2.0)
+        d = rng.normal(size=3)
+        k0 = d / np.linalg.norm(d) * rng.uniform(0.0, kmax)
+        plan.prepare_packet(one, list(x0), sigma, list(k0), [0.5, 0.5, 0.5, 0.5])
+        one /= torch.linalg.vector_norm(one)
+        out += complex(np.exp(1j * rng.uniform(0, 2 * np.pi))) * one
+    out /= torch.linalg.vector_norm(out)
+    return out
+
+
+@pytest.mark.parametrize("m", [0.01, 0.1, 0.3])
+def test_config3_bcc512_properties(qb, m):
+    """BCC N = 512 (33,554,432 sites) at t = 1e4 and 1e6: properties that hold at any size --
+    the group law U^(2t) = U^t U^t, norm and particle weight conserved, and complex64 against the
+    complex128 path (itself pinned to the oracle at smaller sizes)."""
+    N = 512
+    p128 = qb.Plan(3, N, m, "c128")
+    w = device_packets(qb, p128, N, 4, 32.0, 0.5, seed=int(100 * m))
+    a = w.to(torch.complex64)
+    p64 = qb.Plan(3, N, m, "c64")
+    x = a.clone()
+    o0 = p64.observables(x)
+    y = a.clone()
+    p64.evolve_spectral(x, 2 * 10 ** 6)
+    p64.evolve_spectral(y, 10 ** 6)
+    p64.evolve_spectral(y, 10 ** 6)
+    o1 = p64.observables(x)
+    p64.sync()
+    assert float(torch.linalg.vector_norm(x - y) / torch.linalg.vector_norm(y)) <= 1e-5
+    assert abs(o1["norm"] - o0["norm"]) <= 1e-5 and abs(o1["w_particle"] - o0["w_particle"]) <= 1e-5
+    z = a.clone()
+    p64.evolve_spectral(z, 10 ** 4)
+    p64.sync()
+    p64.close()
+    w = a.to(torch.complex128)
+    p128.evolve_spectral(w, 10 ** 4)
+    p128.sync()
+    p128.close()
+    err = float(torch.linalg.vector_norm(z.to(torch.complex128) - w) / torch.linalg.vector_norm(w))
+    print("BCC512 m=%g t=1e4 c64 vs c128 rel-L2 %.3e" % (m, err))
+    assert err <= TOL["c64"]
+
+
 @pytest.mark.parametrize("dim,N", [(1, 64), (2, 12), (3, 8), (3, 16)])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_particle_weights(qb, dim, N, dtype):
