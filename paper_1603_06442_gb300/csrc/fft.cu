@@ -577,43 +577,50 @@ static qw_status launch_2f(const FftPass& p, void* data, cudaStream_t st) {
 }
 
 // Lengths with a two-factor register kernel; returns false for the generic path.
+// With p == nullptr nothing is launched: the call only reports whether L has one
+// (the planner uses this to split long axes into register-kernel passes).
+#define QW_2F(LEN, A, B)                                          \
+  case LEN:                                                       \
+    if (p) *out = launch_2f<T, INV, A, B>(*p, data, st);          \
+    return true;
 template <typename T, bool INV>
-static bool run_2f(const FftPass& p, void* data, cudaStream_t st, qw_status* out) {
-  switch (p.L) {
-    case 16: *out = launch_2f<T, INV, 4, 4>(p, data, st); return true;
-    case 32: *out = launch_2f<T, INV, 8, 4>(p, data, st); return true;
-    case 64: *out = launch_2f<T, INV, 8, 8>(p, data, st); return true;
-    case 128: *out = launch_2f<T, INV, 16, 8>(p, data, st); return true;
-    case 256: *out = launch_2f<T, INV, 16, 16>(p, data, st); return true;
+static bool run_2f(int L, const FftPass* p, void* data, cudaStream_t st, qw_status* out) {
+  switch (L) {
+    QW_2F(16, 4, 4)
+    QW_2F(32, 8, 4)
+    QW_2F(64, 8, 8)
+    QW_2F(128, 16, 8)
+    QW_2F(256, 16, 16)
     default: break;
   }
   if (sizeof(T) != 4) return false;
   // lengths with a factor 3 (complex64; complex128 uses the Stockham kernel)
-  switch (p.L) {
-    case 12: *out = launch_2f<T, INV, 4, 3>(p, data, st); return true;
-    case 18: *out = launch_2f<T, INV, 6, 3>(p, data, st); return true;
-    case 24: *out = launch_2f<T, INV, 8, 3>(p, data, st); return true;
-    case 27: *out = launch_2f<T, INV, 9, 3>(p, data, st); return true;
-    case 36: *out = launch_2f<T, INV, 6, 6>(p, data, st); return true;
-    case 48: *out = launch_2f<T, INV, 8, 6>(p, data, st); return true;
-    case 54: *out = launch_2f<T, INV, 9, 6>(p, data, st); return true;
-    case 72: *out = launch_2f<T, INV, 9, 8>(p, data, st); return true;
-    case 81: *out = launch_2f<T, INV, 9, 9>(p, data, st); return true;
-    case 96: *out = launch_2f<T, INV, 12, 8>(p, data, st); return true;
-    case 108: *out = launch_2f<T, INV, 12, 9>(p, data, st); return true;
-    case 144: *out = launch_2f<T, INV, 12, 12>(p, data, st); return true;
-    case 162: *out = launch_2f<T, INV, 18, 9>(p, data, st); return true;
-    case 192: *out = launch_2f<T, INV, 16, 12>(p, data, st); return true;
-    case 216: *out = launch_2f<T, INV, 18, 12>(p, data, st); return true;
-    case 243: *out = launch_2f<T, INV, 27, 9>(p, data, st); return true;
-    case 288: *out = launch_2f<T, INV, 18, 16>(p, data, st); return true;
-    case 324: *out = launch_2f<T, INV, 18, 18>(p, data, st); return true;
-    case 384: *out = launch_2f<T, INV, 24, 16>(p, data, st); return true;
-    case 432: *out = launch_2f<T, INV, 24, 18>(p, data, st); return true;
-    case 512: *out = launch_2f<T, INV, 32, 16>(p, data, st); return true;
+  switch (L) {
+    QW_2F(12, 4, 3)
+    QW_2F(18, 6, 3)
+    QW_2F(24, 8, 3)
+    QW_2F(27, 9, 3)
+    QW_2F(36, 6, 6)
+    QW_2F(48, 8, 6)
+    QW_2F(54, 9, 6)
+    QW_2F(72, 9, 8)
+    QW_2F(81, 9, 9)
+    QW_2F(96, 12, 8)
+    QW_2F(108, 12, 9)
+    QW_2F(144, 12, 12)
+    QW_2F(162, 18, 9)
+    QW_2F(192, 16, 12)
+    QW_2F(216, 18, 12)
+    QW_2F(243, 27, 9)
+    QW_2F(288, 18, 16)
+    QW_2F(324, 18, 18)
+    QW_2F(384, 24, 16)
+    QW_2F(432, 24, 18)
+    QW_2F(512, 32, 16)
     default: return false;
   }
 }
+#undef QW_2F
 
 // ---------------------------------------------------------------- planning
 static bool radix_plan(int L, int* radix, int* n) {
@@ -635,27 +642,52 @@ bool fft_size_ok(int64_t L) {
   return L == 1;
 }
 
-// Split an axis of length L into 1-3 pass lengths <= maxline (each 2^a 3^b).
+// Relative cost of one pass of length L: every pass reads and writes the whole
+// field once; the generic shared-memory kernel runs several times slower than a
+// register kernel (measured: ~0.7 against ~4 TB/s), worse still for short lines.
+template <typename T>
+static double pass_cost(int64_t L) {
+  qw_status unused;
+  if (run_2f<T, false>((int)L, nullptr, nullptr, nullptr, &unused)) return 1.0;
+  return L < 64 ? 8.0 : 4.0;
+}
+
+// Split an axis of length L (2^a 3^b) into 1-3 pass lengths <= maxline of least
+// total cost; ties go to the most even split.
+template <typename T>
 static bool split_axis(int64_t L, int maxline, std::vector<int>* parts) {
   parts->clear();
-  if (L <= maxline) {
-    parts->push_back((int)L);
-    return true;
+  std::vector<int64_t> dv;  // divisors of L that can be one pass
+  for (int64_t a = 1; a <= maxline; a *= 2)
+    for (int64_t b = a; b <= maxline; b *= 3)
+      if (b >= 2 && L % b == 0) dv.push_back(b);
+  double best = 1e300;
+  auto consider = [&](std::initializer_list<int64_t> fs) {
+    double c = 0.0, spread = 0.0;
+    int64_t lo = L, hi = 1;
+    for (int64_t f : fs) {
+      if (f < 2 || f > maxline) return;
+      c += pass_cost<T>(f);
+      lo = f < lo ? f : lo;
+      hi = f > hi ? f : hi;
+    }
+    spread = 1e-9 * (double)(hi - lo);
+    if (c + spread < best) {
+      best = c + spread;
+      parts->assign(fs.begin(), fs.end());
+    }
+  };
+  if (L <= maxline) consider({L});
+  for (int64_t d1 : dv) {
+    const int64_t r1 = L / d1;
+    if (r1 < 2) continue;
+    consider({d1, r1});
+    for (int64_t d2 : dv) {
+      if (r1 % d2 != 0 || r1 / d2 < 2) continue;
+      consider({d1, d2, r1 / d2});
+    }
   }
-  // greedy: first factor = the largest 2^a 3^b <= maxline dividing L, recurse on the rest
-  int64_t rest = L;
-  while (rest > maxline) {
-    int best = 0;
-    for (int64_t a = 1; a <= maxline; a *= 2)
-      for (int64_t b = a; b <= maxline; b *= 3)
-        if (rest % b == 0 && b > best && rest / b > 1) best = (int)b;
-    if (best <= 1) return false;
-    parts->push_back(best);
-    rest /= best;
-    if (parts->size() >= 3) return false;
-  }
-  parts->push_back((int)rest);
-  return true;
+  return !parts->empty();
 }
 
 template <typename T>
@@ -735,7 +767,7 @@ static qw_status fft_plan_t(FftPlan* f, const Geometry& g) {
       return QW_EINVAL;
     }
     std::vector<int> parts;
-    if (!split_axis(L, maxline, &parts)) {
+    if (!split_axis<T>(L, maxline, &parts)) {
       set_error("axis length %lld cannot be split into <= 3 passes of <= %d", (long long)L, maxline);
       return QW_EINVAL;
     }
@@ -795,6 +827,14 @@ static qw_status trig_tables(FftPlan* f, const Geometry& g) {
     QW_CHECK_CUDA(cudaMalloc(&f->trig32[ax], len * sizeof(float2)));
     QW_CHECK_CUDA(cudaMemcpy(f->trig32[ax], h32.data(), len * sizeof(float2), cudaMemcpyHostToDevice));
   }
+  std::vector<double2> ha(kAngleTab + 1);
+  for (int j = 0; j <= kAngleTab; ++j) {
+    const double th = (double)j * kAngleStep;  // the same product the device forms
+    ha[j].x = std::cos(th);
+    ha[j].y = std::sin(th);
+  }
+  QW_CHECK_CUDA(cudaMalloc(&f->angle, ha.size() * sizeof(double2)));
+  QW_CHECK_CUDA(cudaMemcpy(f->angle, ha.data(), ha.size() * sizeof(double2), cudaMemcpyHostToDevice));
   return QW_OK;
 }
 
@@ -813,6 +853,8 @@ void fft_plan_destroy(FftPlan* f) {
     f->trig[a] = nullptr;
     f->trig32[a] = nullptr;
   }
+  if (f->angle) cudaFree(f->angle);
+  f->angle = nullptr;
   for (int i = 0; i < f->npass; ++i) {
     if (f->pass[i].tw_line) cudaFree(f->pass[i].tw_line);
     if (f->pass[i].tw_hi) cudaFree(f->pass[i].tw_hi);
@@ -825,7 +867,7 @@ template <typename T, bool INV>
 static qw_status run_pass(const FftPass& p, void* data, cudaStream_t st) {
   using V = typename Cx<T>::t;
   qw_status s2;
-  if (run_2f<T, INV>(p, data, st, &s2)) return s2;
+  if (run_2f<T, INV>(p.L, &p, data, st, &s2)) return s2;
   static bool attr[2] = {false, false};
   if (!attr[INV]) {
     QW_CHECK_CUDA(cudaFuncSetAttribute(fft_pass_kernel<T, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,

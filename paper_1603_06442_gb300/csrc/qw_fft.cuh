@@ -52,7 +52,12 @@ struct FftPlan {
   //   dim 3: pi f / M (f < M, the half wave vector kappa / 2 of each axis)
   void* trig[3] = {nullptr, nullptr, nullptr};
   void* trig32[3] = {nullptr, nullptr, nullptr};  // the same tables as float2 (complex64 kernels)
+  // (cos, sin)(j * kAngleStep), j <= kAngleTab: anchors of the fast omega_k refinement
+  void* angle = nullptr;
 };
+
+constexpr int kAngleTab = 1024;
+constexpr double kAngleStep = 3.14159265358979323846 / kAngleTab;
 
 bool fft_size_ok(int64_t L);
 qw_status fft_plan_create(FftPlan* f, const Geometry& g, qw_dtype dt);

@@ -121,6 +121,7 @@ struct SpecAxes {  // digit split of each axis (storage order -> frequency) and 
   int64_t len[3];
   const double2* trig[3];
   const float2* trig32[3];
+  const double2* angle;
 };
 SpecAxes spec_axes(const Geometry& g, const FftPlan& f);
 qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,

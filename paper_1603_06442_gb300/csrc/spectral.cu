@@ -45,6 +45,7 @@ struct AxesDev {
   int64_t len[3];
   const double2* trig[3];
   const float2* trig32[3];
+  const double2* angle;
 };
 
 SpecAxes spec_axes(const Geometry& g, const FftPlan& f) {
@@ -62,6 +63,7 @@ SpecAxes spec_axes(const Geometry& g, const FftPlan& f) {
     a.trig[ax] = static_cast<const double2*>(f.trig[ax]);
     a.trig32[ax] = static_cast<const float2*>(f.trig32[ax]);
   }
+  a.angle = static_cast<const double2*>(f.angle);
   return a;
 }
 
@@ -74,6 +76,7 @@ static AxesDev to_dev(const SpecAxes& a) {
     d.trig[ax] = a.trig[ax];
     d.trig32[ax] = a.trig32[ax];
   }
+  d.angle = a.angle;
   return d;
 }
 
@@ -277,12 +280,38 @@ __device__ __forceinline__ void ghat(int dim, const AxesDev& a, const int64_t (&
   gm = mf * inv;
 }
 
-// omega_k = atan2(sin omega, n u) in FP64 from the FP64 tables (served path: no table)
+// omega = atan2(S, C) for S = sqrt(S2) >= 0, S^2 + C^2 = 1, to FP64 accuracy with
+// few FP64 operations (FP64 runs at ~1/64 of the FP32 rate here):
+//   S   : FP32 square root, one Newton correction in FP64;
+//   w0  : FP32 atan2, only to pick the anchor theta_j = j pi / kAngleTab nearest omega;
+//   x   = sin(omega - theta_j) = S cos theta_j - C sin theta_j (FP64, anchors from an FP64 table),
+//         |x| <= pi / (2 kAngleTab) + 1e-6 < 1.6e-3;
+//   omega = theta_j + asin(x),  asin(x) = x + x^3/6 + 3 x^5/40 + O(x^7)  (x^7 term < 1e-21).
+__device__ __forceinline__ double omega_fast(double C, double S2, const double2* __restrict__ angle) {
+  double S;
+  if (S2 > 1e-30) {
+    const float s0 = sqrtf((float)S2);
+    const double e = fma(-(double)s0, (double)s0, S2);
+    S = fma(e, (double)(0.5f / s0), (double)s0);
+  } else {
+    S = sqrt(S2);
+  }
+  const float w0 = atan2f((float)S, (float)C);
+  int j = __float2int_rn(w0 * (float)(kAngleTab / 3.14159265358979323846));
+  j = j < 0 ? 0 : (j > kAngleTab ? kAngleTab : j);
+  const double2 an = angle[j];
+  const double x = fma(S, an.x, -C * an.y);
+  const double x2 = x * x;
+  const double d = fma(x * x2, fma(x2, 0.075, 1.0 / 6.0), x);
+  return (double)j * kAngleStep + d;
+}
+
+// omega_k in FP64 from the FP64 tables, computed in the kernel (served path: no table)
 __device__ __forceinline__ double omega_of(int dim, const AxesDev& a, const int64_t (&f)[3], int q, double n,
                                           double m) {
   double u, nx, ny, nz;
   symbol_tab<double>(dim, a, f[0], f[1], f[2], q, u, nx, ny, nz);
-  return atan2(sqrt(m * m + n * n * (nx * nx + ny * ny + nz * nz)), n * u);
+  return omega_fast(n * u, m * m + n * n * (nx * nx + ny * ny + nz * nz), a.angle);
 }
 
 template <typename T, int S>

@@ -63,7 +63,8 @@ def test_device_packet_matches_generator(qb, dim, N, dtype):
     plan.close()
 
 
-REQS = [(1, 96, 0.1, 57), (2, 24, 0.3, 33), (3, 16, 0.2, 100), (3, 24, 0.05, 1000), (2, 18, 0.45, 7)]
+REQS = [(1, 96, 0.1, 57), (2, 24, 0.3, 33), (3, 16, 0.2, 100), (3, 24, 0.05, 1000), (2, 18, 0.45, 7),
+        (1, 1024, 0.01, 99991), (2, 48, 0.003, 100000), (3, 32, 0.3, 77777), (1, 4096, 0.0, 31)]
 
 
 def oracle_obs(dim, N, m, t, x0, sig, k0, chi):
