@@ -13,6 +13,10 @@
 // and then writes psi2 = U psi1 at layer i of the tile to HBM.  The input box is the
 // one the one-step kernel loads, so HBM sees one read and one write of the field per
 // two steps; the cost is ~14% extra arithmetic on the halo ring.
+// The kernel is bound by shared-memory bandwidth, so every thread computes two
+// x-adjacent cells from three loaded columns and keeps, in registers, the
+// components its next z-step reads again (pair_step), cutting shared-memory loads
+// per cell by a third.
 // Edge tiles get the periodic images of out-of-range cells as in the one-step kernel.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -39,70 +43,122 @@ constexpr int SMEM2_BYTES = (2 * NS0 + 4) * BUF2_BYTES + 2 * NS0 * 8 + 128;
 static_assert(BUF2_BYTES % 128 == 0, "TMA destinations must stay 128-byte aligned");
 static_assert(SMEM2_BYTES <= 227 * 1024, "shared memory budget");
 
-// One step for one cell of output coset C at box (row r, col q):
-// la / lb = other coset at the h_z = +1 / -1 source layers, own = coset C at the output layer.
-template <int HX, int HY, int HZ, int C>
-__device__ __forceinline__ void cell_term(float2& S0, float2& S1, float2& S2, float2& S3, const float* lay, int r,
-                                          int q) {
-  constexpr int P = HX * HY * HZ;
-  const int rr = (HY == 1) ? r - 1 + C : r + C;
-  const int qq = (HX == 1) ? q - 1 + C : q + C;
-  const float* base = lay + rr * ROWF + 2 * qq;
-  if constexpr (HZ == 1) {
-    const float2 a = *reinterpret_cast<const float2*>(base);
-    const float2 b = *reinterpret_cast<const float2*>(base + CS2);
-    const float2 d = *reinterpret_cast<const float2*>(base + 3 * CS2);
-    cmac<1, -P>(S0, a);
-    cmac<HX, -HY>(S0, b);
-    cmac<-HX, HY>(S2, d);
-    cmac<1, -P>(S3, d);
+// Three consecutive box cells [c0, c0 + 3) of one component row, c0 = 2 tx + OFF:
+// an 8-byte and a 16-byte load (OFF odd) or a 16-byte and an 8-byte load (OFF even).
+template <int OFF>
+__device__ __forceinline__ Row3 srow_at(const float* row, int tx) {
+  const float* p = row + 2 * (2 * tx + OFF);
+  Row3 r;
+  if constexpr (OFF % 2 == 1) {
+    const float2 a = *reinterpret_cast<const float2*>(p);
+    const float4 b = *reinterpret_cast<const float4*>(p + 2);
+    r.lo = a;
+    r.mid = make_float2(b.x, b.y);
+    r.hi = make_float2(b.z, b.w);
   } else {
-    const float2 a = *reinterpret_cast<const float2*>(base);
-    const float2 b = *reinterpret_cast<const float2*>(base + CS2);
-    const float2 c = *reinterpret_cast<const float2*>(base + 2 * CS2);
-    cmac<HX, HY>(S1, a);
-    cmac<1, -P>(S1, b);
-    cmac<1, -P>(S2, c);
-    cmac<-HX, -HY>(S3, c);
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    const float2 b = *reinterpret_cast<const float2*>(p + 4);
+    r.lo = make_float2(a.x, a.y);
+    r.mid = make_float2(a.z, a.w);
+    r.hi = b;
+  }
+  return r;
+}
+
+// One step for the two cells of output coset C at box row R, box columns
+// Q0 = 2 tx + QOFF and Q0 + 1 (QOFF even: 16-byte aligned).  Sources: the other
+// coset at the h_z = +1 layer (la: components 0, 1, 3) and the h_z = -1 layer
+// (lb: components 0, 1, 2), rows R - 1 + C (h_y = +1) and R + C (h_y = -1),
+// columns Q0 - 1 + C .. Q0 + 1 + C; the mass term reads own (coset C).
+//
+// z-reuse: the h_z = -1 layer of this step is the h_z = +1 layer of the same
+// thread's next step (one layer further in z), at the same rows and columns, and
+// both read components 0 and 1 there.  carry keeps those two Row3 pairs in
+// registers between the steps; with first = true they are loaded from la instead.
+template <int C, int QOFF>
+__device__ __forceinline__ void pair_step(Row3 (&carry)[2][2], bool first, const float* la, const float* lb,
+                                          const float* own, int R, int tx, const Coef32& cf, float4 (&res)[4]) {
+  constexpr int OFF = QOFF - 1 + C;
+  float2 S[2][4];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) S[j][q] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int iy = 0; iy < 2; ++iy) {
+    const float* base = la + (R - 1 + C + iy) * ROWF;
+    if (first) {
+      carry[iy][0] = srow_at<OFF>(base, tx);
+      carry[iy][1] = srow_at<OFF>(base + CS2, tx);
+    }
+    const Row3 d = srow_at<OFF>(base + 3 * CS2, tx);
+    if (iy == 0) pair<+1, +1>(S, carry[0][0], carry[0][1], d);
+    else pair<-1, +1>(S, carry[1][0], carry[1][1], d);
+  }
+#pragma unroll
+  for (int iy = 0; iy < 2; ++iy) {
+    const float* base = lb + (R - 1 + C + iy) * ROWF;
+    const Row3 a = srow_at<OFF>(base, tx), b = srow_at<OFF>(base + CS2, tx), c = srow_at<OFF>(base + 2 * CS2, tx);
+    if (iy == 0) pair<+1, -1>(S, a, b, c);
+    else pair<-1, -1>(S, a, b, c);
+    carry[iy][0] = a;
+    carry[iy][1] = b;
+  }
+  const float* ob = own + R * ROWF + 2 * (2 * tx + QOFF);
+  float4 o[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) o[q] = *reinterpret_cast<const float4*>(ob + q * CS2);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 w = o[q ^ 2];
+    const float2 r0 = finish(cf, S[0][q], make_float2(w.x, w.y));
+    const float2 r1 = finish(cf, S[1][q], make_float2(w.z, w.w));
+    res[q] = make_float4(r0.x, r0.y, r1.x, r1.y);
   }
 }
 
-template <int C>
-__device__ __forceinline__ void cell_step(const float* la, const float* lb, const float* own, float* dst, int r,
-                                          int q, const Coef32& cf) {
-  float2 S0 = make_float2(0.f, 0.f), S1 = S0, S2 = S0, S3 = S0;
-  cell_term<+1, +1, +1, C>(S0, S1, S2, S3, la, r, q);
-  cell_term<+1, -1, +1, C>(S0, S1, S2, S3, la, r, q);
-  cell_term<-1, +1, +1, C>(S0, S1, S2, S3, la, r, q);
-  cell_term<-1, -1, +1, C>(S0, S1, S2, S3, la, r, q);
-  cell_term<+1, +1, -1, C>(S0, S1, S2, S3, lb, r, q);
-  cell_term<+1, -1, -1, C>(S0, S1, S2, S3, lb, r, q);
-  cell_term<-1, +1, -1, C>(S0, S1, S2, S3, lb, r, q);
-  cell_term<-1, -1, -1, C>(S0, S1, S2, S3, lb, r, q);
-  const int o = r * ROWF + 2 * q;
-  const float2 o0 = *reinterpret_cast<const float2*>(own + o);
-  const float2 o1 = *reinterpret_cast<const float2*>(own + o + CS2);
-  const float2 o2 = *reinterpret_cast<const float2*>(own + o + 2 * CS2);
-  const float2 o3 = *reinterpret_cast<const float2*>(own + o + 3 * CS2);
-  *reinterpret_cast<float2*>(dst + o) = finish(cf, S0, o2);
-  *reinterpret_cast<float2*>(dst + o + CS2) = finish(cf, S1, o3);
-  *reinterpret_cast<float2*>(dst + o + 2 * CS2) = finish(cf, S2, o0);
-  *reinterpret_cast<float2*>(dst + o + 3 * CS2) = finish(cf, S3, o1);
+template <int QOFF>
+__device__ __forceinline__ void store_smem(float* dst, int R, int tx, const float4 (&res)[4]) {
+  float* d = dst + R * ROWF + 2 * (2 * tx + QOFF);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) *reinterpret_cast<float4*>(d + q * CS2) = res[q];
 }
 
-// psi1 of coset 1 on rows [0, TY2+1), cols [1, 66) and of coset 0 on rows [1, TY2+2), cols [2, 67).
-__device__ __forceinline__ void step1(const float* c0a, const float* c0b, const float* c1a, const float* c1b,
-                                      float* p1c1, float* p1c0, const Coef32& cf, int tid) {
-  constexpr int W = TX + 1, CELLS = W * (TY2 + 1);
-  // coset 1 at layer i: sources coset 0 at layers i (h_z = +1) and i+1, own coset 1 at i
-  for (int k = tid; k < CELLS; k += NT2) {
-    const int r = k / W, q = 1 + (k - (k / W) * W);
-    cell_step<1>(c0a, c0b, c1a, p1c1, r, q, cf);
-  }
-  // coset 0 at layer i+1: sources coset 1 at layers i (h_z = +1) and i+1, own coset 0 at i+1
-  for (int k = tid; k < CELLS; k += NT2) {
-    const int r = 1 + k / W, q = 2 + (k - (k / W) * W);
-    cell_step<0>(c1a, c1b, c0b, p1c0, r, q, cf);
+// psi1 of both cosets on the region step 2 reads:
+//   coset 1 at layer L1 on rows [0, TY2+1), columns [1, 66): pairs at Q0 = 2k, k < 33;
+//   coset 0 at layer L1+1 on rows [1, TY2+2), columns [2, 67): pairs at Q0 = 2k + 2, k < 33.
+// Thread (tx, ty) owns the pair k = tx of row ty (coset 1) and ty + 1 (coset 0),
+// with z-reuse; the last row and the pair k = 32 of each coset (82 pairs) go to
+// threads 0..81 without it.
+struct Step1Src {
+  const float *c0a, *c0b, *c1a, *c1b;  // psi0 coset 0 / 1 at layers L1 (a) and L1 + 1 (b)
+  float *p1c1, *p1c0;                  // psi1 destinations: coset 1 at L1, coset 0 at L1 + 1
+};
+
+__device__ __forceinline__ void step1(const Step1Src& s, Row3 (&k1)[2][2], Row3 (&k0)[2][2], bool first,
+                                      const Coef32& cf, int tx, int ty, int tid) {
+  float4 res[4];
+  // coset 1: la = coset 0 at L1 (h_z = +1), lb = coset 0 at L1 + 1, own coset 1 at L1
+  pair_step<1, 0>(k1, first, s.c0a, s.c0b, s.c1a, ty, tx, cf, res);
+  store_smem<0>(s.p1c1, ty, tx, res);
+  // coset 0 at L1 + 1: la = coset 1 at L1, lb = coset 1 at L1 + 1, own coset 0 at L1 + 1
+  pair_step<0, 2>(k0, first, s.c1a, s.c1b, s.c0b, ty + 1, tx, cf, res);
+  store_smem<2>(s.p1c0, ty + 1, tx, res);
+  // remainder: e < 33: last row; 33 <= e < 41: pair k = 32 of rows 0..7 (coset 1 / 1..8 coset 0)
+  if (tid < 82) {
+    const int cs = tid < 41 ? 1 : 0;
+    const int e = tid < 41 ? tid : tid - 41;
+    const int k = e < 33 ? e : 32;
+    Row3 tmp[2][2];
+    if (cs == 1) {
+      const int R = e < 33 ? TY2 : e - 33;
+      pair_step<1, 0>(tmp, true, s.c0a, s.c0b, s.c1a, R, k, cf, res);
+      store_smem<0>(s.p1c1, R, k, res);
+    } else {
+      const int R = e < 33 ? TY2 + 1 : e - 33 + 1;
+      pair_step<0, 2>(tmp, true, s.c1a, s.c1b, s.c0b, R, k, cf, res);
+      store_smem<2>(s.p1c0, R, k, res);
+    }
   }
 }
 
@@ -189,16 +245,11 @@ __global__ void __launch_bounds__(NT2, 1)
     store_fix(buf0(0, zs), fC0);
     store_fix(buf0(1, zs), fC1);
     ok = __syncthreads_and(ok);
+    // z-reuse carries: step 1 (psi1 coset 1 / coset 0) and step 2 (output coset 0 / 1)
+    Row3 k1[2][2], k0[2][2], q0[2][2], q1[2][2];
     if (ok) {
-      constexpr int W = TX + 1, CELLS = W * (TY2 + 1);
-      for (int k = tid; k < CELLS; k += NT2) {
-        const int r = k / W, q = 1 + (k - (k / W) * W);
-        cell_step<1>(buf0(0, zs - 1), buf0(0, zs), buf0(1, zs - 1), buf1(1, zs - 1), r, q, cf);
-      }
-      for (int k = tid; k < CELLS; k += NT2) {
-        const int r = 1 + k / W, q = 2 + (k - (k / W) * W);
-        cell_step<0>(buf0(1, zs - 1), buf0(1, zs), buf0(0, zs), buf1(0, zs), r, q, cf);
-      }
+      const Step1Src s{buf0(0, zs - 1), buf0(0, zs), buf0(1, zs - 1), buf0(1, zs), buf1(1, zs - 1), buf1(0, zs)};
+      step1(s, k1, k0, true, cf, tx, ty, tid);
     }
     __syncthreads();
 
@@ -220,7 +271,10 @@ __global__ void __launch_bounds__(NT2, 1)
       ok = __syncthreads_and(ok);
       if (!ok) break;
       // step 1: psi1 coset 1 at layer i, coset 0 at layer i+1
-      step1(buf0(0, i), buf0(0, i + 1), buf0(1, i), buf0(1, i + 1), buf1(1, i), buf1(0, i + 1), cf, tid);
+      {
+        const Step1Src s{buf0(0, i), buf0(0, i + 1), buf0(1, i), buf0(1, i + 1), buf1(1, i), buf1(0, i + 1)};
+        step1(s, k1, k0, false, cf, tx, ty, tid);
+      }
       __syncthreads();
       // step 2: psi2 at layer i of the tile
       {
@@ -228,8 +282,13 @@ __global__ void __launch_bounds__(NT2, 1)
         const int64_t orow = (int64_t)i * plane + (int64_t)(y0 + ty) * M + x0;
         float4* d0 = reinterpret_cast<float4*>(out + orow) + tx;
         float4* d1 = reinterpret_cast<float4*>(out + 4 * vol + orow) + tx;
-        compute<0, CS2>(buf1(1, i - 1), buf1(1, i), buf1(0, i), d0, v4, cf, tx, ty);
-        compute<1, CS2>(buf1(0, i), buf1(0, i + 1), buf1(1, i), d1, v4, cf, tx, ty);
+        float4 res[4];
+        pair_step<0, 2>(q0, i == zs, buf1(1, i - 1), buf1(1, i), buf1(0, i), ty + 1, tx, cf, res);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d0[q * v4] = res[q];
+        pair_step<1, 2>(q1, i == zs, buf1(0, i), buf1(0, i + 1), buf1(1, i), ty + 1, tx, cf, res);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d1[q * v4] = res[q];
       }
       __syncthreads();
 #pragma unroll
