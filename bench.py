@@ -35,10 +35,11 @@ if ROOT not in sys.path:
 WORKLOAD = {"name": "bcc_N512_stencil_c64", "dim": 3, "N": 512, "mass": 0.1, "sigma": 32.0,
             "k0": (0.3, 0.2, 0.1), "substeps": 100}
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes (read + write) per launch of a stencil kernel from one ncu capture of it, per site:
-# step3d_c64_tma_kernel at BCC N=384 moved 470.5 MB + 409.9 MB for 14,155,776 sites.  Traffic grows in
-# proportion to the sites, so bench.py reports sites x this figure; kernels without a capture get null.
-NCU_TRAFFIC_BYTES_PER_SITE = {"step3d_c64_tma_kernel": (470507520 + 409899264) / 14155776}
+# DRAM bytes (read + write) per launch of a stencil kernel from one ncu capture of it at BCC N=384
+# (14,155,776 sites), per site.  Traffic grows in proportion to the sites, so bench.py reports
+# sites x this figure; kernels without a capture get null.
+NCU_TRAFFIC_BYTES_PER_SITE = {"step3d_c64_tma_kernel": (469785600 + 409331968) / 14155776,
+                              "step3d_c64_tma2_kernel": (476389632 + 407873280) / 14155776}
 
 
 def parse():
@@ -271,7 +272,12 @@ def run_ours(args, rank, world, local):
         return
     peak, peak_kind = measured_peaks()
     per_launch_ms = stencil_ms / (args.steps * stencil_launches)
-    achieved = 2 * field_bytes / (per_launch_ms / 1e3) / 1e9   # one read + one write of the field per launch
+    # algorithmic bytes per launch: 64 B per site-step (one read + one write of 4 complex64, the
+    # unfused minimum) x the site-steps one launch advances; a fused launch moves one read + one
+    # write of the field for `fused` steps, so its own HBM rate is reported beside it
+    alg_bytes = 2 * field_bytes * fused
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    fused_hbm = 2 * field_bytes / (per_launch_ms / 1e3) / 1e9
     line = {
         "metric": "site-steps/s", "value": value, "unit": "site-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -285,13 +291,15 @@ def run_ours(args, rank, world, local):
                      "frac": achieved / peak,
                      "traffic": (NCU_TRAFFIC_BYTES_PER_SITE[kernel_name] * sites
                                  if kernel_name in NCU_TRAFFIC_BYTES_PER_SITE else None),
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at BCC N=384, "
-                                       "scaled by sites (profiles/step3d_c64_tma_kernel_bcc_N384.txt)",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel at "
+                                       "BCC N=384, scaled by sites (profiles/%s_bcc_N384.txt)" % kernel_name,
                      "kernel": kernel_name, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": 2 * field_bytes,
+                     "algorithmic_bytes_per_launch": alg_bytes,
                      "steps_per_launch": fused,
+                     "kernel_hbm_GBps": fused_hbm,
+                     "kernel_hbm_frac": fused_hbm / peak,
                      "avg_launch_ms": per_launch_ms,
-                     "site_steps_per_s_at_roofline": peak * 1e9 / (2 * field_bytes) * fused * sites},
+                     "site_steps_per_s_at_roofline": peak * 1e9 / (2 * field_bytes) * sites},
         "e2e": {"value": sites * S / (e2e_ms / 1e3), "unit": "site-steps/s",
                 "h2d_bytes_per_step": field_bytes, "d2h_bytes_per_step": 48, "ms_per_step": e2e_ms},
         "gpu_launches": args.steps * launches_per_step,

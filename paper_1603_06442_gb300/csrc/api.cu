@@ -53,11 +53,11 @@ bool make_geometry(int dim, int64_t N, Geometry* g) {
 }
 
 static int default_stencil(const qw_plan_s* p) {
-  // measured on GB300: the one-step TMA kernel is the fastest where it applies
-  // (the fused two-step kernel trades half the HBM traffic for a compute-bound
-  // halo ring at one CTA per SM); qw_plan_autotune re-measures on the device.
-  if (stencil_supported(p->g, p->dtype, QW_STENCIL_TMA)) return QW_STENCIL_TMA;
+  // measured on GB300 (BCC N = 512): the fused two-step kernel (one HBM pass per
+  // two steps, shared-memory bound) ahead of the one-step TMA kernel (HBM bound);
+  // qw_plan_autotune re-measures on the device.
   if (stencil_supported(p->g, p->dtype, QW_STENCIL_TMA2)) return QW_STENCIL_TMA2;
+  if (stencil_supported(p->g, p->dtype, QW_STENCIL_TMA)) return QW_STENCIL_TMA;
   if (stencil_supported(p->g, p->dtype, QW_STENCIL_VEC)) return QW_STENCIL_VEC;
   return QW_STENCIL_PLAIN;
 }

@@ -104,19 +104,52 @@ __device__ __forceinline__ Row3 srow(const float* row, int tx) {
   return r;
 }
 
-template <int HY, int HZ>
-__device__ __forceinline__ void pair(float2 (&S)[2][4], const Row3& a, const Row3& b, const Row3& cd) {
-  constexpr int PP = HY * HZ, PM = -HY * HZ;
-  if constexpr (HZ == 1) {
-    cmac<1, -PP>(S[0][0], a.lo);  cmac<1, -HY>(S[0][0], b.lo);  cmac<-1, HY>(S[0][2], cd.lo);  cmac<1, -PP>(S[0][3], cd.lo);
-    cmac<1, -PP>(S[1][0], a.mid); cmac<1, -HY>(S[1][0], b.mid); cmac<-1, HY>(S[1][2], cd.mid); cmac<1, -PP>(S[1][3], cd.mid);
-    cmac<1, -PM>(S[0][0], a.mid); cmac<-1, -HY>(S[0][0], b.mid); cmac<1, HY>(S[0][2], cd.mid); cmac<1, -PM>(S[0][3], cd.mid);
-    cmac<1, -PM>(S[1][0], a.hi);  cmac<-1, -HY>(S[1][0], b.hi);  cmac<1, HY>(S[1][2], cd.hi);  cmac<1, -PM>(S[1][3], cd.hi);
-  } else {
-    cmac<1, HY>(S[0][1], a.lo);  cmac<1, -PP>(S[0][1], b.lo);  cmac<1, -PP>(S[0][2], cd.lo);  cmac<-1, -HY>(S[0][3], cd.lo);
-    cmac<1, HY>(S[1][1], a.mid); cmac<1, -PP>(S[1][1], b.mid); cmac<1, -PP>(S[1][2], cd.mid); cmac<-1, -HY>(S[1][3], cd.mid);
-    cmac<-1, HY>(S[0][1], a.mid); cmac<1, -PM>(S[0][1], b.mid); cmac<1, -PM>(S[0][2], cd.mid); cmac<1, -HY>(S[0][3], cd.mid);
-    cmac<-1, HY>(S[1][1], a.hi);  cmac<1, -PM>(S[1][1], b.hi);  cmac<1, -PM>(S[1][2], cd.hi);  cmac<1, -HY>(S[1][3], cd.hi);
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// Neighbour sums S0..S3 of cell J (0: lo/mid, 1: mid/hi columns) from the source rows
+// of the two z-layers (index 0: h_y = +1 row, 1: h_y = -1 row):
+//   h_z = +1 layer: components a, b, d;  h_z = -1 layer: components a2, b2, c2.
+// The transition matrices (entries (+-1 +- i)/4, derived in stencil.cu) give, per
+// source layer, terms (1 - i p) v and (+-h_x +- i h_y) v with p = h_x h_y h_z;
+// grouped over the four (h_x, h_y) neighbours of a layer, with v_{xy} the value at
+// h = (x, y),
+//   P = v_{++} + v_{--},  Q = v_{+-} + v_{-+},  U = v_{++} - v_{--},  V = v_{+-} - v_{-+},
+// the sums of (1 -+ i h_x h_y) v are (P + Q) -+ i (P - Q) and those of (h_x -+ i h_y) v
+// are (U + V) -+ i (U - V); 80 additions per cell instead of 128.
+template <int J>
+__device__ __forceinline__ float2 colp(const Row3& r) { return J == 0 ? r.lo : r.mid; }  // h_x = +1
+template <int J>
+__device__ __forceinline__ float2 colm(const Row3& r) { return J == 0 ? r.mid : r.hi; }  // h_x = -1
+
+template <int J>
+__device__ __forceinline__ void bcc_sums(float2 (&S)[4], const Row3 (&a)[2], const Row3 (&b)[2], const Row3 (&d)[2],
+                                         const Row3 (&a2)[2], const Row3 (&b2)[2], const Row3 (&c2)[2]) {
+  // h_z = +1
+  const float2 PA = cadd(colp<J>(a[0]), colm<J>(a[1])), QA = cadd(colp<J>(a[1]), colm<J>(a[0]));
+  const float2 UB = csub(colp<J>(b[0]), colm<J>(b[1])), VB = csub(colp<J>(b[1]), colm<J>(b[0]));
+  const float2 PD = cadd(colp<J>(d[0]), colm<J>(d[1])), QD = cadd(colp<J>(d[1]), colm<J>(d[0]));
+  const float2 UD = csub(colp<J>(d[0]), colm<J>(d[1])), VD = csub(colp<J>(d[1]), colm<J>(d[0]));
+  // h_z = -1
+  const float2 UA = csub(colp<J>(a2[0]), colm<J>(a2[1])), VA = csub(colp<J>(a2[1]), colm<J>(a2[0]));
+  const float2 PB = cadd(colp<J>(b2[0]), colm<J>(b2[1])), QB = cadd(colp<J>(b2[1]), colm<J>(b2[0]));
+  const float2 PC = cadd(colp<J>(c2[0]), colm<J>(c2[1])), QC = cadd(colp<J>(c2[1]), colm<J>(c2[0]));
+  const float2 UC = csub(colp<J>(c2[0]), colm<J>(c2[1])), VC = csub(colp<J>(c2[1]), colm<J>(c2[0]));
+  {  // S0 = sum (1 - i p) a + (h_x - i h_y) b   (h_z = +1)
+    const float2 al = cadd(PA, UB), be = cadd(QA, VB), s = cadd(al, be), t = csub(al, be);
+    S[0] = make_float2(s.x + t.y, s.y - t.x);
+  }
+  {  // S1 = sum (h_x + i h_y) a2 + (1 + i h_x h_y) b2   (h_z = -1)
+    const float2 al = cadd(UA, PB), be = cadd(VA, QB), s = cadd(al, be), t = csub(al, be);
+    S[1] = make_float2(s.x - t.y, s.y + t.x);
+  }
+  {  // S2 = sum (-h_x + i h_y) d + (1 + i h_x h_y) c2
+    const float2 X = cadd(csub(PC, UD), csub(QC, VD)), Y = csub(cadd(PC, UD), cadd(QC, VD));
+    S[2] = make_float2(X.x - Y.y, X.y + Y.x);
+  }
+  {  // S3 = sum (1 - i h_x h_y) d + (-h_x - i h_y) c2
+    const float2 X = cadd(csub(PD, UC), csub(QD, VC)), Y = csub(cadd(PD, UC), cadd(QD, VC));
+    S[3] = make_float2(X.x + Y.y, X.y - Y.x);
   }
 }
 
@@ -126,26 +159,22 @@ __device__ __forceinline__ void pair(float2 (&S)[2][4], const Row3& a, const Row
 template <int C, int CS>
 __device__ __forceinline__ void compute(const float* lay_a, const float* lay_b, const float* own, float4* dst,
                                         int64_t v4, const Coef32& cf, int tx, int ty) {
-  float2 S[2][4];
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) S[j][q] = make_float2(0.f, 0.f);
   // box row of the h_y = +1 source: ty + C, of h_y = -1: ty + 1 + C
+  Row3 a[2], b[2], d[2], a2[2], b2[2], c2[2];
 #pragma unroll
   for (int iy = 0; iy < 2; ++iy) {
-    const int r = ty + C + iy;
-    const float* base = lay_a + r * ROWF;
-    Row3 a = srow<C>(base, tx), b = srow<C>(base + CS, tx), d = srow<C>(base + 3 * CS, tx);
-    if (iy == 0) pair<+1, +1>(S, a, b, d); else pair<-1, +1>(S, a, b, d);
+    const float* base = lay_a + (ty + C + iy) * ROWF;
+    a[iy] = srow<C>(base, tx);
+    b[iy] = srow<C>(base + CS, tx);
+    d[iy] = srow<C>(base + 3 * CS, tx);
+    const float* bb = lay_b + (ty + C + iy) * ROWF;
+    a2[iy] = srow<C>(bb, tx);
+    b2[iy] = srow<C>(bb + CS, tx);
+    c2[iy] = srow<C>(bb + 2 * CS, tx);
   }
-#pragma unroll
-  for (int iy = 0; iy < 2; ++iy) {
-    const int r = ty + C + iy;
-    const float* base = lay_b + r * ROWF;
-    Row3 a = srow<C>(base, tx), b = srow<C>(base + CS, tx), c = srow<C>(base + 2 * CS, tx);
-    if (iy == 0) pair<+1, -1>(S, a, b, c); else pair<-1, -1>(S, a, b, c);
-  }
+  float2 S[2][4];
+  bcc_sums<0>(S[0], a, b, d, a2, b2, c2);
+  bcc_sums<1>(S[1], a, b, d, a2, b2, c2);
   const float* ob = own + (ty + 1) * ROWF + 4 * tx + 4;
   float4 o[4];
 #pragma unroll

@@ -16,7 +16,7 @@
 // The kernel is bound by shared-memory bandwidth, so every thread computes two
 // x-adjacent cells from three loaded columns and keeps, in registers, the
 // components its next z-step reads again (pair_step), cutting shared-memory loads
-// per cell by a third.
+// per cell by a third, and forms the neighbour sums in butterfly order (bcc_sums).
 // Edge tiles get the periodic images of out-of-range cells as in the one-step kernel.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -79,11 +79,7 @@ template <int C, int QOFF>
 __device__ __forceinline__ void pair_step(Row3 (&carry)[2][2], bool first, const float* la, const float* lb,
                                           const float* own, int R, int tx, const Coef32& cf, float4 (&res)[4]) {
   constexpr int OFF = QOFF - 1 + C;
-  float2 S[2][4];
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) S[j][q] = make_float2(0.f, 0.f);
+  Row3 d[2], a2[2], b2[2], c2[2];
 #pragma unroll
   for (int iy = 0; iy < 2; ++iy) {
     const float* base = la + (R - 1 + C + iy) * ROWF;
@@ -91,18 +87,20 @@ __device__ __forceinline__ void pair_step(Row3 (&carry)[2][2], bool first, const
       carry[iy][0] = srow_at<OFF>(base, tx);
       carry[iy][1] = srow_at<OFF>(base + CS2, tx);
     }
-    const Row3 d = srow_at<OFF>(base + 3 * CS2, tx);
-    if (iy == 0) pair<+1, +1>(S, carry[0][0], carry[0][1], d);
-    else pair<-1, +1>(S, carry[1][0], carry[1][1], d);
+    d[iy] = srow_at<OFF>(base + 3 * CS2, tx);
+    const float* bb = lb + (R - 1 + C + iy) * ROWF;
+    a2[iy] = srow_at<OFF>(bb, tx);
+    b2[iy] = srow_at<OFF>(bb + CS2, tx);
+    c2[iy] = srow_at<OFF>(bb + 2 * CS2, tx);
   }
+  const Row3 a[2] = {carry[0][0], carry[1][0]}, b[2] = {carry[0][1], carry[1][1]};
+  float2 S[2][4];
+  bcc_sums<0>(S[0], a, b, d, a2, b2, c2);
+  bcc_sums<1>(S[1], a, b, d, a2, b2, c2);
 #pragma unroll
   for (int iy = 0; iy < 2; ++iy) {
-    const float* base = lb + (R - 1 + C + iy) * ROWF;
-    const Row3 a = srow_at<OFF>(base, tx), b = srow_at<OFF>(base + CS2, tx), c = srow_at<OFF>(base + 2 * CS2, tx);
-    if (iy == 0) pair<+1, -1>(S, a, b, c);
-    else pair<-1, -1>(S, a, b, c);
-    carry[iy][0] = a;
-    carry[iy][1] = b;
+    carry[iy][0] = a2[iy];
+    carry[iy][1] = b2[iy];
   }
   const float* ob = own + R * ROWF + 2 * (2 * tx + QOFF);
   float4 o[4];
@@ -129,7 +127,7 @@ __device__ __forceinline__ void store_smem(float* dst, int R, int tx, const floa
 //   coset 0 at layer L1+1 on rows [1, TY2+2), columns [2, 67): pairs at Q0 = 2k + 2, k < 33.
 // Thread (tx, ty) owns the pair k = tx of row ty (coset 1) and ty + 1 (coset 0),
 // with z-reuse; the last row and the pair k = 32 of each coset (82 pairs) go to
-// threads 0..81 without it.
+// warps 0..3 without it, one kind per warp.
 struct Step1Src {
   const float *c0a, *c0b, *c1a, *c1b;  // psi0 coset 0 / 1 at layers L1 (a) and L1 + 1 (b)
   float *p1c1, *p1c0;                  // psi1 destinations: coset 1 at L1, coset 0 at L1 + 1
@@ -144,20 +142,21 @@ __device__ __forceinline__ void step1(const Step1Src& s, Row3 (&k1)[2][2], Row3 
   // coset 0 at L1 + 1: la = coset 1 at L1, lb = coset 1 at L1 + 1, own coset 0 at L1 + 1
   pair_step<0, 2>(k0, first, s.c1a, s.c1b, s.c0b, ty + 1, tx, cf, res);
   store_smem<2>(s.p1c0, ty + 1, tx, res);
-  // remainder: e < 33: last row; 33 <= e < 41: pair k = 32 of rows 0..7 (coset 1 / 1..8 coset 0)
-  if (tid < 82) {
-    const int cs = tid < 41 ? 1 : 0;
-    const int e = tid < 41 ? tid : tid - 41;
-    const int k = e < 33 ? e : 32;
+  // remainder, one warp per kind: warp 0 coset 1 row TY2, warp 1 coset 0 row TY2 + 1,
+  // warp 2 coset 1 pair k = 32 of rows 0..TY2, warp 3 coset 0 pair k = 32 of rows 1..TY2+1
+  const int w = tid >> 5;
+  if (w < 2 || (w < 4 && tx <= TY2)) {
     Row3 tmp[2][2];
-    if (cs == 1) {
-      const int R = e < 33 ? TY2 : e - 33;
-      pair_step<1, 0>(tmp, true, s.c0a, s.c0b, s.c1a, R, k, cf, res);
-      store_smem<0>(s.p1c1, R, k, res);
+    const bool col = w >= 2;
+    const int kk = col ? 32 : tx;
+    if ((w & 1) == 0) {
+      const int R = col ? tx : TY2;
+      pair_step<1, 0>(tmp, true, s.c0a, s.c0b, s.c1a, R, kk, cf, res);
+      store_smem<0>(s.p1c1, R, kk, res);
     } else {
-      const int R = e < 33 ? TY2 + 1 : e - 33 + 1;
-      pair_step<0, 2>(tmp, true, s.c1a, s.c1b, s.c0b, R, k, cf, res);
-      store_smem<2>(s.p1c0, R, k, res);
+      const int R = col ? tx + 1 : TY2 + 1;
+      pair_step<0, 2>(tmp, true, s.c1a, s.c1b, s.c0b, R, kk, cf, res);
+      store_smem<2>(s.p1c0, R, kk, res);
     }
   }
 }
