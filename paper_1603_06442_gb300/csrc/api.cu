@@ -85,7 +85,7 @@ static qw_status prepare_spectral(qw_plan_s* p) {
   const int nq = p->g.dim == 3 ? 2 : 1;
   QW_CHECK_CUDA(cudaMalloc(&p->omega, sizeof(double) * nq * p->g.vol));
   QW_CHECK_CUDA(cudaMalloc(&p->spec_partials, sizeof(double) * 2 * kObsBlocks));
-  st = launch_omega_table(p->g, spec_axes(p->g, p->fft), p->n, p->mass, p->omega, 0);
+  st = launch_omega_table(p->g, spec_axes(p->g, p->fft), p->n, p->mass, p->omega, 0, p->dtype == QW_C64);
   if (st != QW_OK) return st;
   QW_CHECK_CUDA(cudaDeviceSynchronize());
   p->spec_ready = true;
@@ -273,6 +273,16 @@ qw_status qw_evolve_spectral(qw_plan p, void* psi, int64_t t, void* stream) {
   st = prepare_spectral(p);
   if (st != QW_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (fused_x_supported(p->g, p->fft, p->dtype)) {
+    // y, z forward; x forward + D_k^t + x inverse in one pass; y, z inverse
+    for (int ax = p->g.dim - 1; ax >= 1; --ax)
+      if ((st = fft_forward_axis(p->fft, ax, psi, s)) != QW_OK) return st;
+    st = launch_evolve_fused_x(p->g, spec_axes(p->g, p->fft), p->fft, p->n, p->mass, p->omega, t, psi, s);
+    if (st != QW_OK) return st;
+    for (int ax = 1; ax < p->g.dim; ++ax)
+      if ((st = fft_inverse_axis(p->fft, ax, psi, s)) != QW_OK) return st;
+    return QW_OK;
+  }
   st = fft_forward(p->fft, p->g.dim, psi, s);
   if (st != QW_OK) return st;
   st = launch_evolve_pointwise(p->g, spec_axes(p->g, p->fft), p->dtype, p->n, p->mass, p->omega, t, psi, s);

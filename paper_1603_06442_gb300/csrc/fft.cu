@@ -25,130 +25,9 @@
 
 #include "qw_fft.cuh"
 #include "qw_internal.cuh"
+#include "qw_regdft.cuh"
 
 namespace qw {
-
-template <typename T> struct Cx;
-template <> struct Cx<float> { using t = float2; };
-template <> struct Cx<double> { using t = double2; };
-
-template <typename V>
-__device__ __forceinline__ V cmul(V a, V b) {
-  V r;
-  r.x = a.x * b.x - a.y * b.y;
-  r.y = a.x * b.y + a.y * b.x;
-  return r;
-}
-template <typename V>
-__device__ __forceinline__ V cmulc(V a, V b) {  // a * conj(b)
-  V r;
-  r.x = a.x * b.x + a.y * b.y;
-  r.y = a.y * b.x - a.x * b.y;
-  return r;
-}
-template <typename V>
-__device__ __forceinline__ V cadd(V a, V b) {
-  a.x += b.x;
-  a.y += b.y;
-  return a;
-}
-template <typename V>
-__device__ __forceinline__ V csub(V a, V b) {
-  a.x -= b.x;
-  a.y -= b.y;
-  return a;
-}
-// multiply by -i (forward) or +i (inverse)
-template <bool INV, typename V>
-__device__ __forceinline__ V mul_mi(V a) {
-  V r;
-  if (INV) {
-    r.x = -a.y;
-    r.y = a.x;
-  } else {
-    r.x = a.y;
-    r.y = -a.x;
-  }
-  return r;
-}
-
-template <bool INV, typename V>
-__device__ __forceinline__ void dft2(V& a0, V& a1) {
-  V t = a0;
-  a0 = cadd(t, a1);
-  a1 = csub(t, a1);
-}
-
-template <bool INV, typename V>
-__device__ __forceinline__ void dft4(V& a0, V& a1, V& a2, V& a3) {
-  V s02 = cadd(a0, a2), d02 = csub(a0, a2);
-  V s13 = cadd(a1, a3), d13 = mul_mi<INV>(csub(a1, a3));
-  a0 = cadd(s02, s13);
-  a2 = csub(s02, s13);
-  a1 = cadd(d02, d13);
-  a3 = csub(d02, d13);
-}
-
-template <bool INV, typename T, typename V>
-__device__ __forceinline__ void dft3(V& a0, V& a1, V& a2) {
-  const T h = (T)0.86602540378443864676;  // sqrt(3)/2
-  V t1 = cadd(a1, a2), t2 = csub(a1, a2);
-  V b0 = cadd(a0, t1);
-  V m;
-  m.x = a0.x - (T)0.5 * t1.x;
-  m.y = a0.y - (T)0.5 * t1.y;
-  // forward: X1 = m - i h t2, X2 = m + i h t2 (inverse swaps)
-  V r;
-  r.x = h * t2.y;
-  r.y = -h * t2.x;  // -i h t2
-  if (INV) {
-    r.x = -r.x;
-    r.y = -r.y;
-  }
-  a0 = b0;
-  a1 = cadd(m, r);
-  a2 = csub(m, r);
-}
-
-template <bool INV, typename T, typename V>
-__device__ __forceinline__ void dft8(V (&a)[8]) {
-  // even/odd split into two radix-4 transforms
-  dft4<INV>(a[0], a[2], a[4], a[6]);
-  dft4<INV>(a[1], a[3], a[5], a[7]);
-  const T r2 = (T)0.70710678118654752440;
-  // twiddles w8^k, w8 = exp(-+ 2 pi i / 8)
-  V o1 = a[3], o2 = a[5], o3 = a[7];
-  V w1, w3;
-  if (INV) {
-    w1.x = r2 * (o1.x - o1.y);
-    w1.y = r2 * (o1.x + o1.y);
-    w3.x = -r2 * (o3.x + o3.y);
-    w3.y = r2 * (o3.x - o3.y);
-  } else {
-    w1.x = r2 * (o1.x + o1.y);
-    w1.y = r2 * (o1.y - o1.x);
-    w3.x = r2 * (o3.y - o3.x);
-    w3.y = -r2 * (o3.x + o3.y);
-  }
-  V w2 = mul_mi<INV>(o2);
-  V e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6], o0 = a[1];
-  a[0] = cadd(e0, o0);
-  a[4] = csub(e0, o0);
-  a[1] = cadd(e1, w1);
-  a[5] = csub(e1, w1);
-  a[2] = cadd(e2, w2);
-  a[6] = csub(e2, w2);
-  a[3] = cadd(e3, w3);
-  a[7] = csub(e3, w3);
-}
-
-// omega_N^m = exp(-2 pi i m / N) from the two-level table (m < N)
-template <typename V>
-__device__ __forceinline__ V twiddle_big(const V* hi, const V* lo, int64_t m, int tlo_bits) {
-  const int64_t mh = m >> tlo_bits;
-  const int64_t ml = m & ((int64_t(1) << tlo_bits) - 1);
-  return cmul(hi[mh], lo[ml]);
-}
 
 template <typename T, bool INV>
 __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __restrict__ data, FftPass p,
@@ -291,155 +170,6 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __rest
   }
 }
 
-// ------------------------------------------------- two-factor register kernel
-// Lines of length L = R1 * R2 (R1, R2 in 4, 8, 16): n = n1 + R1 n2,
-//   Y[n1][k2] = omega_L^{n1 k2} sum_{n2} x[n1 + R1 n2] omega_{R2}^{n2 k2}   (step A, registers)
-//   X[k2 + R2 k1] = sum_{n1} Y[n1][k2] omega_{R1}^{n1 k1}                   (step B, registers)
-// with one shared-memory exchange between the steps; index maps are
-// compile-time, so the per-element cost is the butterflies, not the indexing.
-template <int R, bool INV, typename T, typename V> struct RegDFT;
-template <bool INV, typename T, typename V> struct RegDFT<2, INV, T, V> {
-  __device__ __forceinline__ static void run(V (&a)[2]) { dft2<INV>(a[0], a[1]); }
-};
-template <bool INV, typename T, typename V> struct RegDFT<4, INV, T, V> {
-  __device__ __forceinline__ static void run(V (&a)[4]) { dft4<INV>(a[0], a[1], a[2], a[3]); }
-};
-template <bool INV, typename T, typename V> struct RegDFT<8, INV, T, V> {
-  __device__ __forceinline__ static void run(V (&a)[8]) { dft8<INV, T>(a); }
-};
-template <bool INV, typename T, typename V> struct RegDFT<16, INV, T, V> {
-  __device__ __forceinline__ static void run(V (&a)[16]) {
-    // even / odd halves, then X_k = E_k + w16^k O_k, X_{k+8} = E_k - w16^k O_k
-    V e[8], o[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      e[j] = a[2 * j];
-      o[j] = a[2 * j + 1];
-    }
-    dft8<INV, T>(e);
-    dft8<INV, T>(o);
-    const T cs[8] = {(T)1.0, (T)0.92387953251128675613, (T)0.70710678118654752440, (T)0.38268343236508977173,
-                     (T)0.0, (T)-0.38268343236508977173, (T)-0.70710678118654752440, (T)-0.92387953251128675613};
-    const T sn[8] = {(T)0.0, (T)0.38268343236508977173, (T)0.70710678118654752440, (T)0.92387953251128675613,
-                     (T)1.0, (T)0.92387953251128675613, (T)0.70710678118654752440, (T)0.38268343236508977173};
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      V w;  // w16^k = cos - i sin (forward), cos + i sin (inverse)
-      w.x = cs[k];
-      w.y = INV ? sn[k] : -sn[k];
-      const V t = (k == 0) ? o[0] : cmul(o[k], w);
-      a[k] = cadd(e[k], t);
-      a[k + 8] = csub(e[k], t);
-    }
-  }
-};
-
-// Compile-time twiddles exp(-2 pi i m / R) for the composite register DFTs:
-// cos and sin of 2 pi m / R by a Taylor series after reduction to [-pi/4, pi/4]
-// (double precision; the values become immediates).
-constexpr double ce_pi = 3.14159265358979323846264338327950288;
-constexpr double ce_taylor_sin(double x) {
-  double term = x, sum = x;
-  for (int k = 1; k < 14; ++k) {
-    term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
-    sum += term;
-  }
-  return sum;
-}
-constexpr double ce_taylor_cos(double x) {
-  double term = 1.0, sum = 1.0;
-  for (int k = 1; k < 14; ++k) {
-    term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
-    sum += term;
-  }
-  return sum;
-}
-// angle 2 pi m / R, m in [0, R): octant reduction with exact rational arithmetic
-constexpr double ce_trig(int m, int R, bool want_sin) {
-  const int num = 8 * m, q = num / R;                  // octant
-  const double f = (double)(num - q * R) / (double)R;  // fraction of an octant
-  const double x = f * ce_pi / 4.0;
-  const double sx = ce_taylor_sin(x), cx = ce_taylor_cos(x);
-  const double sy = ce_taylor_sin(ce_pi / 4.0 - x), cy = ce_taylor_cos(ce_pi / 4.0 - x);
-  double s = 0.0, c = 0.0;
-  switch (q & 7) {
-    case 0: s = sx; c = cx; break;
-    case 1: s = cy; c = sy; break;
-    case 2: s = cx; c = -sx; break;
-    case 3: s = sy; c = -cy; break;
-    case 4: s = -sx; c = -cx; break;
-    case 5: s = -cy; c = -sy; break;
-    case 6: s = -cx; c = sx; break;
-    default: s = -sy; c = cy; break;
-  }
-  return want_sin ? s : c;
-}
-
-constexpr int reg_first_factor(int R) {
-  // split R = P * Q with Q the factor transformed first
-  return (R % 16 == 0 && R > 16) ? 16 : (R % 8 == 0 && R > 8) ? 8 : (R % 4 == 0 && R > 4) ? 4
-       : (R % 3 == 0 && R > 3) ? R / 3 : (R % 2 == 0 && R > 2) ? 2 : R;
-}
-
-template <bool INV, typename T, typename V> struct RegDFT<3, INV, T, V> {
-  __device__ __forceinline__ static void run(V (&a)[3]) { dft3<INV, T>(a[0], a[1], a[2]); }
-};
-
-// Composite R = P * Q (P = reg_first_factor(R)): Q-point DFTs over a[p + P q],
-// twiddle exp(-+2 pi i p k2 / R), P-point DFTs over p; output index k2 + Q k1.
-// The (p, k2) loops are template recursions so every twiddle is a constant.
-template <int R, int Q, int p, int k2, bool INV, typename T, typename V>
-struct TwApply {
-  __device__ __forceinline__ static void run(const V (&b)[Q], V (&t)[R]) {
-    if constexpr (k2 < Q) {
-      constexpr int m = (p * k2) % R;
-      if constexpr (m == 0) {
-        t[p * Q + k2] = b[k2];
-      } else {
-        constexpr double c = ce_trig(m, R, false), sn = ce_trig(m, R, true);
-        V w;
-        w.x = (T)c;
-        w.y = INV ? (T)sn : (T)-sn;
-        t[p * Q + k2] = cmul(b[k2], w);
-      }
-      TwApply<R, Q, p, k2 + 1, INV, T, V>::run(b, t);
-    }
-  }
-};
-
-template <int R, int P, int Q, int p, bool INV, typename T, typename V>
-struct StepA {
-  __device__ __forceinline__ static void run(const V (&a)[R], V (&t)[R]) {
-    if constexpr (p < P) {
-      V b[Q];
-#pragma unroll
-      for (int q = 0; q < Q; ++q) b[q] = a[p + P * q];
-      RegDFT<Q, INV, T, V>::run(b);
-      TwApply<R, Q, p, 0, INV, T, V>::run(b, t);
-      StepA<R, P, Q, p + 1, INV, T, V>::run(a, t);
-    }
-  }
-};
-
-template <int R, bool INV, typename T, typename V>
-struct RegDFT {
-  static constexpr int P = reg_first_factor(R);
-  static constexpr int Q = R / P;
-  __device__ __forceinline__ static void run(V (&a)[R]) {
-    V t[R];
-    StepA<R, P, Q, 0, INV, T, V>::run(a, t);
-#pragma unroll
-    for (int k2 = 0; k2 < Q; ++k2) {
-      V c[P];
-#pragma unroll
-      for (int p = 0; p < P; ++p) c[p] = t[p * Q + k2];
-      RegDFT<P, INV, T, V>::run(c);
-#pragma unroll
-      for (int k1 = 0; k1 < P; ++k1) a[k2 + Q * k1] = c[k1];
-    }
-  }
-};
-
 template <typename T, bool INV, int R1, int R2, bool CONTIG>
 __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restrict__ data, FftPass p,
                                                     const typename Cx<T>::t* __restrict__ tw_line,
@@ -465,63 +195,54 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restric
     base = o * (int64_t)L * S + i;
     tw_b = i / p.tw_div;
   }
-  // ---- load into shared memory, element n of line c at sm[c + CP n]
+  // twiddles of step A, fetched before the data so their latency overlaps the loads
+  V tw[R2];
+  if (r < R1) {
+#pragma unroll
+    for (int k2 = 1; k2 < R2; ++k2) tw[k2] = tw_line[r * k2];  // omega_L^{n1 k2}
+  }
+  // ---- load into shared memory, element n of line c at sm[c + CP n]; every load of
+  // the thread is issued before the first shared-memory store (full unroll)
   if (CONTIG) {  // S == 1: the CTA's lines are one contiguous run
-#pragma unroll 4
-    for (int e = tid; e < C * L; e += 256) {
-      const int cc = e / L, n = e - cc * L;
-      const int64_t ll = l0 + cc;
-      V v;
-      v.x = 0;
-      v.y = 0;
-      if (ll < nlines) v = data[ll * L + n];
-      sm[cc + CP * n] = v;
+    constexpr int NE = (C * L + 255) / 256;
+    V v[NE];
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+      const int e = tid + 256 * j;
+      const int64_t ll = l0 + e / L;
+      v[j].x = 0;
+      v[j].y = 0;
+      if (e < C * L && ll < nlines) v[j] = data[l0 * L + e];
+    }
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+      const int e = tid + 256 * j;
+      if (e < C * L) {
+        const int cc = e / L, n = e - cc * L;
+        sm[cc + CP * n] = v[j];
+      }
     }
   } else if (r < TPL) {
-#pragma unroll 4
-    for (int n = r; n < L; n += TPL) {
-      V v;
-      v.x = 0;
-      v.y = 0;
-      if (live) {
-        v = data[base + (int64_t)n * S];
-        if (INV && p.twiddle) v = cmulc(v, twiddle_big(tw_hi, tw_lo, (int64_t)n * tw_b, p.tlo_bits));
+    constexpr int NL = (L + TPL - 1) / TPL;
+    V v[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const int n = r + TPL * j;
+      v[j].x = 0;
+      v[j].y = 0;
+      if (live && n < L) v[j] = data[base + (int64_t)n * S];
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const int n = r + TPL * j;
+      if (n < L) {
+        if (INV && p.twiddle && live) v[j] = cmulc(v[j], twiddle_big(tw_hi, tw_lo, (int64_t)n * tw_b, p.tlo_bits));
+        sm[c + CP * n] = v[j];
       }
-      sm[c + CP * n] = v;
     }
   }
   __syncthreads();
-  // ---- step A: thread r = n1 < R1
-  V a[R2];
-  if (r < R1) {
-#pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) a[n2] = sm[c + CP * (r + R1 * n2)];
-    RegDFT<R2, INV, T, V>::run(a);
-#pragma unroll
-    for (int k2 = 1; k2 < R2; ++k2) {
-      const V w = tw_line[r * k2];  // omega_L^{n1 k2}
-      a[k2] = INV ? cmulc(a[k2], w) : cmul(a[k2], w);
-    }
-  }
-  __syncthreads();
-  if (r < R1) {
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) sm[c + CP * (r * R2 + k2)] = a[k2];
-  }
-  __syncthreads();
-  // ---- step B: thread r = k2 < R2
-  V b[R1];
-  if (r < R2) {
-#pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) b[n1] = sm[c + CP * (n1 * R2 + r)];
-    RegDFT<R1, INV, T, V>::run(b);
-  }
-  __syncthreads();
-  if (r < R2) {
-#pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) sm[c + CP * (r + R2 * k1)] = b[k1];
-  }
-  __syncthreads();
+  reg_fft_steps<T, INV, R1, R2, CP>(sm, c, r, tw);
   // ---- store
   if (CONTIG) {
 #pragma unroll 4
@@ -579,44 +300,20 @@ static qw_status launch_2f(const FftPass& p, void* data, cudaStream_t st) {
 // Lengths with a two-factor register kernel; returns false for the generic path.
 // With p == nullptr nothing is launched: the call only reports whether L has one
 // (the planner uses this to split long axes into register-kernel passes).
-#define QW_2F(LEN, A, B)                                          \
-  case LEN:                                                       \
-    if (p) *out = launch_2f<T, INV, A, B>(*p, data, st);          \
+#define QW_2F(LEN, A, B)                                 \
+  case LEN:                                              \
+    if (p) *out = launch_2f<T, INV, A, B>(*p, data, st); \
     return true;
 template <typename T, bool INV>
 static bool run_2f(int L, const FftPass* p, void* data, cudaStream_t st, qw_status* out) {
   switch (L) {
-    QW_2F(16, 4, 4)
-    QW_2F(32, 8, 4)
-    QW_2F(64, 8, 8)
-    QW_2F(128, 16, 8)
-    QW_2F(256, 16, 16)
+    QW_REG_LENGTHS_POW2(QW_2F)
     default: break;
   }
   if (sizeof(T) != 4) return false;
   // lengths with a factor 3 (complex64; complex128 uses the Stockham kernel)
   switch (L) {
-    QW_2F(12, 4, 3)
-    QW_2F(18, 6, 3)
-    QW_2F(24, 8, 3)
-    QW_2F(27, 9, 3)
-    QW_2F(36, 6, 6)
-    QW_2F(48, 8, 6)
-    QW_2F(54, 9, 6)
-    QW_2F(72, 9, 8)
-    QW_2F(81, 9, 9)
-    QW_2F(96, 12, 8)
-    QW_2F(108, 12, 9)
-    QW_2F(144, 12, 12)
-    QW_2F(162, 18, 9)
-    QW_2F(192, 16, 12)
-    QW_2F(216, 18, 12)
-    QW_2F(243, 27, 9)
-    QW_2F(288, 18, 16)
-    QW_2F(324, 18, 18)
-    QW_2F(384, 24, 16)
-    QW_2F(432, 24, 18)
-    QW_2F(512, 32, 16)
+    QW_REG_LENGTHS_F32(QW_2F)
     default: return false;
   }
 }
@@ -835,7 +532,50 @@ static qw_status trig_tables(FftPlan* f, const Geometry& g) {
   }
   QW_CHECK_CUDA(cudaMalloc(&f->angle, ha.size() * sizeof(double2)));
   QW_CHECK_CUDA(cudaMemcpy(f->angle, ha.data(), ha.size() * sizeof(double2), cudaMemcpyHostToDevice));
-  return QW_OK;
+  // double-float tables: hi = RN(v), lo = RN(v - hi)
+  auto df4 = [](double c, double s) {
+    float4 r;
+    r.x = (float)c;
+    r.y = (float)(c - (double)r.x);
+    r.z = (float)s;
+    r.w = (float)(s - (double)r.z);
+    return r;
+  };
+  auto upload4 = [](const std::vector<float4>& h, void** dev) -> qw_status {
+    QW_CHECK_CUDA(cudaMalloc(dev, h.size() * sizeof(float4)));
+    QW_CHECK_CUDA(cudaMemcpy(*dev, h.data(), h.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    return QW_OK;
+  };
+  qw_status st;
+  if (g.dim == 1) {
+    const int64_t N = g.nx, B = kDfFine, nc = (N + B - 1) / B;
+    std::vector<float4> fine(B), coarse(nc);
+    for (int64_t q = 0; q < B; ++q) {
+      const double ang = 2.0 * M_PI * (double)(q % N) / (double)N;
+      fine[q] = df4(std::cos(ang), std::sin(ang));
+    }
+    for (int64_t q = 0; q < nc; ++q) {
+      const double ang = 2.0 * M_PI * (double)((q * B) % N) / (double)N;
+      coarse[q] = df4(std::cos(ang), std::sin(ang));
+    }
+    if ((st = upload4(fine, &f->trigdf[0])) != QW_OK) return st;
+    if ((st = upload4(coarse, &f->trigdf[1])) != QW_OK) return st;
+  } else {
+    for (int ax = 0; ax < (g.dim == 2 ? 1 : 3); ++ax) {
+      // the same angles as trig[ax]: 2D pi q / N (q < 2N), BCC pi q / M (q < M)
+      const int64_t len = g.dim == 2 ? 2 * g.nx : ext[ax];
+      const int64_t period = g.dim == 2 ? 2 * g.nx : 2 * ext[ax];
+      std::vector<float4> h(len);
+      for (int64_t q = 0; q < len; ++q) {
+        const double ang = 2.0 * M_PI * (double)(q % period) / (double)period;
+        h[q] = df4(std::cos(ang), std::sin(ang));
+      }
+      if ((st = upload4(h, &f->trigdf[ax])) != QW_OK) return st;
+    }
+  }
+  std::vector<float4> hd(kAngleTab + 1);
+  for (int j = 0; j <= kAngleTab; ++j) hd[j] = df4(ha[j].x, ha[j].y);
+  return upload4(hd, &f->angdf);
 }
 
 qw_status fft_plan_create(FftPlan* f, const Geometry& g, qw_dtype dt) {
@@ -855,6 +595,12 @@ void fft_plan_destroy(FftPlan* f) {
   }
   if (f->angle) cudaFree(f->angle);
   f->angle = nullptr;
+  for (int a = 0; a < 3; ++a) {
+    if (f->trigdf[a]) cudaFree(f->trigdf[a]);
+    f->trigdf[a] = nullptr;
+  }
+  if (f->angdf) cudaFree(f->angdf);
+  f->angdf = nullptr;
   for (int i = 0; i < f->npass; ++i) {
     if (f->pass[i].tw_line) cudaFree(f->pass[i].tw_line);
     if (f->pass[i].tw_hi) cudaFree(f->pass[i].tw_hi);

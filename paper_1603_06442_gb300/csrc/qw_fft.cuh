@@ -54,7 +54,15 @@ struct FftPlan {
   void* trig32[3] = {nullptr, nullptr, nullptr};  // the same tables as float2 (complex64 kernels)
   // (cos, sin)(j * kAngleStep), j <= kAngleTab: anchors of the fast omega_k refinement
   void* angle = nullptr;
+  // double-float copies (float4: cos hi, cos lo, sin hi, sin lo) of the symbol tables and
+  // the anchors, for the FP64-free omega_k of complex64 requests.  The chain (dim 1)
+  // uses two levels instead of a table as long as the chain: angle 2 pi (kDfFine q1 + q0) / N
+  // from trigdf[1][q1] (coarse) and trigdf[0][q0] (fine).
+  void* trigdf[3] = {nullptr, nullptr, nullptr};
+  void* angdf = nullptr;
 };
+
+constexpr int kDfFine = 4096;
 
 constexpr int kAngleTab = 1024;
 constexpr double kAngleStep = 3.14159265358979323846 / kAngleTab;

@@ -122,13 +122,23 @@ struct SpecAxes {  // digit split of each axis (storage order -> frequency) and 
   const double2* trig[3];
   const float2* trig32[3];
   const double2* angle;
+  const float4* trigdf[3];
+  const float4* angdf;
 };
 SpecAxes spec_axes(const Geometry& g, const FftPlan& f);
+// FP64 omega per wave vector, or (split, complex64 plans) nu = omega / 2 pi as an FP32
+// (hi, lo) pair in the same 8 bytes
 qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,
-                             cudaStream_t st);
+                             cudaStream_t st, bool split);
 // psi_hat (forward DFT, storage order) <- D_k^t psi_hat / |V|, BCC cosets mixed per cell;
 // with norm0 (device, optional) the result is also divided by sqrt(norm0[0]);
 // omega == nullptr computes omega_k in the kernel (FP64) instead of reading a table.
+// Fused x pass: forward DFT along x, D_k^t, inverse DFT along x (complex64, 2D/BCC,
+// x axis in one register pass); y and z are transformed around it by the caller.
+bool fused_x_supported(const Geometry& g, const FftPlan& f, qw_dtype dt);
+qw_status launch_evolve_fused_x(const Geometry& g, const SpecAxes& ax, const FftPlan& f, double n, double m,
+                                const double* omega, int64_t t, void* psi, cudaStream_t st,
+                                const double* norm0 = nullptr);
 qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
                                   const double* omega, int64_t t, void* psi_hat, cudaStream_t st,
                                   const double* norm0 = nullptr);
@@ -163,7 +173,8 @@ struct qw_plan_s {
   // spectral path (allocated by the first spectral call or qw_plan_prepare_spectral)
   bool spec_ready;
   qw::FftPlan fft;
-  double* omega;        // omega_k per stored wave vector (two per cell on the BCC lattice)
+  double* omega;        // omega_k per stored wave vector (two per cell on the BCC lattice); complex64
+                        // plans hold nu = omega / 2 pi as FP32 (hi, lo) pairs instead
   double* spec_partials;  // 2 * kObsBlocks doubles for the particle-weight reduction
   double* red_partials; // 4 * kObsBlocks doubles
   double* red_result;   // 4 doubles (device)

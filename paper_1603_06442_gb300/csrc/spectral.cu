@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "qw_internal.cuh"
+#include "qw_regdft.cuh"
 
 namespace qw {
 
@@ -46,6 +47,8 @@ struct AxesDev {
   const double2* trig[3];
   const float2* trig32[3];
   const double2* angle;
+  const float4* trigdf[3];
+  const float4* angdf;
 };
 
 SpecAxes spec_axes(const Geometry& g, const FftPlan& f) {
@@ -64,6 +67,8 @@ SpecAxes spec_axes(const Geometry& g, const FftPlan& f) {
     a.trig32[ax] = static_cast<const float2*>(f.trig32[ax]);
   }
   a.angle = static_cast<const double2*>(f.angle);
+  for (int ax = 0; ax < 3; ++ax) a.trigdf[ax] = static_cast<const float4*>(f.trigdf[ax]);
+  a.angdf = static_cast<const float4*>(f.angdf);
   return a;
 }
 
@@ -77,8 +82,32 @@ static AxesDev to_dev(const SpecAxes& a) {
     d.trig32[ax] = a.trig32[ax];
   }
   d.angle = a.angle;
+  for (int ax = 0; ax < 3; ++ax) d.trigdf[ax] = a.trigdf[ax];
+  d.angdf = a.angdf;
   return d;
 }
+
+// Mass coefficients n = sqrt(1 - m^2) and m in both precisions, and the step count t
+// (with its FP32 copy when t < 2^24), so that complex64 kernels convert nothing on
+// the FP64 pipe (FP64 runs at ~1/64 of the FP32 rate on this part).
+struct Mass {
+  double n, m;
+  float nf, mf;
+  float2 n_df, n2_df, m2_df;  // n, n^2, m^2 as double-float (hi, lo)
+};
+struct TimeArg {
+  double tt;
+  float tf;
+  int small;  // t < 2^24: the split-nu phase applies
+};
+static float2 split_df(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+static Mass make_mass(double n, double m) {
+  return Mass{n, m, (float)n, (float)m, split_df(n), split_df(n * n), split_df(m * m)};
+}
+static TimeArg make_time(int64_t t) { return TimeArg{(double)t, (float)t, t < (int64_t(1) << 24) ? 1 : 0}; }
 
 // Frequency index of storage position p on an axis split into digits
 // (A), (A, B) or (A, B1, B2): the passes leave frequency k1 + A k2 at B k1 + k2
@@ -169,7 +198,7 @@ __device__ __forceinline__ void coset_phase(int64_t fsum, int64_t M, T& ar, T& a
     ai = (T)s;
   } else {
     float s, c;
-    sincospif((float)q / (float)M, &s, &c);
+    sincospif((float)(int)q / (float)(int)M, &s, &c);  // 32-bit conversions (q < 2M <= 2^13)
     ar = (T)c;
     ai = (T)s;
   }
@@ -183,7 +212,11 @@ __device__ __forceinline__ bool grid_pos(const AxesDev& a, int64_t& x, int64_t& 
   return x < a.len[0];
 }
 
-__global__ void omega_kernel(int dim, AxesDev a, int64_t count, double n, double m, double* __restrict__ omega) {
+// Per wave vector: omega (FP64) or, for complex64 plans (split = true), nu = omega / (2 pi)
+// as an unevaluated FP32 pair (hi, lo), hi = RN(nu), lo = RN(nu - hi): |nu - hi - lo| <=
+// 2^-48 nu, enough for the phase nu t of any t < 2^24 to ~1e-8 cycles with FP32 arithmetic.
+__global__ void omega_kernel(int dim, AxesDev a, int64_t count, double n, double m, double* __restrict__ omega,
+                             bool split) {
   int64_t x, y, z;
   if (grid_pos(a, x, y, z)) {
     const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
@@ -194,9 +227,25 @@ __global__ void omega_kernel(int dim, AxesDev a, int64_t count, double n, double
       double u, nx, ny, nz;
       symbol_tab<double>(dim, a, f[0], f[1], f[2], q, u, nx, ny, nz);
       const double sw = sqrt(m * m + n * n * (nx * nx + ny * ny + nz * nz));
-      omega[idx * nq + q] = atan2(sw, n * u);
+      const double w = atan2(sw, n * u);
+      if (split) {
+        const double nu = w * 0.15915494309189533577;
+        const float hi = (float)nu;
+        reinterpret_cast<float2*>(omega)[idx * nq + q] = make_float2(hi, (float)(nu - (double)hi));
+      } else {
+        omega[idx * nq + q] = w;
+      }
     }
   }
+}
+
+// (cos, sin)(2 pi nu t) for nu = hi + lo (FP32 pair) and integer t < 2^24, in FP32:
+// p + e = hi t exactly (FMA), p - rint(p) is exact, lo t is below 2^-24 |p|.
+__device__ __forceinline__ void phase_split(float2 nu, float tf, float& c, float& s) {
+  const float p = nu.x * tf;
+  const float e = fmaf(nu.x, tf, -p);
+  const float r = (p - rintf(p)) + fmaf(nu.y, tf, e);
+  sincospif(2.0f * r, &s, &c);
 }
 
 // (cos, sin) of omega t with omega t reduced modulo 2 pi in FP64.
@@ -267,11 +316,11 @@ __device__ __forceinline__ void apply_dt(typename Cx2<T>::t (&v)[S], T c, T s, T
 
 // G^ entries for one wave vector in precision T.
 template <typename T>
-__device__ __forceinline__ void ghat(int dim, const AxesDev& a, const int64_t (&f)[3], int q, double n, double m,
+__device__ __forceinline__ void ghat(int dim, const AxesDev& a, const int64_t (&f)[3], int q, const Mass& ms,
                                      T& gx, T& gy, T& gz, T& gm) {
   T u, nx, ny, nz;
   symbol_tab<T>(dim, a, f[0], f[1], f[2], q, u, nx, ny, nz);
-  const T nf = (T)n, mf = (T)m;
+  const T nf = sizeof(T) == 8 ? (T)ms.n : (T)ms.nf, mf = sizeof(T) == 8 ? (T)ms.m : (T)ms.mf;
   const T sw = sqrt(mf * mf + nf * nf * (nx * nx + ny * ny + nz * nz));
   const T inv = sw > (T)0 ? (T)1 / sw : (T)0;
   gx = nf * nx * inv;
@@ -307,8 +356,9 @@ __device__ __forceinline__ double omega_fast(double C, double S2, const double2*
 }
 
 // omega_k in FP64 from the FP64 tables, computed in the kernel (served path: no table)
-__device__ __forceinline__ double omega_of(int dim, const AxesDev& a, const int64_t (&f)[3], int q, double n,
-                                          double m) {
+__device__ __forceinline__ double omega_of(int dim, const AxesDev& a, const int64_t (&f)[3], int q,
+                                          const Mass& ms) {
+  const double n = ms.n, m = ms.m;
   double u, nx, ny, nz;
   symbol_tab<double>(dim, a, f[0], f[1], f[2], q, u, nx, ny, nz);
   return omega_fast(n * u, m * m + n * n * (nx * nx + ny * ny + nz * nz), a.angle);
@@ -329,89 +379,314 @@ __device__ __forceinline__ void cs_of(double omega, double tt, T& c, T& s) {
   }
 }
 
+// ---------------------------------------------------------------- double-float
+// Unevaluated pairs hi + lo of FP32 numbers (|lo| <= ulp(hi)/2, ~46-bit significand),
+// built from error-free transformations (Knuth two-sum, FMA two-product); the _rn
+// intrinsics keep the compiler from contracting or reordering them.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_fast_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return df_fast_sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_sum(p, e);
+}
+__device__ __forceinline__ DF df_of(float2 v) { return DF{v.x, v.y}; }
+
+// (cos, sin) of a symbol-table angle in double-float (the tables of trig[]; the chain
+// combines its two levels by the angle-addition formula)
+__device__ __forceinline__ void tab_df(const AxesDev& a, int dim, int ax, int64_t i, DF& c, DF& s) {
+  if (dim == 1) {
+    const float4 f = a.trigdf[0][i & (kDfFine - 1)], g = a.trigdf[1][i / kDfFine];
+    const DF c0{f.x, f.y}, s0{f.z, f.w}, c1{g.x, g.y}, s1{g.z, g.w};
+    c = df_sub(df_mul(c1, c0), df_mul(s1, s0));
+    s = df_add(df_mul(s1, c0), df_mul(c1, s0));
+  } else {
+    const float4 f = a.trigdf[ax][i];
+    c = DF{f.x, f.y};
+    s = DF{f.z, f.w};
+  }
+}
+
+// nu_k = omega_k / (2 pi) in double-float without FP64 operations: the symbol
+// (u, n~) and C = n u, S^2 = m^2 + n^2 |n~|^2 in double-float, S by an FP32 square root
+// and one Newton correction, and omega = theta_j + asin(S cos theta_j - C sin theta_j)
+// around the nearest anchor theta_j = j pi / kAngleTab (as omega_fast), so that
+// nu = j / (2 kAngleTab) + asin(x) / (2 pi).  Error ~1e-13 in nu.
+__device__ __forceinline__ float2 nu_df(int dim, const AxesDev& a, const int64_t (&f)[3], int q, const Mass& ms) {
+  DF u, nx, ny, nz;
+  if (dim == 1) {
+    DF c, s;
+    tab_df(a, 1, 0, f[0], c, s);
+    u = c;
+    nx = DF{0.f, 0.f};
+    ny = nx;
+    nz = s;
+  } else if (dim == 2) {
+    const int64_t N2 = 2 * a.len[0];
+    int64_t dm = f[0] - f[1];
+    if (dm < 0) dm += N2;
+    DF cx, sx, cy, sy;
+    tab_df(a, 2, 0, f[0] + f[1], cx, sx);
+    tab_df(a, 2, 0, dm, cy, sy);
+    u = df_mul(cx, cy);
+    nx = df_mul(sx, cy);
+    ny = df_mul(cx, sy);
+    nz = df_mul(sx, sy);
+  } else {
+    DF cx, sx, cy, sy, cz, sz;
+    tab_df(a, 3, 0, f[0], cx, sx);
+    tab_df(a, 3, 1, f[1], cy, sy);
+    tab_df(a, 3, 2, f[2], cz, sz);
+    if (q) {
+      cx = df_neg(cx);
+      sx = df_neg(sx);
+    }
+    const DF cxcy = df_mul(cx, cy), sxsy = df_mul(sx, sy), cxsy = df_mul(cx, sy), sxcy = df_mul(sx, cy);
+    u = df_add(df_mul(cxcy, cz), df_mul(sxsy, sz));
+    nx = df_sub(df_mul(sxcy, cz), df_mul(cxsy, sz));
+    ny = df_add(df_mul(cxsy, cz), df_mul(sxcy, sz));
+    nz = df_sub(df_mul(cxcy, sz), df_mul(sxsy, cz));
+  }
+  const DF C = df_mul(df_of(ms.n_df), u);
+  const DF nn = df_add(df_add(df_mul(nx, nx), df_mul(ny, ny)), df_mul(nz, nz));
+  const DF S2 = df_add(df_of(ms.m2_df), df_mul(df_of(ms.n2_df), nn));
+  DF S{0.f, 0.f};
+  if (S2.hi > 0.f) {
+    const float s0 = sqrtf(S2.hi);
+    const float p = __fmul_rn(s0, s0), e = __fmaf_rn(s0, s0, -p);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(S2.hi, p), e), S2.lo);  // S2 - s0^2
+    S = df_fast_sum(s0, __fmul_rn(r, __fdiv_rn(0.5f, s0)));
+  }
+  const float w0 = atan2f(S.hi, C.hi);
+  int j = __float2int_rn(w0 * (float)(kAngleTab / 3.14159265358979323846));
+  j = j < 0 ? 0 : (j > kAngleTab ? kAngleTab : j);
+  const float4 an = a.angdf[j];
+  const DF x = df_sub(df_mul(S, DF{an.x, an.y}), df_mul(C, DF{an.z, an.w}));  // sin(omega - theta_j)
+  const float xf = x.hi, x2 = xf * xf;
+  const float cub = xf * x2 * fmaf(x2, 0.075f, 1.0f / 6.0f);  // asin(x) - x, < 7e-10
+  const DF d = df_add(x, DF{cub, 0.f});
+  const DF inv2pi{1.591549367e-01f, 6.420638243e-09f};          // 1 / (2 pi) in double-float
+  const DF nu = df_add(DF{(float)j * (0.5f / kAngleTab), 0.f}, df_mul(d, inv2pi));
+  return make_float2(nu.hi, nu.lo);
+}
+
+// cos, sin of omega_k t for wave vector q of storage index idx: from the plan's table
+// (FP64 omega; for complex64 the split nu table, t < 2^24) or computed here (no table).
+template <typename T, int S>
+__device__ __forceinline__ void cs_at(int dim, const AxesDev& a, const int64_t (&f)[3], int q, int64_t slot,
+                                      const Mass& ms, const double* __restrict__ omega, const TimeArg& ta, T& c,
+                                      T& s) {
+  if (omega == nullptr) {
+    if (sizeof(T) == 4 && ta.small) {
+      float cf, sf;
+      phase_split(nu_df(dim, a, f, q, ms), ta.tf, cf, sf);
+      c = (T)cf;
+      s = (T)sf;
+    } else {
+      cs_of<T, S>(omega_of(dim, a, f, q, ms), ta.tt, c, s);
+    }
+  } else if (sizeof(T) == 8) {
+    cs_of<T, S>(omega[slot], ta.tt, c, s);
+  } else {
+    const float2 nu = reinterpret_cast<const float2*>(omega)[slot];
+    if (ta.small) {
+      float cf, sf;
+      phase_split(nu, ta.tf, cf, sf);
+      c = (T)cf;
+      s = (T)sf;
+    } else {
+      cs_of<T, S>(6.283185307179586232 * ((double)nu.x + (double)nu.y), ta.tt, c, s);
+    }
+  }
+}
+
+// D_k^t, times the scale (1/|V|, optionally the initial norm), on the spectral values
+// of storage position (x, y, z) (storage index idx): v[0..s) in 1D/2D, and in BCC the
+// two cosets' four components v[0..4) (coset 0) and v[4..8) (coset 1).
 template <typename T>
-__global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t count, double n, double m,
-                                                     const double* __restrict__ omega, double tt, T scale_in,
+__device__ __forceinline__ void evolve_point(int dim, const AxesDev& a, int64_t x, int64_t y, int64_t z,
+                                             int64_t idx, const Mass& ms, const double* __restrict__ omega,
+                                             const TimeArg& ta, T scale, typename Cx2<T>::t (&v)[8]) {
+  using V = typename Cx2<T>::t;
+  int64_t f[3], fs;
+  wave_vectors(dim, x, y, z, a, f, fs);
+  if (dim == 1) {
+    V w[2] = {v[0], v[1]};
+    T c, s, gx, gy, gz, gm;
+    cs_at<T, 2>(1, a, f, 0, idx, ms, omega, ta, c, s);
+    ghat<T>(1, a, f, 0, ms, gx, gy, gz, gm);
+    apply_dt<T, 2>(w, c, s, (T)0, gx, gy, gz, gm);
+    v[0] = make_vec(w[0], scale);
+    v[1] = make_vec(w[1], scale);
+  } else if (dim == 2) {
+    V w[4] = {v[0], v[1], v[2], v[3]};
+    T c, s, gx, gy, gz, gm;
+    cs_at<T, 4>(2, a, f, 0, idx, ms, omega, ta, c, s);
+    ghat<T>(2, a, f, 0, ms, gx, gy, gz, gm);
+    apply_dt<T, 4>(w, c, s, (T)0, gx, gy, gz, gm);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = make_vec(w[q], scale);
+  } else {
+    T ar, ai;
+    coset_phase<T>(fs, a.len[0], ar, ai);  // a = exp(i (k1 + k2 + k3)/2)
+    V c0[4], c1[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      // a* Psi1
+      V b;
+      b.x = ar * v[4 + q].x + ai * v[4 + q].y;
+      b.y = ar * v[4 + q].y - ai * v[4 + q].x;
+      c0[q].x = (T)0.5 * (v[q].x + b.x);
+      c0[q].y = (T)0.5 * (v[q].y + b.y);
+      c1[q].x = (T)0.5 * (v[q].x - b.x);
+      c1[q].y = (T)0.5 * (v[q].y - b.y);
+    }
+    {
+      T c, s, gx, gy, gz, gm;
+      cs_at<T, 4>(3, a, f, 0, 2 * idx, ms, omega, ta, c, s);
+      ghat<T>(3, a, f, 0, ms, gx, gy, gz, gm);
+      apply_dt<T, 4>(c0, c, s, (T)0, gx, gy, gz, gm);
+    }
+    {
+      T c, s, gx, gy, gz, gm;
+      cs_at<T, 4>(3, a, f, 1, 2 * idx + 1, ms, omega, ta, c, s);
+      ghat<T>(3, a, f, 1, ms, gx, gy, gz, gm);
+      apply_dt<T, 4>(c1, c, s, (T)0, gx, gy, gz, gm);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      V s0, d, s1;
+      s0.x = c0[q].x + c1[q].x;
+      s0.y = c0[q].y + c1[q].y;
+      d.x = c0[q].x - c1[q].x;
+      d.y = c0[q].y - c1[q].y;
+      s1.x = ar * d.x - ai * d.y;
+      s1.y = ar * d.y + ai * d.x;
+      v[q] = make_vec(s0, scale);
+      v[4 + q] = make_vec(s1, scale);
+    }
+  }
+}
+
+__device__ __forceinline__ int planes_of(int dim) { return dim == 1 ? 2 : (dim == 2 ? 4 : 8); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t count, Mass ms,
+                                                     const double* __restrict__ omega, TimeArg ta, T scale_in,
                                                      const double* __restrict__ norm0,
                                                      typename Cx2<T>::t* __restrict__ data) {
   using V = typename Cx2<T>::t;
   // optional normalisation of the initial state, folded into the 1/|V| scale
-  const T scale = norm0 ? (T)((double)scale_in / sqrt(norm0[0])) : scale_in;
+  const T scale = norm0 ? (sizeof(T) == 8 ? (T)((double)scale_in / sqrt(norm0[0]))
+                                           : (T)(scale_in * rsqrtf((float)norm0[0])))
+                        : scale_in;
   int64_t x, y, z;
   if (grid_pos(a, x, y, z)) {
     const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
-    int64_t f[3], fs;
-    wave_vectors(dim, x, y, z, a, f, fs);
-    if (dim == 1) {
-      V v[2] = {data[idx], data[count + idx]};
-      T c, s, gx, gy, gz, gm;
-      cs_of<T, 2>(omega ? omega[idx] : omega_of(1, a, f, 0, n, m), tt, c, s);
-      ghat<T>(1, a, f, 0, n, m, gx, gy, gz, gm);
-      apply_dt<T, 2>(v, c, s, (T)0, gx, gy, gz, gm);
-      data[idx] = make_vec(v[0], scale);
-      data[count + idx] = make_vec(v[1], scale);
-    } else if (dim == 2) {
-      V v[4];
+    const int P = planes_of(dim);
+    V v[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = data[q * count + idx];
-      T c, s, gx, gy, gz, gm;
-      cs_of<T, 4>(omega ? omega[idx] : omega_of(2, a, f, 0, n, m), tt, c, s);
-      ghat<T>(2, a, f, 0, n, m, gx, gy, gz, gm);
-      apply_dt<T, 4>(v, c, s, (T)0, gx, gy, gz, gm);
+    for (int q = 0; q < 8; ++q)
+      if (q < P) v[q] = data[q * count + idx];
+    evolve_point<T>(dim, a, x, y, z, idx, ms, omega, ta, scale, v);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) data[q * count + idx] = make_vec(v[q], scale);
-    } else {
-      V p0[4], p1[4];
+    for (int q = 0; q < 8; ++q)
+      if (q < P) data[q * count + idx] = v[q];
+  }
+}
+
+// Fused x pass of the Fourier form (complex64): for RW rows of every component
+// plane, the forward DFT along x, D_k^t per wave vector (BCC coset mix included)
+// and the inverse DFT along x, with one read and one write of those rows.  The y
+// and z transforms run as ordinary passes before and after (transforms along
+// different axes commute).  Needs the x axis in one register pass of length
+// L = R1 * R2 (natural order along x); y, z may be digit-permuted (freq_of).
+template <int R1, int R2>
+__global__ void __launch_bounds__(256) fused_x_kernel(int dim, AxesDev a, int64_t count, Mass ms,
+                                                      const double* __restrict__ omega, TimeArg ta, float scale_in,
+                                                      const double* __restrict__ norm0, float2* __restrict__ data,
+                                                      const float2* __restrict__ tw_line) {
+  using V = float2;
+  constexpr int L = R1 * R2, TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
+  constexpr int CP = (C % 2 == 0) ? C + 1 : C;
+  extern __shared__ __align__(16) unsigned char fx_smem[];
+  V* sm = reinterpret_cast<V*>(fx_smem);
+  const float scale = norm0 ? scale_in * rsqrtf((float)norm0[0]) : scale_in;
+  const int P = planes_of(dim);
+  const int RW = C / P;                     // rows per CTA (C >= 8 >= P)
+  const int CU = RW * P;                    // lines in use: line p * RW + w = plane p, row row0 + w
+  const int64_t nrows = count / L;          // rows per plane
+  const int64_t row0 = (int64_t)blockIdx.x * RW;
+  const int tid = threadIdx.x, c = tid % C, r = tid / C;
+  const TwRow<V> tw{tw_line, r};
+  // ---- load: consecutive threads read consecutive x of one line
+  {
+    constexpr int NE = (C * L + 255) / 256;
+    V v[NE];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        p0[q] = data[q * count + idx];
-        p1[q] = data[(4 + q) * count + idx];
-      }
-      T ar, ai;
-      coset_phase<T>(fs, a.len[0], ar, ai);  // a = exp(i (k1 + k2 + k3)/2)
-      V c0[4], c1[4];
+    for (int j = 0; j < NE; ++j) {
+      const int e = tid + 256 * j, cc = e / L, xx = e - cc * L;
+      const int p = cc / (RW > 0 ? RW : 1), w = cc - p * RW;
+      v[j].x = 0.f;
+      v[j].y = 0.f;
+      if (cc < CU && row0 + w < nrows) v[j] = data[p * count + (row0 + w) * L + xx];
+    }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        // a* Psi1
-        V b;
-        b.x = ar * p1[q].x + ai * p1[q].y;
-        b.y = ar * p1[q].y - ai * p1[q].x;
-        c0[q].x = (T)0.5 * (p0[q].x + b.x);
-        c0[q].y = (T)0.5 * (p0[q].y + b.y);
-        c1[q].x = (T)0.5 * (p0[q].x - b.x);
-        c1[q].y = (T)0.5 * (p0[q].y - b.y);
-      }
-      {
-        T c, s, gx, gy, gz, gm;
-        cs_of<T, 4>(omega ? omega[2 * idx] : omega_of(3, a, f, 0, n, m), tt, c, s);
-        ghat<T>(3, a, f, 0, n, m, gx, gy, gz, gm);
-        apply_dt<T, 4>(c0, c, s, (T)0, gx, gy, gz, gm);
-      }
-      {
-        T c, s, gx, gy, gz, gm;
-        cs_of<T, 4>(omega ? omega[2 * idx + 1] : omega_of(3, a, f, 1, n, m), tt, c, s);
-        ghat<T>(3, a, f, 1, n, m, gx, gy, gz, gm);
-        apply_dt<T, 4>(c1, c, s, (T)0, gx, gy, gz, gm);
-      }
+    for (int j = 0; j < NE; ++j) {
+      const int e = tid + 256 * j, cc = e / L, xx = e - cc * L;
+      if (cc < C) sm[cc + CP * xx] = v[j];
+    }
+  }
+  __syncthreads();
+  reg_fft_steps<float, false, R1, R2, CP>(sm, c, r, tw);
+  // ---- D_k^t at every (row, k) of the CTA
+  for (int q = tid; q < RW * L; q += 256) {
+    const int w = q / L, k = q - w * L;
+    const int64_t row = row0 + w;
+    if (row >= nrows) continue;
+    const int ny = (int)a.len[1], rowi = (int)row;  // rows per plane < 2^31
+    const int64_t yy = rowi % ny, zz = rowi / ny;
+    V v[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        V s0, d, s1;
-        s0.x = c0[q].x + c1[q].x;
-        s0.y = c0[q].y + c1[q].y;
-        d.x = c0[q].x - c1[q].x;
-        d.y = c0[q].y - c1[q].y;
-        s1.x = ar * d.x - ai * d.y;
-        s1.y = ar * d.y + ai * d.x;
-        data[q * count + idx] = make_vec(s0, scale);
-        data[(4 + q) * count + idx] = make_vec(s1, scale);
-      }
+    for (int pp = 0; pp < 8; ++pp)
+      if (pp < P) v[pp] = sm[pp * RW + w + CP * k];
+    evolve_point<float>(dim, a, k, yy, zz, row * L + k, ms, omega, ta, scale, v);
+#pragma unroll
+    for (int pp = 0; pp < 8; ++pp)
+      if (pp < P) sm[pp * RW + w + CP * k] = v[pp];
+  }
+  __syncthreads();
+  reg_fft_steps<float, true, R1, R2, CP>(sm, c, r, tw);
+  // ---- store
+  {
+    constexpr int NE = (C * L + 255) / 256;
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+      const int e = tid + 256 * j, cc = e / L, xx = e - cc * L;
+      const int p = cc / (RW > 0 ? RW : 1), w = cc - p * RW;
+      if (cc < CU && row0 + w < nrows) data[p * count + (row0 + w) * L + xx] = sm[cc + CP * xx];
     }
   }
 }
 
 // Particle weight: sum |c|^2 and sum c^dag G^ c over every wave vector.
 template <typename T>
-__global__ void __launch_bounds__(256) weights_kernel(int dim, AxesDev a, int64_t count, double n, double m,
+__global__ void __launch_bounds__(256) weights_kernel(int dim, AxesDev a, int64_t count, Mass ms,
                                                       const typename Cx2<T>::t* __restrict__ data,
                                                       double* __restrict__ partials) {
   using V = typename Cx2<T>::t;
@@ -444,7 +719,7 @@ __global__ void __launch_bounds__(256) weights_kernel(int dim, AxesDev a, int64_
     }
     for (int j = 0; j < nq; ++j) {
       T gx, gy, gz, gm;
-      ghat<T>(dim, a, f, dim == 3 ? j : 0, n, m, gx, gy, gz, gm);
+      ghat<T>(dim, a, f, dim == 3 ? j : 0, ms, gx, gy, gz, gm);
       // cos = 1, sin = 1 turns apply_dt into v - i G^ v; recover G^ v from it
       T nrm = 0, gdot = 0;
       if (S == 2) {
@@ -497,8 +772,8 @@ static dim3 grid3(const Geometry& g) {
 }
 
 qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,
-                             cudaStream_t st) {
-  omega_kernel<<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), kcount(g), n, m, omega);
+                             cudaStream_t st, bool split) {
+  omega_kernel<<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), kcount(g), n, m, omega, split);
   QW_CHECK_LAUNCH("omega table launch");
   return QW_OK;
 }
@@ -509,13 +784,68 @@ qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtyp
   const int64_t count = kcount(g);
   const double inv = 1.0 / (double)g.vol;
   if (dt == QW_C64)
-    evolve_kernel<float><<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), count, n, m, omega, (double)t,
-                                                         (float)inv, norm0, static_cast<float2*>(psi_hat));
+    evolve_kernel<float><<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), count, make_mass(n, m), omega,
+                                                         make_time(t), (float)inv, norm0,
+                                                         static_cast<float2*>(psi_hat));
   else
-    evolve_kernel<double><<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), count, n, m, omega, (double)t, inv,
-                                                          norm0, static_cast<double2*>(psi_hat));
+    evolve_kernel<double><<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), count, make_mass(n, m), omega,
+                                                          make_time(t), inv, norm0, static_cast<double2*>(psi_hat));
   QW_CHECK_LAUNCH("evolve launch");
   return QW_OK;
+}
+
+template <int R1, int R2>
+static qw_status launch_fused(const Geometry& g, const SpecAxes& ax, double n, double m, const double* omega,
+                              int64_t t, void* psi, const void* tw_line, cudaStream_t st, const double* norm0) {
+  constexpr int L = R1 * R2, TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
+  constexpr int CP = (C % 2 == 0) ? C + 1 : C;
+  const int P = g.dim == 1 ? 2 : (g.dim == 2 ? 4 : 8);
+  const int RW = C / P;
+  const int64_t nrows = g.vol / L;
+  const int64_t grid = (nrows + RW - 1) / RW;
+  const size_t smem = (size_t)L * CP * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    QW_CHECK_CUDA(cudaFuncSetAttribute(fused_x_kernel<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    attr = true;
+  }
+  fused_x_kernel<R1, R2><<<(unsigned)grid, 256, smem, st>>>(g.dim, to_dev(ax), g.vol, make_mass(n, m), omega,
+                                                           make_time(t),
+                                                           (float)(1.0 / (double)g.vol), norm0,
+                                                           static_cast<float2*>(psi),
+                                                           static_cast<const float2*>(tw_line));
+  QW_CHECK_LAUNCH("fused x pass launch");
+  return QW_OK;
+}
+
+bool fused_x_supported(const Geometry& g, const FftPlan& f, qw_dtype dt) {
+  if (dt != QW_C64 || f.axis[0].count != 1 || g.dim < 2) return false;
+  switch (g.nx) {
+#define QW_FX(LEN, A, B) case LEN:
+    QW_REG_LENGTHS_POW2(QW_FX)
+    QW_REG_LENGTHS_F32(QW_FX)
+#undef QW_FX
+      return true;
+    default:
+      return false;
+  }
+}
+
+qw_status launch_evolve_fused_x(const Geometry& g, const SpecAxes& ax, const FftPlan& f, double n, double m,
+                                const double* omega, int64_t t, void* psi, cudaStream_t st, const double* norm0) {
+  const void* tw = f.pass[f.axis[0].first].tw_line;
+  switch (g.nx) {
+#define QW_FX(LEN, A, B) \
+  case LEN:              \
+    return launch_fused<A, B>(g, ax, n, m, omega, t, psi, tw, st, norm0);
+    QW_REG_LENGTHS_POW2(QW_FX)
+    QW_REG_LENGTHS_F32(QW_FX)
+#undef QW_FX
+    default:
+      set_error("fused x pass: no register kernel for length %lld", (long long)g.nx);
+      return QW_EINVAL;
+  }
 }
 
 qw_status launch_particle_weights(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
@@ -523,10 +853,10 @@ qw_status launch_particle_weights(const Geometry& g, const SpecAxes& ax, qw_dtyp
   const int64_t count = kcount(g);
   const int nblk = kObsBlocks;
   if (dt == QW_C64)
-    weights_kernel<float><<<nblk, 256, 0, st>>>(g.dim, to_dev(ax), count, n, m,
+    weights_kernel<float><<<nblk, 256, 0, st>>>(g.dim, to_dev(ax), count, make_mass(n, m),
                                                 static_cast<const float2*>(psi_hat), partials);
   else
-    weights_kernel<double><<<nblk, 256, 0, st>>>(g.dim, to_dev(ax), count, n, m,
+    weights_kernel<double><<<nblk, 256, 0, st>>>(g.dim, to_dev(ax), count, make_mass(n, m),
                                                  static_cast<const double2*>(psi_hat), partials);
   QW_CHECK_LAUNCH("weights launch");
   fold2_kernel<<<1, 256, 0, st>>>(partials, nblk, result);
