@@ -204,23 +204,30 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restric
   // ---- load into shared memory, element n of line c at sm[c + CP n]; every load of
   // the thread is issued before the first shared-memory store (full unroll)
   if (CONTIG) {  // S == 1: the CTA's lines are one contiguous run
+    // element e = tid + 256 j of the run sits at line e / L, position e % L; both come
+    // from tid / L and tid % L plus compile-time offsets (no division per element)
     constexpr int NE = (C * L + 255) / 256;
+    const int t_c = tid / L, t_x = tid - (tid / L) * L;
     V v[NE];
 #pragma unroll
     for (int j = 0; j < NE; ++j) {
-      const int e = tid + 256 * j;
-      const int64_t ll = l0 + e / L;
+      int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
+      if (xx >= L) {
+        xx -= L;
+        ++cc;
+      }
       v[j].x = 0;
       v[j].y = 0;
-      if (e < C * L && ll < nlines) v[j] = data[l0 * L + e];
+      if (cc < C && l0 + cc < nlines) v[j] = data[l0 * L + tid + 256 * j];
     }
 #pragma unroll
     for (int j = 0; j < NE; ++j) {
-      const int e = tid + 256 * j;
-      if (e < C * L) {
-        const int cc = e / L, n = e - cc * L;
-        sm[cc + CP * n] = v[j];
+      int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
+      if (xx >= L) {
+        xx -= L;
+        ++cc;
       }
+      if (cc < C) sm[cc + CP * xx] = v[j];
     }
   } else if (r < TPL) {
     constexpr int NL = (L + TPL - 1) / TPL;
@@ -245,11 +252,16 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restric
   reg_fft_steps<T, INV, R1, R2, CP>(sm, c, r, tw);
   // ---- store
   if (CONTIG) {
-#pragma unroll 4
-    for (int e = tid; e < C * L; e += 256) {
-      const int cc = e / L, n = e - cc * L;
-      const int64_t ll = l0 + cc;
-      if (ll < nlines) data[ll * L + n] = sm[cc + CP * n];
+    constexpr int NE = (C * L + 255) / 256;
+    const int t_c = tid / L, t_x = tid - (tid / L) * L;
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+      int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
+      if (xx >= L) {
+        xx -= L;
+        ++cc;
+      }
+      if (cc < C && l0 + cc < nlines) data[l0 * L + tid + 256 * j] = sm[cc + CP * xx];
     }
   } else if (r < TPL) {
 #pragma unroll 4

@@ -629,26 +629,38 @@ __global__ void __launch_bounds__(256) fused_x_kernel(int dim, AxesDev a, int64_
   const float scale = norm0 ? scale_in * rsqrtf((float)norm0[0]) : scale_in;
   const int P = planes_of(dim);
   const int RW = C / P;                     // rows per CTA (C >= 8 >= P)
-  const int CU = RW * P;                    // lines in use: line p * RW + w = plane p, row row0 + w
+  const int CU = RW * P;                    // lines in use
   const int64_t nrows = count / L;          // rows per plane
   const int64_t row0 = (int64_t)blockIdx.x * RW;
   const int tid = threadIdx.x, c = tid % C, r = tid / C;
   const TwRow<V> tw{tw_line, r};
-  // ---- load: consecutive threads read consecutive x of one line
+  // ---- load: consecutive threads read consecutive x of one line; line cc = w P + p
+  // holds plane p of row row0 + w (P is a power of two).  Element e = tid + 256 j sits
+  // at line e / L, position e % L, from tid / L and tid % L plus compile-time offsets.
+  constexpr int NE = (C * L + 255) / 256;
+  const int t_c = tid / L, t_x = tid - (tid / L) * L;
+  const int lgP = dim == 1 ? 1 : (dim == 2 ? 2 : 3);
   {
-    constexpr int NE = (C * L + 255) / 256;
     V v[NE];
 #pragma unroll
     for (int j = 0; j < NE; ++j) {
-      const int e = tid + 256 * j, cc = e / L, xx = e - cc * L;
-      const int p = cc / (RW > 0 ? RW : 1), w = cc - p * RW;
+      int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
+      if (xx >= L) {
+        xx -= L;
+        ++cc;
+      }
+      const int p = cc & (P - 1), w = cc >> lgP;
       v[j].x = 0.f;
       v[j].y = 0.f;
       if (cc < CU && row0 + w < nrows) v[j] = data[p * count + (row0 + w) * L + xx];
     }
 #pragma unroll
     for (int j = 0; j < NE; ++j) {
-      const int e = tid + 256 * j, cc = e / L, xx = e - cc * L;
+      int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
+      if (xx >= L) {
+        xx -= L;
+        ++cc;
+      }
       if (cc < C) sm[cc + CP * xx] = v[j];
     }
   }
@@ -664,23 +676,24 @@ __global__ void __launch_bounds__(256) fused_x_kernel(int dim, AxesDev a, int64_
     V v[8];
 #pragma unroll
     for (int pp = 0; pp < 8; ++pp)
-      if (pp < P) v[pp] = sm[pp * RW + w + CP * k];
+      if (pp < P) v[pp] = sm[w * P + pp + CP * k];
     evolve_point<float>(dim, a, k, yy, zz, row * L + k, ms, omega, ta, scale, v);
 #pragma unroll
     for (int pp = 0; pp < 8; ++pp)
-      if (pp < P) sm[pp * RW + w + CP * k] = v[pp];
+      if (pp < P) sm[w * P + pp + CP * k] = v[pp];
   }
   __syncthreads();
   reg_fft_steps<float, true, R1, R2, CP>(sm, c, r, tw);
   // ---- store
-  {
-    constexpr int NE = (C * L + 255) / 256;
 #pragma unroll
-    for (int j = 0; j < NE; ++j) {
-      const int e = tid + 256 * j, cc = e / L, xx = e - cc * L;
-      const int p = cc / (RW > 0 ? RW : 1), w = cc - p * RW;
-      if (cc < CU && row0 + w < nrows) data[p * count + (row0 + w) * L + xx] = sm[cc + CP * xx];
+  for (int j = 0; j < NE; ++j) {
+    int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
+    if (xx >= L) {
+      xx -= L;
+      ++cc;
     }
+    const int p = cc & (P - 1), w = cc >> lgP;
+    if (cc < CU && row0 + w < nrows) data[p * count + (row0 + w) * L + xx] = sm[cc + CP * xx];
   }
 }
 
