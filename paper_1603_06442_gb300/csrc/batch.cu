@@ -11,7 +11,8 @@
 //     every walk still running (walks sorted by length, so that set is a prefix).
 // Before working on round s of tile i of walk w a CTA waits (bounded) until the
 // tiles within the stencil's reach of tile i (cyclically, the box is periodic)
-// have finished round s-1: per-tile round counters, release/acquire.  That
+// have finished round s-1: per-tile round counters, release/acquire (the lanes
+// of warp 0 acquire the counters, then a CTA barrier orders the tile's loads).  That
 // covers both the data tile i reads (written in round s-1) and the buffer it
 // overwrites (read by its neighbours in round s-1), and lets consecutive rounds
 // of a walk overlap as a wavefront instead of meeting at a barrier.  Every item
@@ -76,7 +77,7 @@ __device__ __forceinline__ int64_t upper_index(const int64_t* a, int64_t n, int6
   return lo;
 }
 
-__global__ void __launch_bounds__(256) batch_kernel(const BatchWalk* __restrict__ walks,
+__global__ void __launch_bounds__(256, 6) batch_kernel(const BatchWalk* __restrict__ walks,
                                                     const BatchGroup* __restrict__ groups, int ngroups,
                                                     const int64_t* __restrict__ tile_prefix,
                                                     const int64_t* __restrict__ round_prefix, int64_t total_items,
@@ -105,12 +106,14 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchWalk* __restrict_
     const int tile = (int)(off - tp[wl]);
     const int wi = G.first + wl;
     const BatchWalk W = walks[wi];
-    // ---- wait for round s-1 of the tiles within reach
-    if (tid == 0 && s > 0) {
+    // ---- wait for round s-1 of the tiles within reach: the lanes of warp 0 poll the
+    // tiles' counters in parallel (one L2 round trip instead of one per tile)
+    if (tid < 32 && s > 0) {
       const int span = 2 * W.reach + 1 >= W.ntiles ? W.ntiles : 2 * W.reach + 1;
       const int first = 2 * W.reach + 1 >= W.ntiles ? 0 : tile - W.reach;
       long long spins = 0;
-      for (int d = 0; d < span && !s_abort; ++d) {
+      bool gave_up = false;
+      for (int d = tid; d < span && !gave_up; d += 32) {
         int j = first + d;
         j = j < 0 ? j + W.ntiles : (j >= W.ntiles ? j - W.ntiles : j);
         cuda::atomic_ref<unsigned int, cuda::thread_scope_device> c(done[W.tile_base + j]);
@@ -119,12 +122,13 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchWalk* __restrict_
               cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).load(cuda::memory_order_relaxed)) {
             cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).store(1, cuda::memory_order_relaxed);
             atomicExch(&ctl->err, 1);
-            s_abort = 1;
+            gave_up = true;
             break;
           }
           __nanosleep(64);
         }
       }
+      if (gave_up) s_abort = 1;
     }
     __syncthreads();
     if (s_abort) break;
@@ -134,21 +138,32 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchWalk* __restrict_
     const int nx32 = (int)W.nx, ny32 = (int)W.ny;   // tiles and rows fit 32-bit indices
     const int nsite = (int)((r1 - r0) * W.nx);
     if (s < W.t) {
-      const float2* in = W.buf[s & 1];
-      float2* out = W.buf[(s + 1) & 1];
-      for (int k = tid; k < nsite; k += blockDim.x) {
-        const int kr = k / nx32;
-        const int64_t row = r0 + kr, x = k - kr * nx32;
+      // (buffers picked by selects: a dynamically indexed member array would put W in local memory)
+      const float2* in = (s & 1) ? W.buf[1] : W.buf[0];
+      float2* out = (s & 1) ? W.buf[0] : W.buf[1];
+      // site k = tid + 256 i of the tile: (row, x) advanced by (256 / nx, 256 % nx) per
+      // iteration, so no division per site; 32-bit indices (walks hold < 2^31 values)
+      const int r0i = (int)r0;
+      int kr = tid / nx32, x = tid - kr * nx32;
+      const int dr = 256 / nx32, dx = 256 - dr * nx32;
+      for (int k = tid; k < nsite; k += 256) {
+        const int row = r0i + kr;
         if (W.dim == 1) {
-          site_update_1d<float, false>(in, out, W.nx, x, W.cf);
+          site_update_1d<float, false, int>(in, out, nx32, x, W.cf);
         } else if (W.dim == 2) {
-          site_update_2d<float, false>(in, out, W.nx, x, row, W.cf);
+          site_update_2d<float, false, int>(in, out, nx32, x, row, W.cf);
         } else {
           // rows interleave the cosets: row = 2 (z M + y) + c
-          const int c = (int)(row & 1);
-          const int zy = (int)(row >> 1);
+          const int c = row & 1;
+          const int zy = row >> 1;
           const int z = zy / ny32;
-          site_update_3d<float, false>(in, out, W.nx, c, z, zy - z * ny32, x, W.cf);
+          site_update_3d<float, false, int>(in, out, nx32, c, z, zy - z * ny32, x, W.cf);
+        }
+        x += dx;
+        kr += dr;
+        if (x >= nx32) {
+          x -= nx32;
+          ++kr;
         }
       }
     } else {

@@ -53,60 +53,62 @@ template <typename R> struct CoefOf;
 template <> struct CoefOf<float> { using T = Coef32; };
 template <> struct CoefOf<double> { using T = Coef64; };
 
-__device__ __forceinline__ int64_t wrapm(int64_t v, int64_t M) { return v < 0 ? v + M : (v >= M ? v - M : v); }
+template <typename I>
+__device__ __forceinline__ I wrapm(I v, I M) { return v < 0 ? v + M : (v >= M ? v - M : v); }
 
 
 // ------------------------------------------------------------ per-site updates
 // chain, s = 2: psi'_0(x) = n psi_0(x-1) + i m psi_1(x), psi'_1(x) = i m psi_0(x) + n psi_1(x+1)
-template <typename R, bool NC = true>
+// (I: index type; the batched kernel's walks fit 32-bit indices)
+template <typename R, bool NC = true, typename I = int64_t>
 __device__ __forceinline__ void site_update_1d(const typename CplxOf<R>::T* __restrict__ in,
-                                               typename CplxOf<R>::T* __restrict__ out, int64_t N, int64_t x,
+                                               typename CplxOf<R>::T* __restrict__ out, I N, I x,
                                                const typename CoefOf<R>::T& cf) {
   using C = typename CplxOf<R>::T;
   const C* p0 = in;
   const C* p1 = in + N;
-  C a = ldg<NC>(p0 + wrapm(x - 1, N));   // psi_0(x - 1)
-  C b = ldg<NC>(p1 + wrapm(x + 1, N));   // psi_1(x + 1)
+  C a = ldg<NC>(p0 + wrapm<I>(x - 1, N));   // psi_0(x - 1)
+  C b = ldg<NC>(p1 + wrapm<I>(x + 1, N));   // psi_1(x + 1)
   C o0 = ldg<NC>(p0 + x), o1 = ldg<NC>(p1 + x);
   out[x] = finish(cf, a, o1);
   out[N + x] = finish(cf, b, o0);
 }
 
 // square lattice, s = 4 (tables above), site (x, y) of the N x N box
-template <typename R, bool NC = true>
+template <typename R, bool NC = true, typename I = int64_t>
 __device__ __forceinline__ void site_update_2d(const typename CplxOf<R>::T* __restrict__ in,
-                                               typename CplxOf<R>::T* __restrict__ out, int64_t N, int64_t x,
-                                               int64_t y, const typename CoefOf<R>::T& cf) {
+                                               typename CplxOf<R>::T* __restrict__ out, I N, I x, I y,
+                                               const typename CoefOf<R>::T& cf) {
   using C = typename CplxOf<R>::T;
-  const int64_t vol = N * N;
-  const int64_t xm = wrapm(x - 1, N), xp = wrapm(x + 1, N);
-  const int64_t ym = wrapm(y - 1, N), yp = wrapm(y + 1, N);
+  const I vol = N * N;
+  const I xm = wrapm<I>(x - 1, N), xp = wrapm<I>(x + 1, N);
+  const I ym = wrapm<I>(y - 1, N), yp = wrapm<I>(y + 1, N);
   C S0 = {0, 0}, S1 = {0, 0}, S2 = {0, 0}, S3 = {0, 0};
   {  // h = +e1: source (x - 1, y)
-    const int64_t i = y * N + xm;
+    const I i = y * N + xm;
     C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
     cmac<1, 1>(S0, a); cmac<1, -1>(S0, b); cmac<1, 1>(S1, a); cmac<1, -1>(S1, b);
     cmac<1, -1>(S2, c); cmac<-1, 1>(S2, d); cmac<-1, -1>(S3, c); cmac<1, 1>(S3, d);
   }
   {  // h = -e1: source (x + 1, y)
-    const int64_t i = y * N + xp;
+    const I i = y * N + xp;
     C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
     cmac<1, 1>(S0, a); cmac<-1, 1>(S0, b); cmac<-1, -1>(S1, a); cmac<1, -1>(S1, b);
     cmac<1, -1>(S2, c); cmac<1, -1>(S2, d); cmac<1, 1>(S3, c); cmac<1, 1>(S3, d);
   }
   {  // h = +e2: source (x, y - 1)
-    const int64_t i = ym * N + x;
+    const I i = ym * N + x;
     C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
     cmac<1, -1>(S0, a); cmac<1, 1>(S0, b); cmac<1, -1>(S1, a); cmac<1, 1>(S1, b);
     cmac<1, 1>(S2, c); cmac<-1, -1>(S2, d); cmac<-1, 1>(S3, c); cmac<1, -1>(S3, d);
   }
   {  // h = -e2: source (x, y + 1)
-    const int64_t i = yp * N + x;
+    const I i = yp * N + x;
     C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
     cmac<1, -1>(S0, a); cmac<-1, -1>(S0, b); cmac<-1, 1>(S1, a); cmac<1, 1>(S1, b);
     cmac<1, 1>(S2, c); cmac<1, 1>(S2, d); cmac<1, -1>(S3, c); cmac<1, -1>(S3, d);
   }
-  const int64_t i = y * N + x;
+  const I i = y * N + x;
   C o0 = ldg<NC>(in + i), o1 = ldg<NC>(in + vol + i), o2 = ldg<NC>(in + 2 * vol + i), o3 = ldg<NC>(in + 3 * vol + i);
   out[i] = finish(cf, S0, o2);
   out[vol + i] = finish(cf, S1, o3);
@@ -116,8 +118,8 @@ __device__ __forceinline__ void site_update_2d(const typename CplxOf<R>::T* __re
 
 // BCC, s = 4: output coset c at cell (x, y, z) reads coset 1-c at (per axis)
 // m - 1 + c for h = +1 and m + c for h = -1 (the site x - h of the other sublattice).
-template <int HX, int HY, int HZ, bool NC = true, typename C>
-__device__ __forceinline__ void bcc_term(C& S0, C& S1, C& S2, C& S3, const C* __restrict__ src, int64_t vol) {
+template <int HX, int HY, int HZ, bool NC = true, typename C, typename I>
+__device__ __forceinline__ void bcc_term(C& S0, C& S1, C& S2, C& S3, const C* __restrict__ src, I vol) {
   constexpr int P = HX * HY * HZ;
   if constexpr (HZ == 1) {
     C a = ldg<NC>(src), b = ldg<NC>(src + vol), d = ldg<NC>(src + 3 * vol);
@@ -134,16 +136,16 @@ __device__ __forceinline__ void bcc_term(C& S0, C& S1, C& S2, C& S3, const C* __
   }
 }
 
-template <typename R, bool NC = true>
+template <typename R, bool NC = true, typename I = int64_t>
 __device__ __forceinline__ void site_update_3d(const typename CplxOf<R>::T* __restrict__ in,
-                                               typename CplxOf<R>::T* __restrict__ out, int64_t M, int c,
-                                               int64_t z, int64_t y, int64_t x, const typename CoefOf<R>::T& cf) {
+                                               typename CplxOf<R>::T* __restrict__ out, I M, int c, I z, I y, I x,
+                                               const typename CoefOf<R>::T& cf) {
   using C = typename CplxOf<R>::T;
-  const int64_t plane = M * M, vol = plane * M;
-  const int64_t xa = wrapm(x - 1 + c, M), xb = wrapm(x + c, M);
-  const int64_t ya = wrapm(y - 1 + c, M), yb = wrapm(y + c, M);
-  const int64_t za = wrapm(z - 1 + c, M), zb = wrapm(z + c, M);
-  const C* src = in + (int64_t)(1 - c) * 4 * vol;
+  const I plane = M * M, vol = plane * M;
+  const I xa = wrapm<I>(x - 1 + c, M), xb = wrapm<I>(x + c, M);
+  const I ya = wrapm<I>(y - 1 + c, M), yb = wrapm<I>(y + c, M);
+  const I za = wrapm<I>(z - 1 + c, M), zb = wrapm<I>(z + c, M);
+  const C* src = in + (I)(1 - c) * 4 * vol;
   C S0 = {0, 0}, S1 = {0, 0}, S2 = {0, 0}, S3 = {0, 0};
   bcc_term<+1, +1, +1, NC>(S0, S1, S2, S3, src + za * plane + ya * M + xa, vol);
   bcc_term<+1, -1, +1, NC>(S0, S1, S2, S3, src + za * plane + yb * M + xa, vol);
@@ -153,10 +155,10 @@ __device__ __forceinline__ void site_update_3d(const typename CplxOf<R>::T* __re
   bcc_term<+1, -1, -1, NC>(S0, S1, S2, S3, src + zb * plane + yb * M + xa, vol);
   bcc_term<-1, +1, -1, NC>(S0, S1, S2, S3, src + zb * plane + ya * M + xb, vol);
   bcc_term<-1, -1, -1, NC>(S0, S1, S2, S3, src + zb * plane + yb * M + xb, vol);
-  const int64_t i = z * plane + y * M + x;
-  const C* own = in + (int64_t)c * 4 * vol + i;
+  const I i = z * plane + y * M + x;
+  const C* own = in + (I)c * 4 * vol + i;
   C o0 = ldg<NC>(own), o1 = ldg<NC>(own + vol), o2 = ldg<NC>(own + 2 * vol), o3 = ldg<NC>(own + 3 * vol);
-  C* dst = out + (int64_t)c * 4 * vol + i;
+  C* dst = out + (I)c * 4 * vol + i;
   dst[0] = finish(cf, S0, o2);
   dst[vol] = finish(cf, S1, o3);
   dst[2 * vol] = finish(cf, S2, o0);
