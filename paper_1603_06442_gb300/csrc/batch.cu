@@ -67,71 +67,95 @@ struct BatchCtl {
 
 constexpr long long kBatchSpin = 1ll << 24;
 
-__device__ __forceinline__ int64_t upper_index(const int64_t* a, int64_t n, int64_t v) {
-  // largest i in [0, n) with a[i] <= v (a ascending, a[0] = 0 <= v)
-  int64_t lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (a[mid] <= v) lo = mid; else hi = mid - 1;
+// Largest i in [0, n) with a[i] <= v (a ascending, a[0] <= v), searched by the 32 lanes
+// of a warp together: each round cuts the range into 32 slices and keeps the last
+// slice whose first element is <= v, so it takes log32(n) dependent loads instead of
+// log2(n).  Every lane returns the same i.
+__device__ __forceinline__ int64_t warp_upper_index(const int64_t* __restrict__ a, int64_t n, int64_t v, int lane) {
+  int64_t lo = 0, len = n;  // a[lo] <= v; the answer lies in [lo, lo + len)
+  while (len > 1) {
+    const int64_t step = (len + 31) / 32, end = lo + len;
+    const int64_t idx = lo + (int64_t)lane * step;
+    const bool ok = idx < end && a[idx] <= v;
+    const int c = __popc(__ballot_sync(0xffffffffu, ok));  // lanes 0 .. c-1 (a ascending)
+    lo += (int64_t)(c - 1) * step;
+    len = step < end - lo ? step : end - lo;
   }
   return lo;
 }
 
 __global__ void __launch_bounds__(256, 6) batch_kernel(const BatchWalk* __restrict__ walks,
-                                                    const BatchGroup* __restrict__ groups, int ngroups,
+                                                    const BatchGroup* __restrict__ groups,
+                                                    const int64_t* __restrict__ group_item0, int ngroups,
                                                     const int64_t* __restrict__ tile_prefix,
                                                     const int64_t* __restrict__ round_prefix, int64_t total_items,
                                                     unsigned int* __restrict__ done, BatchCtl* __restrict__ ctl) {
-  __shared__ int64_t s_item;
-  __shared__ int s_abort;
+  __shared__ int64_t s_next, s_round;
+  __shared__ int s_abort, s_walk, s_tile;
   const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_next = (int64_t)atomicAdd(&ctl->next, 1ull);
+    s_abort = 0;
+  }
   for (;;) {
-    if (tid == 0) {
-      s_item = (int64_t)atomicAdd(&ctl->next, 1ull);
-      s_abort = cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).load(cuda::memory_order_relaxed);
-    }
+    if (tid == 0 && cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).load(cuda::memory_order_relaxed))
+      s_abort = 1;
     __syncthreads();
-    const int64_t item = s_item;
+    const int64_t item = s_next;
     if (item >= total_items || s_abort) break;
-    // ---- decode (group, round, walk, tile)
-    int g = 0;
-    while (g + 1 < ngroups && groups[g + 1].item0 <= item) ++g;
-    const BatchGroup G = groups[g];
-    const int64_t jj = item - G.item0;
-    const int64_t* rp = round_prefix + G.round_off;
-    const int64_t s = upper_index(rp, G.nrounds + 1, jj);
-    const int64_t off = jj - rp[s];
-    const int64_t* tp = tile_prefix + G.tile_off;
-    const int wl = (int)upper_index(tp, G.nw + 1, off);
-    const int tile = (int)(off - tp[wl]);
-    const int wi = G.first + wl;
-    const BatchWalk W = walks[wi];
-    // ---- wait for round s-1 of the tiles within reach: the lanes of warp 0 poll the
-    // tiles' counters in parallel (one L2 round trip instead of one per tile)
-    if (tid < 32 && s > 0) {
-      const int span = 2 * W.reach + 1 >= W.ntiles ? W.ntiles : 2 * W.reach + 1;
-      const int first = 2 * W.reach + 1 >= W.ntiles ? 0 : tile - W.reach;
-      long long spins = 0;
-      bool gave_up = false;
-      for (int d = tid; d < span && !gave_up; d += 32) {
-        int j = first + d;
-        j = j < 0 ? j + W.ntiles : (j >= W.ntiles ? j - W.ntiles : j);
-        cuda::atomic_ref<unsigned int, cuda::thread_scope_device> c(done[W.tile_base + j]);
-        while (c.load(cuda::memory_order_acquire) < (unsigned int)s) {
-          if (++spins > kBatchSpin ||
-              cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).load(cuda::memory_order_relaxed)) {
-            cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).store(1, cuda::memory_order_relaxed);
-            atomicExch(&ctl->err, 1);
-            gave_up = true;
-            break;
-          }
-          __nanosleep(64);
-        }
+    // ---- warp 0: decode (group, round, walk, tile) with warp-cooperative searches, then
+    // wait for round s-1 of the tiles within reach, the lanes polling the tiles'
+    // counters in parallel; the other warps wait at the barrier
+    if (tid < 32) {
+      const int g = (int)warp_upper_index(group_item0, ngroups, item, tid);
+      const BatchGroup G = groups[g];
+      const int64_t jj = item - G.item0;
+      const int64_t* rp = round_prefix + G.round_off;
+      const int64_t s = warp_upper_index(rp, G.nrounds + 1, jj, tid);
+      const int64_t off = jj - rp[s];
+      const int64_t* tp = tile_prefix + G.tile_off;
+      const int wl = (int)warp_upper_index(tp, G.nw + 1, off, tid);
+      const int tile = (int)(off - tp[wl]);
+      const int wi = G.first + wl;
+      if (tid == 0) {
+        s_round = s;
+        s_walk = wi;
+        s_tile = tile;
       }
-      if (gave_up) s_abort = 1;
+      if (s > 0) {
+        const int ntiles = walks[wi].ntiles, reach = walks[wi].reach;
+        const int64_t tbase = walks[wi].tile_base;
+        const int span = 2 * reach + 1 >= ntiles ? ntiles : 2 * reach + 1;
+        const int first = 2 * reach + 1 >= ntiles ? 0 : tile - reach;
+        long long spins = 0;
+        bool gave_up = false;
+        for (int d = tid; d < span && !gave_up; d += 32) {
+          int j = first + d;
+          j = j < 0 ? j + ntiles : (j >= ntiles ? j - ntiles : j);
+          cuda::atomic_ref<unsigned int, cuda::thread_scope_device> c(done[tbase + j]);
+          while (c.load(cuda::memory_order_acquire) < (unsigned int)s) {
+            if (++spins > kBatchSpin ||
+                cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).load(cuda::memory_order_relaxed)) {
+              cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).store(1, cuda::memory_order_relaxed);
+              atomicExch(&ctl->err, 1);
+              gave_up = true;
+              break;
+            }
+            __nanosleep(64);
+          }
+        }
+        if (gave_up) s_abort = 1;
+      }
     }
     __syncthreads();
     if (s_abort) break;
+    const int64_t s = s_round;
+    const int tile = s_tile;
+    const BatchWalk W = walks[s_walk];
+    // claim the next item now (every thread read s_next before the barrier above): the
+    // atomic's round trip overlaps this item's work, and the claimed item is started by
+    // this CTA right after this one, so every claimed item still gets done
+    if (tid == 0) s_next = (int64_t)atomicAdd(&ctl->next, 1ull);
     // ---- the tile's rows
     const int64_t r0 = (int64_t)tile * W.rows_per_tile;
     const int64_t r1 = min(W.rows, r0 + W.rows_per_tile);
@@ -185,9 +209,10 @@ __global__ void __launch_bounds__(256, 6) batch_kernel(const BatchWalk* __restri
       }
     }
     __syncthreads();
-    if (tid == 0)
+    if (tid == 0) {
       cuda::atomic_ref<unsigned int, cuda::thread_scope_device>(done[W.tile_base + tile])
           .store((unsigned int)(s + 1), cuda::memory_order_release);
+    }
   }
 }
 
@@ -203,6 +228,7 @@ struct qw_batch_s {
   std::vector<void*> partners;    // per original walk
   BatchWalk* d_walks = nullptr;
   BatchGroup* d_groups = nullptr;
+  int64_t* d_group_item0 = nullptr;  // first item of each group (warp search key)
   int64_t* d_tiles = nullptr;
   int64_t* d_rounds = nullptr;
   unsigned int* d_done = nullptr;
@@ -230,11 +256,13 @@ static void free_schedule(qw_batch_s* b) {
   b->graph = nullptr;
   if (b->d_walks) cudaFree(b->d_walks);
   if (b->d_groups) cudaFree(b->d_groups);
+  if (b->d_group_item0) cudaFree(b->d_group_item0);
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_rounds) cudaFree(b->d_rounds);
   if (b->d_done) cudaFree(b->d_done);
   b->d_walks = nullptr;
   b->d_groups = nullptr;
+  b->d_group_item0 = nullptr;
   b->d_tiles = nullptr;
   b->d_rounds = nullptr;
   b->d_done = nullptr;
@@ -346,6 +374,10 @@ static qw_status build_schedule(qw_batch_s* b) {
   QW_CHECK_CUDA(cudaMalloc(&b->d_done, std::max<int64_t>(1, ndone_acc) * sizeof(unsigned int)));
   QW_CHECK_CUDA(cudaMemcpy(b->d_walks, walks.data(), walks.size() * sizeof(BatchWalk), cudaMemcpyHostToDevice));
   QW_CHECK_CUDA(cudaMemcpy(b->d_groups, groups.data(), groups.size() * sizeof(BatchGroup), cudaMemcpyHostToDevice));
+  std::vector<int64_t> gi0(groups.size());
+  for (size_t i = 0; i < groups.size(); ++i) gi0[i] = groups[i].item0;
+  QW_CHECK_CUDA(cudaMalloc(&b->d_group_item0, gi0.size() * sizeof(int64_t)));
+  QW_CHECK_CUDA(cudaMemcpy(b->d_group_item0, gi0.data(), gi0.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   QW_CHECK_CUDA(cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   QW_CHECK_CUDA(cudaMemcpy(b->d_rounds, rounds.data(), rounds.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   int per_sm = 0, nsm = 0;
@@ -358,7 +390,8 @@ static qw_status build_schedule(qw_batch_s* b) {
 static qw_status launch_batch(qw_batch_s* b, cudaStream_t s) {
   QW_CHECK_CUDA(cudaMemsetAsync(b->d_done, 0, std::max<int64_t>(1, b->ndone) * sizeof(unsigned int), s));
   QW_CHECK_CUDA(cudaMemsetAsync(b->d_ctl, 0, sizeof(BatchCtl), s));
-  batch_kernel<<<b->grid, 256, 0, s>>>(b->d_walks, b->d_groups, b->ngroups, b->d_tiles, b->d_rounds,
+  batch_kernel<<<b->grid, 256, 0, s>>>(b->d_walks, b->d_groups, b->d_group_item0, b->ngroups, b->d_tiles,
+                                       b->d_rounds,
                                        b->total_items, b->d_done, b->d_ctl);
   QW_CHECK_LAUNCH("batch kernel launch");
   return QW_OK;
