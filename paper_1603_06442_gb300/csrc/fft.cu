@@ -170,6 +170,21 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __rest
   }
 }
 
+// Global -> shared copy of one complex element without a register round trip
+// (cp.async; a source size of 0 writes zeros), and the wait for this thread's copies.
+template <typename V>
+__device__ __forceinline__ void cp_async_elem(V* dst, const V* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned n = valid ? (unsigned)sizeof(V) : 0u;
+  if constexpr (sizeof(V) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename T, bool INV, int R1, int R2, bool CONTIG>
 __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restrict__ data, FftPass p,
                                                     const typename Cx<T>::t* __restrict__ tw_line,
@@ -195,20 +210,16 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restric
     base = o * (int64_t)L * S + i;
     tw_b = i / p.tw_div;
   }
-  // twiddles of step A, fetched before the data so their latency overlaps the loads
-  V tw[R2];
-  if (r < R1) {
-#pragma unroll
-    for (int k2 = 1; k2 < R2; ++k2) tw[k2] = tw_line[r * k2];  // omega_L^{n1 k2}
-  }
-  // ---- load into shared memory, element n of line c at sm[c + CP n]; every load of
-  // the thread is issued before the first shared-memory store (full unroll)
-  if (CONTIG) {  // S == 1: the CTA's lines are one contiguous run
+  // twiddles of step A, read from the per-line table (L1-resident) when needed
+  const TwRow<V> tw{tw_line, r};
+  // ---- load into shared memory, element n of line c at sm[c + CP n], by cp.async: the
+  // copies go straight to shared memory, so all of them are in flight at once without
+  // holding registers (zero-filled past the last line)
+  if (CONTIG) {  // S == 1: the CTA's lines are one contiguous run (never a twiddled pass)
     // element e = tid + 256 j of the run sits at line e / L, position e % L; both come
     // from tid / L and tid % L plus compile-time offsets (no division per element)
     constexpr int NE = (C * L + 255) / 256;
     const int t_c = tid / L, t_x = tid - (tid / L) * L;
-    V v[NE];
 #pragma unroll
     for (int j = 0; j < NE; ++j) {
       int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
@@ -216,35 +227,23 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restric
         xx -= L;
         ++cc;
       }
-      v[j].x = 0;
-      v[j].y = 0;
-      if (cc < C && l0 + cc < nlines) v[j] = data[l0 * L + tid + 256 * j];
+      const bool ok = l0 + cc < nlines;
+      if (cc < C) cp_async_elem(&sm[cc + CP * xx], ok ? data + l0 * L + tid + 256 * j : data, ok);
     }
-#pragma unroll
-    for (int j = 0; j < NE; ++j) {
-      int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
-      if (xx >= L) {
-        xx -= L;
-        ++cc;
-      }
-      if (cc < C) sm[cc + CP * xx] = v[j];
-    }
+    cp_async_wait_all();
   } else if (r < TPL) {
     constexpr int NL = (L + TPL - 1) / TPL;
-    V v[NL];
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
       const int n = r + TPL * j;
-      v[j].x = 0;
-      v[j].y = 0;
-      if (live && n < L) v[j] = data[base + (int64_t)n * S];
+      if (n < L) cp_async_elem(&sm[c + CP * n], live ? data + base + (int64_t)n * S : data, live);
     }
+    cp_async_wait_all();
+    if (INV && p.twiddle && live) {  // the inverse applies the inter-pass twiddle on load
 #pragma unroll
-    for (int j = 0; j < NL; ++j) {
-      const int n = r + TPL * j;
-      if (n < L) {
-        if (INV && p.twiddle && live) v[j] = cmulc(v[j], twiddle_big(tw_hi, tw_lo, (int64_t)n * tw_b, p.tlo_bits));
-        sm[c + CP * n] = v[j];
+      for (int j = 0; j < NL; ++j) {
+        const int n = r + TPL * j;
+        if (n < L) sm[c + CP * n] = cmulc(sm[c + CP * n], twiddle_big(tw_hi, tw_lo, (int64_t)n * tw_b, p.tlo_bits));
       }
     }
   }
