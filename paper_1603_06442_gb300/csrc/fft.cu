@@ -170,21 +170,6 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __rest
   }
 }
 
-// Global -> shared copy of one complex element without a register round trip
-// (cp.async; a source size of 0 writes zeros), and the wait for this thread's copies.
-template <typename V>
-__device__ __forceinline__ void cp_async_elem(V* dst, const V* src, bool valid) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  const unsigned n = valid ? (unsigned)sizeof(V) : 0u;
-  if constexpr (sizeof(V) == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
-  else
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
 template <typename T, bool INV, int R1, int R2, bool CONTIG>
 __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restrict__ data, FftPass p,
                                                     const typename Cx<T>::t* __restrict__ tw_line,

@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t
 // different axes commute).  Needs the x axis in one register pass of length
 // L = R1 * R2 (natural order along x); y, z may be digit-permuted (freq_of).
 template <int R1, int R2>
-__global__ void __launch_bounds__(256) fused_x_kernel(int dim, AxesDev a, int64_t count, Mass ms,
+__global__ void __launch_bounds__(256, 3) fused_x_kernel(int dim, AxesDev a, int64_t count, Mass ms,
                                                       const double* __restrict__ omega, TimeArg ta, float scale_in,
                                                       const double* __restrict__ norm0, float2* __restrict__ data,
                                                       const float2* __restrict__ tw_line) {
@@ -634,36 +634,24 @@ __global__ void __launch_bounds__(256) fused_x_kernel(int dim, AxesDev a, int64_
   const int64_t row0 = (int64_t)blockIdx.x * RW;
   const int tid = threadIdx.x, c = tid % C, r = tid / C;
   const TwRow<V> tw{tw_line, r};
-  // ---- load: consecutive threads read consecutive x of one line; line cc = w P + p
+  // ---- load (cp.async): consecutive threads read consecutive x of one line; line cc = w P + p
   // holds plane p of row row0 + w (P is a power of two).  Element e = tid + 256 j sits
   // at line e / L, position e % L, from tid / L and tid % L plus compile-time offsets.
   constexpr int NE = (C * L + 255) / 256;
   const int t_c = tid / L, t_x = tid - (tid / L) * L;
   const int lgP = dim == 1 ? 1 : (dim == 2 ? 2 : 3);
-  {
-    V v[NE];
 #pragma unroll
-    for (int j = 0; j < NE; ++j) {
-      int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
-      if (xx >= L) {
-        xx -= L;
-        ++cc;
-      }
-      const int p = cc & (P - 1), w = cc >> lgP;
-      v[j].x = 0.f;
-      v[j].y = 0.f;
-      if (cc < CU && row0 + w < nrows) v[j] = data[p * count + (row0 + w) * L + xx];
+  for (int j = 0; j < NE; ++j) {
+    int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
+    if (xx >= L) {
+      xx -= L;
+      ++cc;
     }
-#pragma unroll
-    for (int j = 0; j < NE; ++j) {
-      int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
-      if (xx >= L) {
-        xx -= L;
-        ++cc;
-      }
-      if (cc < C) sm[cc + CP * xx] = v[j];
-    }
+    const int p = cc & (P - 1), w = cc >> lgP;
+    const bool ok = cc < CU && row0 + w < nrows;
+    if (cc < C) cp_async_elem(&sm[cc + CP * xx], ok ? data + p * count + (row0 + w) * L + xx : data, ok);
   }
+  cp_async_wait_all();
   __syncthreads();
   reg_fft_steps<float, false, R1, R2, CP>(sm, c, r, tw);
   // ---- D_k^t at every (row, k) of the CTA
