@@ -64,8 +64,12 @@ def build(force=False, verbose=False, extra_flags=()):
         return obj
 
     srcs = sources()
-    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    # the register-FFT units are the long poles: start them first
+    heavy = [f for f in srcs if os.path.basename(f).startswith(("fused_x_", "fft", "spectral"))]
+    order = heavy + [f for f in srcs if f not in heavy]
+    workers = max(1, min(len(srcs), os.cpu_count() or 8, 16))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        objs = list(ex.map(compile_one, order))
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)

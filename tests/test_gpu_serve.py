@@ -64,7 +64,9 @@ def test_device_packet_matches_generator(qb, dim, N, dtype):
 
 
 REQS = [(1, 96, 0.1, 57), (2, 24, 0.3, 33), (3, 16, 0.2, 100), (3, 24, 0.05, 1000), (2, 18, 0.45, 7),
-        (1, 1024, 0.01, 99991), (2, 48, 0.003, 100000), (3, 32, 0.3, 77777), (1, 4096, 0.0, 31)]
+        (1, 1024, 0.01, 99991), (2, 48, 0.003, 100000), (3, 32, 0.3, 77777), (1, 4096, 0.0, 31),
+        # x lengths with a fused x pass (weights, D_k^t and the x transforms in one kernel)
+        (2, 64, 0.2, 5000), (2, 96, 0.35, 123), (3, 128, 0.15, 1000)]
 
 
 def oracle_obs(dim, N, m, t, x0, sig, k0, chi):
@@ -94,8 +96,8 @@ def test_served_results_match_oracle(qb):
 
 
 def test_same_result_alone_and_in_the_mix(qb):
-    probe = (3, 32, 0.17, 4321)
-    kw = dict(x0=[16, 16, 16], sigma=3.0, k0=[0.1, 0.2, 0.0], chi=CHI[3])
+    probe = (3, 128, 0.17, 4321)   # x length 64: the fused x pass
+    kw = dict(x0=[64, 64, 64], sigma=8.0, k0=[0.1, 0.2, 0.0], chi=CHI[3])
     srv = qb.qw_server_create(512 << 20, slots=6, max_pending=256)
     tk = qb.qw_submit(srv, qb.make_request(*probe, **kw))
     alone = wait_all(qb, srv, [tk])[tk][0]

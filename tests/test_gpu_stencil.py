@@ -119,6 +119,7 @@ def test_config_1d_packet(qb, dtype):
     got = run_steps(qb, 1, N, m, dtype, a, t)
     exp = walk.step(1, m, a, t)
     err = rel_l2(got, exp)
+    print("1D N=1024 t=512 stencil %s rel-L2 %.3e norm drift %.3e" % (dtype, err, abs(np.sum(np.abs(got) ** 2) - 1.0)))
     assert err <= tol(dtype, t), err
 
 
@@ -166,6 +167,7 @@ def test_bcc512_sampled(qb, dtype, variant):
         M = N // 2
         g = got[0, :, centre[2] // 2 % M, centre[1] // 2 % M, centre[0] // 2 % M]
         worst = max(worst, np.linalg.norm(g - exp) / np.linalg.norm(exp))
+    print("BCC512 t=6 sampled %s %s worst rel-L2 %.3e" % (dtype, variant, worst))
     assert worst <= (1e-11 if dtype == "c128" else 1e-5), worst
 
 
