@@ -85,6 +85,8 @@ static qw_status prepare_spectral(qw_plan_s* p) {
   const int nq = p->g.dim == 3 ? 2 : 1;
   QW_CHECK_CUDA(cudaMalloc(&p->omega, sizeof(double) * nq * p->g.vol));
   QW_CHECK_CUDA(cudaMalloc(&p->spec_partials, sizeof(double) * 2 * kObsBlocks));
+  if (fused_x_supported(p->g, p->fft, p->dtype))
+    QW_CHECK_CUDA(cudaMalloc(&p->xw_partials, sizeof(double) * 2 * fused_x_grid(p->g)));
   st = launch_omega_table(p->g, spec_axes(p->g, p->fft), p->n, p->mass, p->omega, 0, p->dtype == QW_C64);
   if (st != QW_OK) return st;
   QW_CHECK_CUDA(cudaDeviceSynchronize());
@@ -191,6 +193,7 @@ qw_status qw_plan_destroy(qw_plan p) {
   fft_plan_destroy(&p->fft);
   if (p->omega) cudaFree(p->omega);
   if (p->spec_partials) cudaFree(p->spec_partials);
+  if (p->xw_partials) cudaFree(p->xw_partials);
   delete p;
   return QW_OK;
 }
@@ -369,17 +372,30 @@ qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   st = launch_position_moments(p->g, p->dtype, psi, p->red_partials, p->red_result, s);
   if (st != QW_OK) return st;
-  // particle weights need the spectrum: forward DFT of a copy in the scratch field
+  // particle weights need the spectrum (computed into the scratch field)
   const bool kspace = fft_size_ok(p->g.nx) && fft_size_ok(p->g.ny) && fft_size_ok(p->g.nz);
   if (kspace) {
     st = prepare_spectral(p);
     if (st != QW_OK) return st;
-    QW_CHECK_CUDA(cudaMemcpyAsync(p->scratch, psi, (size_t)p->g.elems * p->elem_bytes, cudaMemcpyDeviceToDevice, s));
-    st = fft_forward(p->fft, p->g.dim, p->scratch, s);
-    if (st != QW_OK) return st;
-    st = launch_particle_weights(p->g, spec_axes(p->g, p->fft), p->dtype, p->n, p->mass, p->scratch,
-                                 p->spec_partials, p->red_result + 4, s);
-    if (st != QW_OK) return st;
+    const SpecAxes ax = spec_axes(p->g, p->fft);
+    if (p->xw_partials) {
+      // the outermost axis reads psi and writes the scratch field, the middle axis works in
+      // place, and the x transform is done in shared memory by the weights kernel itself
+      st = fft_forward_axis_from(p->fft, p->g.dim - 1, psi, p->scratch, s);
+      for (int a = p->g.dim - 2; a >= 1 && st == QW_OK; --a) st = fft_forward_axis(p->fft, a, p->scratch, s);
+      if (st != QW_OK) return st;
+      st = launch_weights_fused_x(p->g, ax, p->fft, p->n, p->mass, p->scratch, p->xw_partials, p->red_result + 4, s);
+      if (st != QW_OK) return st;
+    } else {
+      // particle weights need the spectrum: forward DFT of a copy in the scratch field
+      QW_CHECK_CUDA(
+          cudaMemcpyAsync(p->scratch, psi, (size_t)p->g.elems * p->elem_bytes, cudaMemcpyDeviceToDevice, s));
+      st = fft_forward(p->fft, p->g.dim, p->scratch, s);
+      if (st != QW_OK) return st;
+      st = launch_particle_weights(p->g, ax, p->dtype, p->n, p->mass, p->scratch, p->spec_partials,
+                                   p->red_result + 4, s);
+      if (st != QW_OK) return st;
+    }
   }
   QW_CHECK_CUDA(cudaMemcpyAsync(p->red_host, p->red_result, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
   st = check_flags(p, s);

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __rest
 }
 
 template <typename T, bool INV, int R1, int R2, bool CONTIG>
-__global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restrict__ data, FftPass p,
+__global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* data, const typename Cx<T>::t* src, FftPass p,
                                                     const typename Cx<T>::t* __restrict__ tw_line,
                                                     const typename Cx<T>::t* __restrict__ tw_hi,
                                                     const typename Cx<T>::t* __restrict__ tw_lo) {
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restric
         ++cc;
       }
       const bool ok = l0 + cc < nlines;
-      if (cc < C) cp_async_elem(&sm[cc + CP * xx], ok ? data + l0 * L + tid + 256 * j : data, ok);
+      if (cc < C) cp_async_elem(&sm[cc + CP * xx], ok ? src + l0 * L + tid + 256 * j : src, ok);
     }
     cp_async_wait_all();
   } else if (r < TPL) {
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restric
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
       const int n = r + TPL * j;
-      if (n < L) cp_async_elem(&sm[c + CP * n], live ? data + base + (int64_t)n * S : data, live);
+      if (n < L) cp_async_elem(&sm[c + CP * n], live ? src + base + (int64_t)n * S : src, live);
     }
     cp_async_wait_all();
     if (INV && p.twiddle && live) {  // the inverse applies the inter-pass twiddle on load
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* __restric
 }
 
 template <typename T, bool INV, int R1, int R2>
-static qw_status launch_2f(const FftPass& p, void* data, cudaStream_t st) {
+static qw_status launch_2f(const FftPass& p, void* data, const void* src, cudaStream_t st) {
   using V = typename Cx<T>::t;
   constexpr int L = R1 * R2, TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
   const size_t smem = (size_t)L * ((C % 2 == 0) ? C + 1 : C) * sizeof(V);
@@ -277,7 +277,7 @@ static qw_status launch_2f(const FftPass& p, void* data, cudaStream_t st) {
       attr[0] = true;
     }
     fft2f_kernel<T, INV, R1, R2, true><<<(unsigned)grid, 256, smem, st>>>(
-        static_cast<V*>(data), p, static_cast<const V*>(p.tw_line), static_cast<const V*>(p.tw_hi),
+        static_cast<V*>(data), static_cast<const V*>(src), p, static_cast<const V*>(p.tw_line), static_cast<const V*>(p.tw_hi),
         static_cast<const V*>(p.tw_lo));
   } else {
     if (!attr[1]) {
@@ -286,7 +286,7 @@ static qw_status launch_2f(const FftPass& p, void* data, cudaStream_t st) {
       attr[1] = true;
     }
     fft2f_kernel<T, INV, R1, R2, false><<<(unsigned)grid, 256, smem, st>>>(
-        static_cast<V*>(data), p, static_cast<const V*>(p.tw_line), static_cast<const V*>(p.tw_hi),
+        static_cast<V*>(data), static_cast<const V*>(src), p, static_cast<const V*>(p.tw_line), static_cast<const V*>(p.tw_hi),
         static_cast<const V*>(p.tw_lo));
   }
   QW_CHECK_LAUNCH("fft two-factor pass launch");
@@ -298,10 +298,10 @@ static qw_status launch_2f(const FftPass& p, void* data, cudaStream_t st) {
 // (the planner uses this to split long axes into register-kernel passes).
 #define QW_2F(LEN, A, B)                                 \
   case LEN:                                              \
-    if (p) *out = launch_2f<T, INV, A, B>(*p, data, st); \
+    if (p) *out = launch_2f<T, INV, A, B>(*p, data, src, st); \
     return true;
 template <typename T, bool INV>
-static bool run_2f(int L, const FftPass* p, void* data, cudaStream_t st, qw_status* out) {
+static bool run_2f(int L, const FftPass* p, void* data, const void* src, cudaStream_t st, qw_status* out) {
   switch (L) {
     QW_REG_LENGTHS_POW2(QW_2F)
     default: break;
@@ -341,7 +341,7 @@ bool fft_size_ok(int64_t L) {
 template <typename T>
 static double pass_cost(int64_t L) {
   qw_status unused;
-  if (run_2f<T, false>((int)L, nullptr, nullptr, nullptr, &unused)) return 1.0;
+  if (run_2f<T, false>((int)L, nullptr, nullptr, nullptr, nullptr, &unused)) return 1.0;
   return L < 64 ? 8.0 : 4.0;
 }
 
@@ -606,10 +606,14 @@ void fft_plan_destroy(FftPlan* f) {
 }
 
 template <typename T, bool INV>
-static qw_status run_pass(const FftPass& p, void* data, cudaStream_t st) {
+static qw_status run_pass(const FftPass& p, void* data, cudaStream_t st, const void* src = nullptr) {
   using V = typename Cx<T>::t;
   qw_status s2;
-  if (run_2f<T, INV>(p.L, &p, data, st, &s2)) return s2;
+  if (run_2f<T, INV>(p.L, &p, data, src ? src : data, st, &s2)) return s2;
+  if (src && src != data) {  // the Stockham kernel works in place: copy first
+    const size_t bytes = (size_t)(p.O * p.S) * p.L * sizeof(V);
+    QW_CHECK_CUDA(cudaMemcpyAsync(data, src, bytes, cudaMemcpyDeviceToDevice, st));
+  }
   static bool attr[2] = {false, false};
   if (!attr[INV]) {
     QW_CHECK_CUDA(cudaFuncSetAttribute(fft_pass_kernel<T, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -635,6 +639,18 @@ qw_status fft_forward_axis(const FftPlan& f, int ax, void* data, cudaStream_t st
   for (int q = 0; q < A.count; ++q) {
     const FftPass& p = f.pass[A.first + q];
     qw_status s = f.dtype == QW_C64 ? run_pass<float, false>(p, data, st) : run_pass<double, false>(p, data, st);
+    if (s != QW_OK) return s;
+  }
+  return QW_OK;
+}
+
+qw_status fft_forward_axis_from(const FftPlan& f, int ax, const void* src, void* dst, cudaStream_t st) {
+  const FftAxis& A = f.axis[ax];
+  for (int q = 0; q < A.count; ++q) {
+    const FftPass& p = f.pass[A.first + q];
+    const void* from = q == 0 ? src : nullptr;
+    qw_status s = f.dtype == QW_C64 ? run_pass<float, false>(p, dst, st, from)
+                                    : run_pass<double, false>(p, dst, st, from);
     if (s != QW_OK) return s;
   }
   return QW_OK;

@@ -75,5 +75,8 @@ qw_status fft_forward(const FftPlan& f, int dim, void* data, cudaStream_t st);
 qw_status fft_inverse(const FftPlan& f, int dim, void* data, cudaStream_t st);
 qw_status fft_forward_axis(const FftPlan& f, int ax, void* data, cudaStream_t st);
 qw_status fft_inverse_axis(const FftPlan& f, int ax, void* data, cudaStream_t st);
+// Forward passes of one axis reading src and writing dst (the first pass out of place,
+// the rest in place on dst); src is not modified.
+qw_status fft_forward_axis_from(const FftPlan& f, int ax, const void* src, void* dst, cudaStream_t st);
 
 }  // namespace qw

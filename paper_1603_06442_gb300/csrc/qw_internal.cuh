@@ -139,6 +139,12 @@ bool fused_x_supported(const Geometry& g, const FftPlan& f, qw_dtype dt);
 qw_status launch_evolve_fused_x(const Geometry& g, const SpecAxes& ax, const FftPlan& f, double n, double m,
                                 const double* omega, int64_t t, void* psi, cudaStream_t st,
                                 const double* norm0 = nullptr);
+// With the same tiling, the particle-weight sums of a spectrum still to be transformed
+// along x (complex64): 2 doubles per CTA (fused_x_grid CTAs) into partials, folded into
+// result[0..1]; data is only read.
+int64_t fused_x_grid(const Geometry& g);
+qw_status launch_weights_fused_x(const Geometry& g, const SpecAxes& ax, const FftPlan& f, double n, double m,
+                                 const void* data, double* partials, double* result, cudaStream_t st);
 qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
                                   const double* omega, int64_t t, void* psi_hat, cudaStream_t st,
                                   const double* norm0 = nullptr);
@@ -176,6 +182,7 @@ struct qw_plan_s {
   double* omega;        // omega_k per stored wave vector (two per cell on the BCC lattice); complex64
                         // plans hold nu = omega / 2 pi as FP32 (hi, lo) pairs instead
   double* spec_partials;  // 2 * kObsBlocks doubles for the particle-weight reduction
+  double* xw_partials;    // 2 doubles per CTA of the x-pass weights (when the x pass is fused)
   double* red_partials; // 4 * kObsBlocks doubles
   double* red_result;   // 4 doubles (device)
   double* red_host;     // 4 doubles (pinned host)

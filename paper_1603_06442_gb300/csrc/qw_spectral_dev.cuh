@@ -677,6 +677,90 @@ qw_status launch_fused(const Geometry& g, const SpecAxes& ax, double n, double m
   return QW_OK;
 }
 
+// Particle-weight sums of a spectrum whose remaining transform is the x DFT (complex64):
+// the rows of every plane (already transformed along y and z) come in by cp.async, are
+// transformed along x in shared memory and summed per wave vector (weights_point); nothing
+// is written back.  Same tiling as fused_x_kernel; partials[2 b], [2 b + 1] per CTA b.
+template <int R1, int R2>
+__global__ void __launch_bounds__(256, 3) weights_x_kernel(int dim, AxesDev a, int64_t count, Mass ms,
+                                                        const float2* __restrict__ data,
+                                                        const float2* __restrict__ tw_line,
+                                                        double* __restrict__ partials) {
+  using V = float2;
+  constexpr int L = R1 * R2, TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
+  constexpr int CP = (C % 2 == 0) ? C + 1 : C;
+  extern __shared__ __align__(16) unsigned char wx_smem[];
+  V* sm = reinterpret_cast<V*>(wx_smem);
+  const int P = planes_of(dim);
+  const int RW = C / P, CU = RW * P;
+  const int64_t nrows = count / L;
+  const int64_t row0 = (int64_t)blockIdx.x * RW;
+  const int tid = threadIdx.x, c = tid % C, r = tid / C;
+  const TwRow<V> tw{tw_line, r};
+  constexpr int NE = (C * L + 255) / 256;
+  const int t_c = tid / L, t_x = tid - (tid / L) * L;
+  const int lgP = dim == 1 ? 1 : (dim == 2 ? 2 : 3);
+#pragma unroll
+  for (int j = 0; j < NE; ++j) {
+    int xx = t_x + (256 * j) % L, cc = t_c + (256 * j) / L;
+    if (xx >= L) {
+      xx -= L;
+      ++cc;
+    }
+    const int p = cc & (P - 1), w = cc >> lgP;
+    const bool ok = cc < CU && row0 + w < nrows;
+    if (cc < C) cp_async_elem(&sm[cc + CP * xx], ok ? data + p * count + (row0 + w) * L + xx : data, ok);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  reg_fft_steps<float, false, R1, R2, CP>(sm, c, r, tw);
+  double acc[2] = {0.0, 0.0};
+  for (int q = tid; q < RW * L; q += 256) {
+    const int w = q / L, k = q - w * L;
+    const int64_t row = row0 + w;
+    if (row >= nrows) continue;
+    const int ny = (int)a.len[1], rowi = (int)row;
+    const int64_t yy = rowi % ny, zz = rowi / ny;
+    V v[8];
+#pragma unroll
+    for (int pp = 0; pp < 8; ++pp)
+      if (pp < P) v[pp] = sm[w * P + pp + CP * k];
+    weights_point<float>(dim, a, k, yy, zz, ms, v, acc);
+  }
+  block_sum<2, 256>(acc);
+  if (tid == 0) {
+    partials[2 * blockIdx.x] = acc[0];
+    partials[2 * blockIdx.x + 1] = acc[1];
+  }
+}
+
+// CTAs of the fused x pass and of weights_x_kernel (rows of RW per CTA)
+template <int R1, int R2>
+inline int64_t fused_x_ctas(const Geometry& g) {
+  constexpr int TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
+  const int RW = C / (g.dim == 1 ? 2 : (g.dim == 2 ? 4 : 8));
+  return (g.vol / g.nx + RW - 1) / RW;
+}
+
+template <int R1, int R2>
+qw_status launch_weights_x(const Geometry& g, const SpecAxes& ax, double n, double m, const void* data,
+                           const void* tw_line, double* partials, cudaStream_t st) {
+  constexpr int L = R1 * R2, TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
+  constexpr int CP = (C % 2 == 0) ? C + 1 : C;
+  const size_t smem = (size_t)L * CP * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    QW_CHECK_CUDA(cudaFuncSetAttribute(weights_x_kernel<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    attr = true;
+  }
+  weights_x_kernel<R1, R2><<<(unsigned)fused_x_ctas<R1, R2>(g), 256, smem, st>>>(
+      g.dim, to_dev(ax), g.vol, make_mass(n, m), static_cast<const float2*>(data),
+      static_cast<const float2*>(tw_line), partials);
+  QW_CHECK_LAUNCH("x-pass particle weights launch");
+  return QW_OK;
+}
+
 // Line lengths of the fused x pass: the register lengths from 64 up (shorter x axes are
 // small boxes, where the separate passes cost as little), in six groups that the
 // instantiation units fused_x_[1-6].cu compile in parallel.
@@ -689,11 +773,15 @@ qw_status launch_fused(const Geometry& g, const SpecAxes& ax, double n, double m
 #define QW_FUSED_LENGTHS(X)                                                                       \
   QW_FUSED_LENGTHS_1(X) QW_FUSED_LENGTHS_2(X) QW_FUSED_LENGTHS_3(X) QW_FUSED_LENGTHS_4(X) \
   QW_FUSED_LENGTHS_5(X) QW_FUSED_LENGTHS_6(X)
-#define QW_FUSED_X_INSTANTIATE(LEN, A, B)                                                                    \
-  template qw_status launch_fused<A, B>(const Geometry&, const SpecAxes&, double, double, const double*, \
-                                        int64_t, void*, const void*, cudaStream_t, const double*);
-#define QW_FUSED_X_EXTERN(LEN, A, B)                                                                              \
-  extern template qw_status launch_fused<A, B>(const Geometry&, const SpecAxes&, double, double, const double*, \
-                                               int64_t, void*, const void*, cudaStream_t, const double*);
+#define QW_FUSED_X_INSTANTIATE(LEN, A, B)                                                                     \
+  template qw_status launch_fused<A, B>(const Geometry&, const SpecAxes&, double, double, const double*,  \
+                                        int64_t, void*, const void*, cudaStream_t, const double*);         \
+  template qw_status launch_weights_x<A, B>(const Geometry&, const SpecAxes&, double, double, const void*, \
+                                            const void*, double*, cudaStream_t);
+#define QW_FUSED_X_EXTERN(LEN, A, B)                                                                               \
+  extern template qw_status launch_fused<A, B>(const Geometry&, const SpecAxes&, double, double, const double*,  \
+                                               int64_t, void*, const void*, cudaStream_t, const double*);         \
+  extern template qw_status launch_weights_x<A, B>(const Geometry&, const SpecAxes&, double, double, const void*, \
+                                                   const void*, double*, cudaStream_t);
 
 }  // namespace qw

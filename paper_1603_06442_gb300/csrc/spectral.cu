@@ -199,6 +199,39 @@ qw_status launch_evolve_fused_x(const Geometry& g, const SpecAxes& ax, const Fft
   }
 }
 
+int64_t fused_x_grid(const Geometry& g) {
+  switch (g.nx) {
+#define QW_FX(LEN, A, B) \
+  case LEN:              \
+    return fused_x_ctas<A, B>(g);
+    QW_FUSED_LENGTHS(QW_FX)
+#undef QW_FX
+    default:
+      return 0;
+  }
+}
+
+qw_status launch_weights_fused_x(const Geometry& g, const SpecAxes& ax, const FftPlan& f, double n, double m,
+                                 const void* data, double* partials, double* result, cudaStream_t st) {
+  const void* tw = f.pass[f.axis[0].first].tw_line;
+  qw_status s2 = QW_OK;
+  switch (g.nx) {
+#define QW_FX(LEN, A, B)                                                      \
+  case LEN:                                                                   \
+    s2 = launch_weights_x<A, B>(g, ax, n, m, data, tw, partials, st); \
+    break;
+    QW_FUSED_LENGTHS(QW_FX)
+#undef QW_FX
+    default:
+      set_error("x-pass weights: no register kernel for length %lld", (long long)g.nx);
+      return QW_EINVAL;
+  }
+  if (s2 != QW_OK) return s2;
+  fold2_kernel<<<1, 256, 0, st>>>(partials, (int)fused_x_grid(g), result);
+  QW_CHECK_LAUNCH("x-pass weights fold launch");
+  return QW_OK;
+}
+
 qw_status launch_particle_weights(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
                                   const void* psi_hat, double* partials, double* result, cudaStream_t st) {
   const int64_t count = kcount(g);

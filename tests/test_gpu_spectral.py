@@ -236,9 +236,11 @@ def test_config3_bcc512_properties(qb, m):
     assert err <= TOL["c64"]
 
 
-@pytest.mark.parametrize("dim,N", [(1, 64), (2, 12), (3, 8), (3, 16)])
+@pytest.mark.parametrize("dim,N", [(1, 64), (2, 12), (3, 8), (3, 16), (2, 64), (2, 96), (3, 128)])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_particle_weights(qb, dim, N, dtype):
+    """Particle weights against the oracle's projectors; the 2D N=64, 96 and BCC N=128 boxes take
+    the complex64 path whose x transform happens inside the weights kernel."""
     m = 0.3
     a = inputs.random_field(dim, N, seed=40 + N)
     plan = qb.Plan(dim, N, m, dtype)
@@ -254,8 +256,8 @@ def test_particle_weights(qb, dim, N, dtype):
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_particle_weight_of_eigenpacket(qb, dtype):
     """A packet built from the paper's eigenvectors with |c+|^2 = 0.7 has w+ = 0.7, conserved."""
-    dim, N, m = 3, 16, 0.2
-    psi = states.packet(3, m, N, (0.3, 0.1, 0.0), 2.0, (8, 8, 8),
+    dim, N, m = 3, 128, 0.2   # x length 64: the x-pass weights kernel in complex64
+    psi = states.packet(3, m, N, (0.3, 0.1, 0.0), 6.0, (64, 64, 64),
                         {(1, 1): np.sqrt(0.7), (-1, -1): np.sqrt(0.3)})
     a = walk.to_device(3, N, psi)
     plan = qb.Plan(dim, N, m, dtype)
