@@ -540,7 +540,8 @@ def batched_measurement(qb, dev, stream, runs=3, n_walks=256):
     return {"walks": len(mix), "site_steps_per_run": site_steps, "ms_per_run": ms,
             "site_steps_per_s": rate, "algorithmic_GBps_at_64B": rate * 64 / 1e9,
             "frac_of_hbm_at_64B": rate * 64 / 1e9 / peak,
-            "note": "groups of walks run L2-resident, so the 64 B/site-step traffic need not reach HBM",
+            "note": "walks are grouped under the autotuned footprint budget; groups within an L2-sized "
+                    "budget run L2-resident, larger budgets trade that for more parallel tiles",
             "autotuned_tile_sites": tile, "autotuned_l2_budget_MiB": budget / 2 ** 20,
             "max_norm_drift_after_%d_runs" % (runs + 1): worst_norm,
             "launches_per_run": 1, "graph": True}

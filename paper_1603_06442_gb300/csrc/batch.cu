@@ -546,7 +546,8 @@ qw_status qw_batch_autotune(qw_batch b, int64_t rounds_cap, void* stream, int64_
     site_steps += g.sites * w.t;
   }
   const int64_t tiles[] = {1024, 2048, 4096, 8192, 16384};
-  const int64_t budgets[] = {int64_t(24) << 20, int64_t(48) << 20, int64_t(96) << 20};
+  const int64_t budgets[] = {int64_t(24) << 20, int64_t(48) << 20, int64_t(96) << 20, int64_t(192) << 20,
+                             int64_t(1) << 30, int64_t(16) << 30};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
