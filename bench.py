@@ -518,7 +518,7 @@ def batched_measurement(qb, dev, stream, runs=3, n_walks=256):
                                    [0.5, 0.5, 0.5j, -0.5j])
         fields.append(torch.from_numpy(a.astype(np.complex64)).to(dev))
     b = qb.Batch([(w["dim"], w["N"], w["mass"], w["t"], x) for w, x in zip(mix, fields)])
-    tile, budget, tuned_rate = b.autotune(rounds_cap=32, stream=stream)
+    tile, budget, tuned_rate = b.autotune(rounds_cap=256, stream=stream)
     site_steps = 0
     for w in mix:
         sites = w["N"] ** 2 if w["dim"] == 2 else w["N"] ** 3 // 4

@@ -190,10 +190,12 @@ qw_status qw_batch_set_tiling(qw_batch batch, int64_t tile_sites, int64_t l2_bud
 qw_status qw_batch_get_tiling(qw_batch batch, int64_t* tile_sites, int64_t* l2_budget_bytes, int64_t* items);
 
 /* Autotuner: times the batch kernel for every tile size in {1K, 2K, 4K, 8K,
- * 16K} sites and L2 share in {24, 48, 96} MiB on stand-in fields of the same
- * sizes (zero-filled scratch, allocated and freed here; the walks' fields are
- * not touched), with every walk's step count capped at rounds_cap, and keeps
- * the fastest setting.  Optional outputs: chosen tile, budget and the measured
+ * 16K} sites and footprint budget in {24, 48, 96, 192 MiB, 1, 16 GiB} (walks
+ * whose two buffers fit one budget form a group; small budgets keep a group in
+ * L2, large ones give more parallel tiles) on stand-in fields of the same sizes
+ * (zero-filled scratch, allocated and freed here; the walks' fields are not
+ * touched), with the step counts scaled so that the longest walk runs
+ * rounds_cap steps (the mix keeps its shape), and keeps the fastest setting.  Optional outputs: chosen tile, budget and the measured
  * site-steps/s.  Synchronous.  Errors: QW_EINVAL, QW_ENOMEM, QW_ECUDA. */
 qw_status qw_batch_autotune(qw_batch batch, int64_t rounds_cap, void* stream, int64_t* best_tile,
                             int64_t* best_budget, double* best_rate);

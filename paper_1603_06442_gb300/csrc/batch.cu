@@ -537,10 +537,14 @@ qw_status qw_batch_autotune(qw_batch b, int64_t rounds_cap, void* stream, int64_
   QW_CHECK_CUDA(cudaMemsetAsync(pool, 0, total, s));
   int64_t off = 0;
   int64_t site_steps = 0;
+  int64_t tmax = 1;
+  for (auto& w : b->desc) tmax = std::max<int64_t>(tmax, w.t);
   for (auto& w : b->desc) {
     w.psi_dev = static_cast<char*>(pool) + off;
     off += field_bytes(w);
-    w.t = std::min<int64_t>(w.t, rounds_cap);
+    // step counts scaled so the longest walk runs rounds_cap steps: the tuning run keeps the
+    // mix's shape, the tail of the longest walks included (capping every walk would drop it)
+    if (tmax > rounds_cap) w.t = std::max<int64_t>(1, (w.t * rounds_cap + tmax - 1) / tmax);
     Geometry g;
     make_geometry(w.dim, w.N, &g);
     site_steps += g.sites * w.t;
