@@ -524,9 +524,11 @@ __device__ __forceinline__ int planes_of(int dim) { return dim == 1 ? 2 : (dim =
 
 // Particle-weight sums of the spectral values v of storage position (x, y, z) (v as in
 // evolve_point): acc[0] += sum |c|^2, acc[1] += sum c^dag G^ c over the wave vector(s).
-template <typename T>
+// (A: the accumulator type; complex64 callers sum a few points in FP32 and move the sums
+// to FP64 afterwards, since every FP64 operation costs ~64 FP32 ones here)
+template <typename T, typename A>
 __device__ __forceinline__ void weights_point(int dim, const AxesDev& a, int64_t x, int64_t y, int64_t z,
-                                              const Mass& ms, const typename Cx2<T>::t (&vin)[8], double (&acc)[2]) {
+                                              const Mass& ms, const typename Cx2<T>::t (&vin)[8], A (&acc)[2]) {
   using V = typename Cx2<T>::t;
   int64_t f[3], fs;
   wave_vectors(dim, x, y, z, a, f, fs);
@@ -574,8 +576,8 @@ __device__ __forceinline__ void weights_point(int dim, const AxesDev& a, int64_t
         gdot += -(v[q].x * w[q].y - v[q].y * w[q].x);
       }
     }
-    acc[0] += (double)nrm;
-    acc[1] += (double)gdot;
+    acc[0] += (A)nrm;
+    acc[1] += (A)gdot;
   }
 }
 
@@ -714,7 +716,7 @@ __global__ void __launch_bounds__(256, 3) weights_x_kernel(int dim, AxesDev a, i
   cp_async_wait_all();
   __syncthreads();
   reg_fft_steps<float, false, R1, R2, CP>(sm, c, r, tw);
-  double acc[2] = {0.0, 0.0};
+  float facc[2] = {0.f, 0.f};  // a thread sums RW L / 256 points (2-4) in FP32
   for (int q = tid; q < RW * L; q += 256) {
     const int w = q / L, k = q - w * L;
     const int64_t row = row0 + w;
@@ -725,12 +727,29 @@ __global__ void __launch_bounds__(256, 3) weights_x_kernel(int dim, AxesDev a, i
 #pragma unroll
     for (int pp = 0; pp < 8; ++pp)
       if (pp < P) v[pp] = sm[w * P + pp + CP * k];
-    weights_point<float>(dim, a, k, yy, zz, ms, v, acc);
+    weights_point<float>(dim, a, k, yy, zz, ms, v, facc);
   }
-  block_sum<2, 256>(acc);
+  // warp sums in FP32 (64 points), the eight warp sums in FP64 in a fixed order: an FP64
+  // block reduction per thread would cost more than the thread's points here
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    facc[0] += __shfl_xor_sync(0xffffffffu, facc[0], o);
+    facc[1] += __shfl_xor_sync(0xffffffffu, facc[1], o);
+  }
+  __shared__ float wsum[8][2];
+  if ((tid & 31) == 0) {
+    wsum[tid >> 5][0] = facc[0];
+    wsum[tid >> 5][1] = facc[1];
+  }
+  __syncthreads();
   if (tid == 0) {
-    partials[2 * blockIdx.x] = acc[0];
-    partials[2 * blockIdx.x + 1] = acc[1];
+    double a0 = 0.0, a1 = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      a0 += (double)wsum[w][0];
+      a1 += (double)wsum[w][1];
+    }
+    partials[2 * blockIdx.x] = a0;
+    partials[2 * blockIdx.x + 1] = a1;
   }
 }
 

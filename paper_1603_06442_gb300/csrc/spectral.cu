@@ -113,15 +113,37 @@ __global__ void __launch_bounds__(256) weights_kernel(int dim, AxesDev a, int64_
   double acc[2] = {0.0, 0.0};
   const int64_t nx = a.len[0], ny = a.len[1];
   const int P = planes_of(dim);
+  // segments of up to 16 points summed in T, segment sums added in FP64
+  T seg[2] = {(T)0, (T)0};
+  int nseg = 0;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t x = idx % nx, y = (idx / nx) % ny, z = idx / (nx * ny);
+    int64_t x, y, z;
+    if (count <= 0x7fffffff) {  // 32-bit index arithmetic for planes below 2^31 values
+      const int i32 = (int)idx, nx32 = (int)nx, ny32 = (int)ny;
+      const int yz = i32 / nx32;
+      x = i32 - yz * nx32;
+      y = yz % ny32;
+      z = yz / ny32;
+    } else {
+      x = idx % nx;
+      y = (idx / nx) % ny;
+      z = idx / (nx * ny);
+    }
     V v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
       if (q < P) v[q] = data[q * count + idx];
-    weights_point<T>(dim, a, x, y, z, ms, v, acc);
+    weights_point<T>(dim, a, x, y, z, ms, v, seg);
+    if (++nseg == 16) {
+      acc[0] += (double)seg[0];
+      acc[1] += (double)seg[1];
+      seg[0] = seg[1] = (T)0;
+      nseg = 0;
+    }
   }
+  acc[0] += (double)seg[0];
+  acc[1] += (double)seg[1];
   block_sum<2, 256>(acc);
   if (threadIdx.x == 0) {
     partials[2 * blockIdx.x] = acc[0];

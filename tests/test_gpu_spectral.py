@@ -77,7 +77,7 @@ def test_spectral_line_lengths(qb, N, dtype):
     got = run_spectral(qb, 1, N, m, dtype, a, t)
     exp = walk.step(1, m, a, t)
     err = rel_l2(got, exp)
-    print("1D N=1024 t=512 spectral %s rel-L2 %.3e" % (dtype, err))
+    print("1D line N=%d t=5 spectral %s rel-L2 %.3e" % (N, dtype, err))
     assert err <= TOL[dtype]
 
 
@@ -111,7 +111,7 @@ def test_spectral_long_chain_multipass(qb, dtype, N):
     got = run_spectral(qb, 1, N, m, dtype, a, t)
     exp = walk.step(1, m, a, t)
     err = rel_l2(got, exp)
-    print("1D N=1024 t=512 spectral %s rel-L2 %.3e" % (dtype, err))
+    print("1D N=%d t=3 multipass spectral %s rel-L2 %.3e" % (N, dtype, err))
     assert err <= TOL[dtype]
 
 
