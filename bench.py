@@ -165,7 +165,7 @@ def oracle_cpu_baseline(seconds=12.0):
         psi = walk.step(3, m, psi, 1, mats=mats)
         steps += 1
     dt = time.perf_counter() - t0
-    return {"value": sites * steps / dt, "unit": "site-steps/s", "cores": 1, "kind": "oracle",
+    return {"value": sites * steps / dt, "unit": "site-steps/s", "cores": 1, "kind": "oracle", "seconds": dt,
             "sample": "BCC N=64 box (%d sites), %d oracle update steps in FP64 numpy, %.1f s" % (sites, steps, dt)}
 
 
@@ -183,7 +183,7 @@ def run_reference(args, rank, world):
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": "site-steps/s", "value": v, "unit": "site-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 3000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": 1e3 * float(np.mean([r["seconds"] for r in t_steps])), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c128", "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "note": "oracle timed on a bounded BCC N=64 sample"},
             "cpu_baseline": {"value": v, "unit": "site-steps/s", "cores": 1, "kind": "oracle",
