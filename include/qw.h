@@ -163,6 +163,22 @@ qw_status qw_sync(qw_plan plan, void* stream);
  * Errors: QW_EINVAL, QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
 qw_status qw_observables(qw_plan plan, const void* psi_dev, qw_obs* out, void* stream);
 
+/* End-to-end runs on HOST fields.  For j = 0 .. count-1: copy the field
+ * psi_host[j] (host memory, device layout, qw_plan_field_elems elements;
+ * page-locked memory copies fastest and overlaps) to the device, advance it by
+ * nsteps applications of the update rule (as qw_step) and compute its
+ * observables into out[j] (as qw_observables).  If psi_out_host is not NULL,
+ * psi_out_host[j] (host memory, same size; may equal psi_host[j]) receives the
+ * evolved field.  The fields pass through two device buffers owned by the plan
+ * (allocated by the first call, freed with the plan): the copy of field j + 1
+ * runs on the plan's copy stream while field j is advanced on `stream`, and the
+ * read-back of field j on the copy stream overlaps field j + 1.  Synchronous:
+ * returns when every result is on the host.  count = 0 does nothing.
+ * Errors: QW_EINVAL (null plan, count < 0, nsteps < 0, null psi_host / out or a
+ * null entry), QW_ENOMEM (device buffers), QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
+qw_status qw_run_host(qw_plan plan, const void* const* psi_host, void* const* psi_out_host, int count,
+                      int64_t nsteps, qw_obs* out, void* stream);
+
 /* ---------------------------------------------------------------- batches
  * Many independent walks of uneven size advanced together by one persistent
  * kernel launch, replayed from a CUDA graph (complex64 only).  Each walk is the

@@ -93,6 +93,8 @@ _SIGS = {
     "qw_evolve_spectral": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "qw_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(qw_obs),
                                       ctypes.c_void_p]),
+    "qw_run_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                   ctypes.c_int, ctypes.c_int64, ctypes.POINTER(qw_obs), ctypes.c_void_p]),
 }
 
 
@@ -273,6 +275,32 @@ def qw_observables(plan, psi, stream=None):
     return out.as_dict()
 
 
+def _host_ptr(x):
+    """Address of a host buffer: a CPU torch tensor, a numpy array or an int."""
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if x.is_cuda:
+            raise ValueError("qw_run_host takes host buffers")
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def qw_run_host(plan, fields, nsteps, out_fields=None, stream=None):
+    """Copy each host field to the device, advance it nsteps and return its observables
+    (one dict per field); out_fields (optional) receive the evolved fields."""
+    n = len(fields)
+    ins = (ctypes.c_void_p * max(n, 1))(*[_host_ptr(f) for f in fields])
+    outs = None
+    if out_fields is not None:
+        if len(out_fields) != n:
+            raise ValueError("out_fields must match fields")
+        outs = (ctypes.c_void_p * max(n, 1))(*[_host_ptr(f) for f in out_fields])
+    res = (qw_obs * max(n, 1))()
+    _check(load().qw_run_host(plan, ins, outs, n, int(nsteps), res, _stream(stream)))
+    return [res[j].as_dict() for j in range(n)]
+
+
 def qw_batch_create(walks):
     """walks: list of (dim, N, mass, t, field tensor or device address)."""
     arr = (qw_walk * len(walks))()
@@ -416,6 +444,23 @@ class Plan:
     def observables(self, psi, stream=None):
         self.check_field(psi)
         return qw_observables(self.handle, psi, stream)
+
+    def check_host_field(self, f):
+        if hasattr(f, "is_cuda"):
+            ok = (not f.is_cuda) and f.is_contiguous() and f.dtype == self.torch_dtype and f.numel() == self.elems
+        else:
+            import numpy as np
+            want = np.complex64 if self.dtype == QW_C64 else np.complex128
+            ok = f.dtype == want and f.flags["C_CONTIGUOUS"] and f.size == self.elems
+        if not ok:
+            raise ValueError("host field must be a contiguous CPU %s array with %d elements"
+                             % (self.torch_dtype, self.elems))
+
+    def run_host(self, fields, nsteps, out_fields=None, stream=None):
+        """End to end on host fields (page-locked copies overlap): see qw_run_host."""
+        for f in list(fields) + list(out_fields or []):
+            self.check_host_field(f)
+        return qw_run_host(self.handle, fields, nsteps, out_fields, stream)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -194,6 +194,14 @@ qw_status qw_plan_destroy(qw_plan p) {
   if (p->omega) cudaFree(p->omega);
   if (p->spec_partials) cudaFree(p->spec_partials);
   if (p->xw_partials) cudaFree(p->xw_partials);
+  for (int b = 0; b < 2; ++b) {
+    if (p->hbuf[b]) cudaFree(p->hbuf[b]);
+    if (p->ev_copied[b]) cudaEventDestroy(p->ev_copied[b]);
+    if (p->ev_freed[b]) cudaEventDestroy(p->ev_freed[b]);
+    if (p->ev_stepped[b]) cudaEventDestroy(p->ev_stepped[b]);
+  }
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  if (p->hstage) cudaFreeHost(p->hstage);
   delete p;
   return QW_OK;
 }
@@ -362,18 +370,14 @@ qw_status qw_sync(qw_plan p, void* stream) {
   return check_flags(p, static_cast<cudaStream_t>(stream));
 }
 
-qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) {
-  if (!p || !psi || !out) {
-    set_error("qw_observables: null argument");
-    return QW_EINVAL;
-  }
-  qw_status st = use_device(p);
-  if (st != QW_OK) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  st = launch_position_moments(p->g, p->dtype, psi, p->red_partials, p->red_result, s);
+// Observables of psi: the reductions are enqueued on s, then obs_finish waits for them
+// and fills *out.  kspace: whether the particle weights are computed (axis lengths 2^a 3^b).
+static qw_status obs_enqueue(qw_plan_s* p, const void* psi, cudaStream_t s, double* host_dst, bool* kspace_out) {
+  qw_status st = launch_position_moments(p->g, p->dtype, psi, p->red_partials, p->red_result, s);
   if (st != QW_OK) return st;
   // particle weights need the spectrum (computed into the scratch field)
   const bool kspace = fft_size_ok(p->g.nx) && fft_size_ok(p->g.ny) && fft_size_ok(p->g.nz);
+  *kspace_out = kspace;
   if (kspace) {
     st = prepare_spectral(p);
     if (st != QW_OK) return st;
@@ -397,10 +401,12 @@ qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) 
       if (st != QW_OK) return st;
     }
   }
-  QW_CHECK_CUDA(cudaMemcpyAsync(p->red_host, p->red_result, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  st = check_flags(p, s);
-  if (st != QW_OK) return st;
-  const double* r = p->red_host;
+  QW_CHECK_CUDA(cudaMemcpyAsync(host_dst, p->red_result, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return QW_OK;
+}
+
+// *out from the six reduced sums r (norm, three first moments, the two weight sums).
+static void obs_fill(const qw_plan_s* p, const double* r, bool kspace, qw_obs* out) {
   out->norm = r[0];
   for (int j = 0; j < 3; ++j) out->x_mean[j] = (j < p->g.dim && r[0] > 0) ? r[1 + j] / r[0] : 0.0;
   if (kspace && r[4] > 0) {
@@ -410,7 +416,112 @@ qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) 
     out->w_particle = NAN;
     out->w_antiparticle = NAN;
   }
+}
+
+qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) {
+  if (!p || !psi || !out) {
+    set_error("qw_observables: null argument");
+    return QW_EINVAL;
+  }
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bool kspace = false;
+  st = obs_enqueue(p, psi, s, p->red_host, &kspace);
+  if (st != QW_OK) return st;
+  st = check_flags(p, s);  // waits for the stream
+  if (st != QW_OK) return st;
+  obs_fill(p, p->red_host, kspace, out);
   return QW_OK;
+}
+
+// Two device fields, a non-blocking copy stream and its events for qw_run_host.
+static qw_status host_run_setup(qw_plan_s* p) {
+  if (p->copy_stream) return QW_OK;
+  const size_t bytes = (size_t)p->g.elems * p->elem_bytes;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    if (!p->hbuf[b]) e = cudaMalloc(&p->hbuf[b], bytes);
+    if (e == cudaSuccess && !p->ev_copied[b]) e = cudaEventCreateWithFlags(&p->ev_copied[b], cudaEventDisableTiming);
+    if (e == cudaSuccess && !p->ev_freed[b]) e = cudaEventCreateWithFlags(&p->ev_freed[b], cudaEventDisableTiming);
+    if (e == cudaSuccess && !p->ev_stepped[b])
+      e = cudaEventCreateWithFlags(&p->ev_stepped[b], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess && !p->hstage) e = cudaMallocHost(&p->hstage, sizeof(double) * 16);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    const qw_status st = (e == cudaErrorMemoryAllocation) ? QW_ENOMEM : QW_ECUDA;
+    set_error("qw_run_host: device buffers / copy stream: %s", cudaGetErrorString(e));
+    p->copy_stream = nullptr;
+    return st;
+  }
+  return QW_OK;
+}
+
+qw_status qw_run_host(qw_plan p, const void* const* psi_host, void* const* psi_out_host, int count, int64_t nsteps,
+                      qw_obs* out, void* stream) {
+  if (!p || count < 0 || nsteps < 0 || (count > 0 && (!psi_host || !out))) {
+    set_error("qw_run_host: null plan/array, count < 0 or nsteps < 0");
+    return QW_EINVAL;
+  }
+  for (int j = 0; j < count; ++j)
+    if (!psi_host[j] || (psi_out_host && !psi_out_host[j])) {
+      set_error("qw_run_host: null field pointer at index %d", j);
+      return QW_EINVAL;
+    }
+  if (count == 0) return QW_OK;
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  st = host_run_setup(p);
+  if (st != QW_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream), cs = p->copy_stream;
+  const size_t bytes = (size_t)p->g.elems * p->elem_bytes;
+  // field j lives in hbuf[j % 2]; on the copy stream: in(0), in(1), out(0), in(2), out(1), ...
+  // in(j + 2) waits for field j's observables (ev_freed) and follows out(j) in stream order.
+  // Field j's sums go to the pinned stage j % 2; the host reads them only after field
+  // j + 1's step is enqueued, so the device never waits for the host between fields.
+  QW_CHECK_CUDA(cudaMemcpyAsync(p->hbuf[0], psi_host[0], bytes, cudaMemcpyHostToDevice, cs));
+  QW_CHECK_CUDA(cudaEventRecord(p->ev_copied[0], cs));
+  bool kspace = false;
+  int done = 0;  // fields whose observables are on the host
+  for (int j = 0; j < count && st == QW_OK; ++j) {
+    const int b = j & 1;
+    if (j + 1 < count) {
+      const int nb = b ^ 1;
+      if (j >= 1) QW_CHECK_CUDA(cudaStreamWaitEvent(cs, p->ev_freed[nb], 0));
+      QW_CHECK_CUDA(cudaMemcpyAsync(p->hbuf[nb], psi_host[j + 1], bytes, cudaMemcpyHostToDevice, cs));
+      QW_CHECK_CUDA(cudaEventRecord(p->ev_copied[nb], cs));
+    }
+    QW_CHECK_CUDA(cudaStreamWaitEvent(s, p->ev_copied[b], 0));
+    st = qw_step(p, p->hbuf[b], nsteps, stream);
+    if (st != QW_OK) break;
+    if (psi_out_host) {
+      QW_CHECK_CUDA(cudaEventRecord(p->ev_stepped[b], s));
+      QW_CHECK_CUDA(cudaStreamWaitEvent(cs, p->ev_stepped[b], 0));
+      QW_CHECK_CUDA(cudaMemcpyAsync(psi_out_host[j], p->hbuf[b], bytes, cudaMemcpyDeviceToHost, cs));
+    }
+    st = obs_enqueue(p, p->hbuf[b], s, p->hstage + 8 * b, &kspace);
+    if (st != QW_OK) break;
+    QW_CHECK_CUDA(cudaEventRecord(p->ev_freed[b], s));
+    if (j >= 1) {  // the previous field's sums
+      const cudaError_t e = cudaEventSynchronize(p->ev_freed[b ^ 1]);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "qw_run_host: observables");
+        break;
+      }
+      obs_fill(p, p->hstage + 8 * (b ^ 1), kspace, &out[j - 1]);
+      done = j;
+    }
+  }
+  // the last field's sums, the device error word, and every copy (the last read-back
+  // included) before the host buffers are handed back
+  const qw_status sf = check_flags(p, s);
+  if (st == QW_OK) st = sf;
+  if (st == QW_OK && done == count - 1) obs_fill(p, p->hstage + 8 * ((count - 1) & 1), kspace, &out[count - 1]);
+  const cudaError_t e = cudaStreamSynchronize(cs);
+  if (st == QW_OK && e != cudaSuccess) return cuda_fail(e, "qw_run_host: copy stream");
+  return st;
 }
 
 }  // extern "C"

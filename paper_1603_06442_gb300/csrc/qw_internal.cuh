@@ -186,4 +186,10 @@ struct qw_plan_s {
   double* red_partials; // 4 * kObsBlocks doubles
   double* red_result;   // 4 doubles (device)
   double* red_host;     // 4 doubles (pinned host)
+  // host-field runs (qw_run_host): two device fields, a copy stream and its events,
+  // allocated by the first call
+  void* hbuf[2];
+  cudaStream_t copy_stream;
+  cudaEvent_t ev_copied[2], ev_freed[2], ev_stepped[2];
+  double* hstage;  // 2 x 8 doubles (pinned): observables of the two fields in flight
 };

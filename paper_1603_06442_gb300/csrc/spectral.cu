@@ -151,13 +151,29 @@ __global__ void __launch_bounds__(256) weights_kernel(int dim, AxesDev a, int64_
   }
 }
 
-__global__ void fold2_kernel(const double* __restrict__ partials, int nblk, double* __restrict__ result) {
-  double acc[2] = {0.0, 0.0};
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-    acc[0] += partials[2 * b];
-    acc[1] += partials[2 * b + 1];
+// Sum of nblk (a, b) partial pairs in a fixed order: 1024 threads, four independent
+// accumulators per thread (the partial count reaches 10^5 for the x-pass weights).
+constexpr int kFoldThreads = 1024;
+__global__ void __launch_bounds__(kFoldThreads) fold2_kernel(const double* __restrict__ partials, int nblk,
+                                                              double* __restrict__ result) {
+  const double2* p = reinterpret_cast<const double2*>(partials);
+  double a0[4] = {0.0, 0.0, 0.0, 0.0}, a1[4] = {0.0, 0.0, 0.0, 0.0};
+  int b = threadIdx.x;
+  for (; b + 3 * kFoldThreads < nblk; b += 4 * kFoldThreads) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const double2 v = p[b + u * kFoldThreads];
+      a0[u] += v.x;
+      a1[u] += v.y;
+    }
   }
-  block_sum<2, 256>(acc);
+  for (; b < nblk; b += kFoldThreads) {
+    const double2 v = p[b];
+    a0[0] += v.x;
+    a1[0] += v.y;
+  }
+  double acc[2] = {(a0[0] + a0[1]) + (a0[2] + a0[3]), (a1[0] + a1[1]) + (a1[2] + a1[3])};
+  block_sum<2, kFoldThreads>(acc);
   if (threadIdx.x == 0) {
     result[0] = acc[0];
     result[1] = acc[1];
@@ -249,7 +265,7 @@ qw_status launch_weights_fused_x(const Geometry& g, const SpecAxes& ax, const Ff
       return QW_EINVAL;
   }
   if (s2 != QW_OK) return s2;
-  fold2_kernel<<<1, 256, 0, st>>>(partials, (int)fused_x_grid(g), result);
+  fold2_kernel<<<1, kFoldThreads, 0, st>>>(partials, (int)fused_x_grid(g), result);
   QW_CHECK_LAUNCH("x-pass weights fold launch");
   return QW_OK;
 }
@@ -265,7 +281,7 @@ qw_status launch_particle_weights(const Geometry& g, const SpecAxes& ax, qw_dtyp
     weights_kernel<double><<<nblk, 256, 0, st>>>(g.dim, to_dev(ax), count, make_mass(n, m),
                                                  static_cast<const double2*>(psi_hat), partials);
   QW_CHECK_LAUNCH("weights launch");
-  fold2_kernel<<<1, 256, 0, st>>>(partials, nblk, result);
+  fold2_kernel<<<1, kFoldThreads, 0, st>>>(partials, nblk, result);
   QW_CHECK_LAUNCH("fold launch");
   return QW_OK;
 }
