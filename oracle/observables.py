@@ -5,6 +5,10 @@
                    (Sec. 5.2, X = sum_x x |x><x| (x) I), coordinates in the
                    fixed window [0, N) of the periodic box (lattice coordinates
                    (a, b) in 2D, physical coordinates in 3D).
+* projections:     the probability density sum_s |psi_s(x)|^2 summed over the
+                   axes that are not kept (the projections of a localised
+                   state's distribution onto axes and planes, Sec. 5.3), on the
+                   same window and coordinates as the mean position.
 * particle weight: the weight of the positive-frequency part, i.e. of the
                    eigenspace of U_k with eigenvalue exp(-i omega_k) (Eq. eigen-D,
                    s = +).  U_k = cos(omega) I - i G_k with G_k Hermitian, so
@@ -18,7 +22,7 @@ import numpy as np
 from .walk import site_coordinates
 from .spectral import dft, symbol_grid
 
-__all__ = ["norm", "mean_position", "particle_weights", "projectors"]
+__all__ = ["norm", "mean_position", "projection", "particle_weights", "projectors"]
 
 
 def norm(psi):
@@ -33,6 +37,17 @@ def mean_position(dim, psi):
     dens = np.sum(np.abs(psi) ** 2, axis=0)
     tot = np.sum(dens)
     return [float(np.sum(c * dens) / tot) for c in site_coordinates(dim, N)]
+
+
+def projection(dim, psi, keep):
+    """Density summed over the axes not in ``keep`` (a set of axis numbers 0 = x,
+    1 = y, 2 = z, each < dim).  Returns an array indexed [x][y][z] over the kept
+    axes only, N per axis; on the BCC lattice the physical points that are not
+    sites hold 0."""
+    psi = np.asarray(psi)
+    dens = np.sum(np.abs(psi) ** 2, axis=0)
+    drop = tuple(a for a in range(dim) if a not in keep)
+    return np.sum(dens, axis=drop) if drop else dens
 
 
 def projectors(D):
