@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--N", type=int, default=None, help="override the box side (profiling runs)")
     ap.add_argument("--stencil", default=None, help="force a stencil variant (plain, vec, tma)")
-    ap.add_argument("--only", default=None, choices=["spectral", "batched", "served"],
+    ap.add_argument("--only", default=None, choices=["spectral", "batched", "served", "projection"],
                     help="run one secondary workload alone and print its JSON (profiling runs)")
     ap.add_argument("--requests", type=int, default=1000, help="served workload: number of requests")
     ap.add_argument("--walks", type=int, default=256, help="batched workload: number of walks")
@@ -365,6 +365,7 @@ def extra_measurements(qb, dev, stream):
                           "equiv_GBps_at_64B_per_site_step": 2 * plan.elems * 8 / (ms / 1e3) / 1e9}
     out["c64_stencil_variants"] = variants
     out["spectral"] = spectral_measurement(qb, dev, stream)
+    out["projection"] = projection_measurement(qb, dev, stream)
     out["batched"] = batched_measurement(qb, dev, stream)
     out["served"] = served_measurement(qb, dev, stream)
     return out
@@ -397,6 +398,39 @@ def spectral_measurement(qb, dev, stream):
                                          "effective_GBps_vs_4_field_passes": bytes_min / (ms / 1e3) / 1e9}
         plan.close()
     return spec
+
+
+def projection_measurement(qb, dev, stream):
+    """Probability projections of the bench field (complex64 BCC N=512): one read of the field
+    per call, so HBM-bound; GB/s against the measured copy peak."""
+    import torch
+    W = WORKLOAD
+    plan = qb.Plan(3, W["N"], W["mass"], "c64")
+    psi = torch.zeros(plan.elems, dtype=torch.complex64, device=dev)
+    psi[::5] = 1e-3
+    peak, kind = measured_peaks()
+    field_bytes = plan.elems * 8
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, keep in (("x", {0}), ("xy_plane", {0, 1}), ("yz_plane", {1, 2}), ("density", {0, 1, 2})):
+        out = plan.projection(psi, keep, stream)
+        torch.cuda.synchronize(dev)
+        reps = 10
+        s0.record(stream)
+        for _ in range(reps):
+            plan.projection(psi, keep, stream)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = s0.elapsed_time(s1) / reps
+        written = out.numel() * 8
+        gbps = (field_bytes + written) / (ms / 1e3) / 1e9
+        res[name] = {"ms": ms, "algorithmic_GBps": gbps, "frac_of_hbm": gbps / peak,
+                     "bytes": field_bytes + written}
+        del out
+    res["note"] = ("algorithmic bytes = one read of the field + the FP64 output; the output "
+                   "tensor is allocated by the binding per call; peak %s" % kind)
+    plan.close()
+    return res
 
 
 def fp64_plain_rates(qb, dev, stream):
@@ -546,6 +580,8 @@ def run_only(args, local):
         out = served_measurement(qb, dev, stream, n_req=args.requests)
     elif args.only == "batched":
         out = batched_measurement(qb, dev, stream, n_walks=args.walks)
+    elif args.only == "projection":
+        out = projection_measurement(qb, dev, stream)
     else:
         out = spectral_measurement(qb, dev, stream)
     print(json.dumps({"only": args.only, "config": {"workload": WORKLOAD["name"], "N": WORKLOAD["N"]},

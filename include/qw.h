@@ -163,6 +163,26 @@ qw_status qw_sync(qw_plan plan, void* stream);
  * Errors: QW_EINVAL, QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
 qw_status qw_observables(qw_plan plan, const void* psi_dev, qw_obs* out, void* stream);
 
+/* Probability projections (Sec. 5.3: the distribution of a localised state
+ * projected onto axes and planes).  The density rho(x) = sum_s |psi_s(x)|^2 of
+ * psi_dev, summed over the axes NOT named in `keep` (bit 0 = x, bit 1 = y,
+ * bit 2 = z; only axes below dim; at least one), on the physical grid of the
+ * box with the coordinates of qw_observables' mean position: lattice
+ * coordinates (a, b) in 2D, physical BCC coordinates 2 (x, y, z) + c (1, 1, 1)
+ * in 3D, each in [0, N).
+ * out_dev: caller-owned DEVICE array of qw_projection_elems(plan, keep) =
+ * N^(number of kept axes) doubles, indexed with x fastest, then y, then z among
+ * the kept axes.  On the BCC lattice, kept-coordinate tuples that are not sites
+ * (mixed parity, two or more kept axes) hold 0.  keep = all axes gives the
+ * density itself.  Sums are FP64 in a fixed order (site densities in the
+ * field's precision): the result is deterministic.  Asynchronous on `stream`;
+ * the first call needing chunk partials allocates them in the plan (a few MB).
+ * Errors: QW_EINVAL (null argument, bad keep), QW_ENOMEM, QW_ECUDA. */
+qw_status qw_projection(qw_plan plan, const void* psi_dev, int keep, double* out_dev, void* stream);
+
+/* Number of doubles qw_projection writes for `keep`, or -1 for a bad plan/mask. */
+int64_t qw_projection_elems(qw_plan plan, int keep);
+
 /* End-to-end runs on HOST fields.  For j = 0 .. count-1: copy the field
  * psi_host[j] (host memory, device layout, qw_plan_field_elems elements;
  * page-locked memory copies fastest and overlaps) to the device, advance it by

@@ -93,6 +93,9 @@ _SIGS = {
     "qw_evolve_spectral": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "qw_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(qw_obs),
                                       ctypes.c_void_p]),
+    "qw_projection": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
+    "qw_projection_elems": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int]),
     "qw_run_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                    ctypes.c_int, ctypes.c_int64, ctypes.POINTER(qw_obs), ctypes.c_void_p]),
 }
@@ -275,6 +278,24 @@ def qw_observables(plan, psi, stream=None):
     return out.as_dict()
 
 
+def keep_mask(keep):
+    """Axis set (0 = x, 1 = y, 2 = z) or int mask -> int mask."""
+    if isinstance(keep, int):
+        return keep
+    m = 0
+    for a in keep:
+        m |= 1 << int(a)
+    return m
+
+
+def qw_projection_elems(plan, keep):
+    return int(load().qw_projection_elems(plan, keep_mask(keep)))
+
+
+def qw_projection(plan, psi, keep, out, stream=None):
+    _check(load().qw_projection(plan, _ptr(psi), keep_mask(keep), _ptr(out), _stream(stream)))
+
+
 def _host_ptr(x):
     """Address of a host buffer: a CPU torch tensor, a numpy array or an int."""
     if isinstance(x, int):
@@ -444,6 +465,20 @@ class Plan:
     def observables(self, psi, stream=None):
         self.check_field(psi)
         return qw_observables(self.handle, psi, stream)
+
+    def projection(self, psi, keep, stream=None):
+        """Density summed over the axes not in `keep` (axis set or mask): a CUDA float64
+        tensor shaped (N,) * kept axes, indexed [z][y][x] over the kept ones."""
+        import torch
+        self.check_field(psi)
+        mask = keep_mask(keep)
+        n = qw_projection_elems(self.handle, mask)
+        if n < 0:
+            raise ValueError("bad keep mask %r for dim %d" % (keep, self.dim))
+        kept = bin(mask).count("1")
+        out = torch.empty((self.N,) * kept, dtype=torch.float64, device=psi.device)
+        qw_projection(self.handle, psi, mask, out, stream)
+        return out
 
     def check_host_field(self, f):
         if hasattr(f, "is_cuda"):

@@ -201,6 +201,7 @@ qw_status qw_plan_destroy(qw_plan p) {
     if (p->ev_stepped[b]) cudaEventDestroy(p->ev_stepped[b]);
   }
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  if (p->proj_partials) cudaFree(p->proj_partials);
   if (p->hstage) cudaFreeHost(p->hstage);
   delete p;
   return QW_OK;
@@ -433,6 +434,33 @@ qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) 
   if (st != QW_OK) return st;
   obs_fill(p, p->red_host, kspace, out);
   return QW_OK;
+}
+
+qw_status qw_projection(qw_plan p, const void* psi, int keep, double* out, void* stream) {
+  if (!p || !psi || !out) {
+    set_error("qw_projection: null argument");
+    return QW_EINVAL;
+  }
+  if (keep <= 0 || keep >= (1 << p->g.dim)) {
+    set_error("qw_projection: keep mask %d must name 1..%d of the axes below dim %d", keep, p->g.dim, p->g.dim);
+    return QW_EINVAL;
+  }
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  const int64_t need = projection_partials(p->g, keep);
+  if (need > p->proj_cap) {
+    if (p->proj_partials) QW_CHECK_CUDA(cudaFree(p->proj_partials));
+    p->proj_partials = nullptr;
+    p->proj_cap = 0;
+    QW_CHECK_CUDA(cudaMalloc(&p->proj_partials, sizeof(double) * need));
+    p->proj_cap = need;
+  }
+  return launch_projection(p->g, p->dtype, psi, keep, out, p->proj_partials, static_cast<cudaStream_t>(stream));
+}
+
+int64_t qw_projection_elems(qw_plan p, int keep) {
+  if (!p || keep <= 0 || keep >= (1 << p->g.dim)) return -1;
+  return projection_outputs(p->g, keep);
 }
 
 // Two device fields, a non-blocking copy stream and its events for qw_run_host.

@@ -1,0 +1,242 @@
+// Probability projections (Sec. 5.3: the distribution of a localised state projected
+// onto axes and planes): rho(x) = sum_s |psi_s(x)|^2 summed over the axes that are not
+// kept, on the physical grid (lattice coordinates (a, b) in 2D, physical BCC
+// coordinates 2 m + c (1, 1, 1) in 3D), in FP64.
+//
+// A storage row is the x line of one (coset, z, y).  An output row is a (coset, kept z,
+// kept y); its reduced rows are the (z, y) that match it.  Two kernels:
+//   x kept    a thread owns one x of an output row and a chunk of its reduced rows
+//             (the threads of a warp read consecutive x);
+//   x summed  a warp owns an output row and a chunk of its reduced rows, lanes striding
+//             along x, then a warp sum.
+// With one chunk a kernel writes the physical output directly; otherwise it writes
+// partials [chunk][output] and proj_fold_kernel adds the chunks in order.  Site densities
+// are taken in the field's precision and summed in FP64 in a fixed order: deterministic.
+#include <cuda_runtime.h>
+
+#include "qw_internal.cuh"
+
+namespace qw {
+namespace {
+
+struct ProjGeo {
+  int dim, s, ncos, N;
+  int nx, ny, nz;
+  int kx, ky, kz;        // kept axes
+  int oy, oz;            // output-row extents: ny or 1, nz or 1
+  int ry;                // reduced-row extent along y: 1 (kept) or ny
+  int chunks;
+  int64_t vol;
+  int64_t n_orows;       // ncos * oz * oy
+  int64_t rrows;         // reduced rows per output row
+  int64_t nout;          // storage outputs: n_orows * (kx ? nx : 1)
+};
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+__device__ __forceinline__ void decode_orow(const ProjGeo& p, int64_t orow, int& c, int& zk, int& yk) {
+  yk = (int)(orow % p.oy);
+  const int64_t t = orow / p.oy;
+  zk = (int)(t % p.oz);
+  c = (int)(t / p.oz);
+}
+
+// Physical output index of storage output (c, zk, yk, xk): x fastest, then y, then z
+// among the kept axes.
+__device__ __forceinline__ int64_t phys_index(const ProjGeo& p, int c, int zk, int yk, int xk) {
+  const int sc = p.dim == 3 ? 2 : 1, off = p.dim == 3 ? c : 0;
+  int64_t idx = 0, mul = 1;
+  if (p.kx) {
+    idx += (int64_t)(sc * xk + off);
+    mul = p.N;
+  }
+  if (p.ky) {
+    idx += (int64_t)(sc * yk + off) * mul;
+    mul *= p.N;
+  }
+  if (p.kz) idx += (int64_t)(sc * zk + off) * mul;
+  return idx;
+}
+
+template <typename R>
+__device__ __forceinline__ R density(const typename Cx<R>::T* __restrict__ q, int s, int64_t vol) {
+  R d = 0;
+  for (int j = 0; j < s; ++j) {
+    const typename Cx<R>::T v = q[(int64_t)j * vol];
+    d = fma(v.x, v.x, d);
+    d = fma(v.y, v.y, d);
+  }
+  return d;
+}
+
+// Walks the storage rows (c, z, y) of reduced rows r0, r0 + 1, ... of output row
+// (c, zk, yk) without a division per row.
+struct RowWalk {
+  int z, y;
+  __device__ RowWalk(const ProjGeo& p, int zk, int yk, int64_t r0) {
+    z = p.kz ? zk : (int)(r0 / p.ry);
+    y = p.ky ? yk : (int)(r0 % p.ry);
+  }
+  __device__ __forceinline__ int64_t offset(const ProjGeo& p, int c) const {
+    return (int64_t)c * p.s * p.vol + ((int64_t)z * p.ny + y) * p.nx;
+  }
+  __device__ __forceinline__ void next(const ProjGeo& p) {
+    if (!p.ky && ++y < p.ny) return;
+    y = p.ky ? y : 0;
+    ++z;  // z is not kept here: a kept z has one reduced row per y
+  }
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) proj_x_kernel(const typename Cx<R>::T* __restrict__ psi, ProjGeo p,
+                                                     double* __restrict__ out, double* __restrict__ partials) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= p.nout) return;
+  const int x = (int)(gid % p.nx);
+  const int64_t orow = gid / p.nx;
+  int c, zk, yk;
+  decode_orow(p, orow, c, zk, yk);
+  const int j = blockIdx.y;
+  const int64_t r0 = j * p.rrows / p.chunks, r1 = (j + 1) * p.rrows / p.chunks;
+  double acc = 0.0;
+  RowWalk w(p, zk, yk, r0);
+  int64_t r = r0;
+  // groups of four rows summed in the field's precision, then in FP64
+  for (; r + 4 <= r1; r += 4) {
+    R g = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      g += density<R>(psi + w.offset(p, c) + x, p.s, p.vol);
+      w.next(p);
+    }
+    acc += (double)g;
+  }
+  for (; r < r1; ++r) {
+    acc += (double)density<R>(psi + w.offset(p, c) + x, p.s, p.vol);
+    w.next(p);
+  }
+  if (p.chunks == 1)
+    out[phys_index(p, c, zk, yk, x)] = acc;
+  else
+    partials[(int64_t)j * p.nout + gid] = acc;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) proj_w_kernel(const typename Cx<R>::T* __restrict__ psi, ProjGeo p,
+                                                     double* __restrict__ out, double* __restrict__ partials) {
+  const int64_t orow = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (orow >= p.n_orows) return;  // whole warps leave together
+  int c, zk, yk;
+  decode_orow(p, orow, c, zk, yk);
+  const int j = blockIdx.y;
+  const int64_t r0 = j * p.rrows / p.chunks, r1 = (j + 1) * p.rrows / p.chunks;
+  double acc = 0.0;
+  RowWalk w(p, zk, yk, r0);
+  for (int64_t r = r0; r < r1; ++r) {
+    const typename Cx<R>::T* row = psi + w.offset(p, c);
+    R g = 0;
+    for (int x = lane; x < p.nx; x += 32) g += density<R>(row + x, p.s, p.vol);
+    acc += (double)g;
+    w.next(p);
+  }
+  acc = warp_sum_d(acc);
+  if (lane == 0) {
+    if (p.chunks == 1)
+      out[phys_index(p, c, zk, yk, 0)] = acc;
+    else
+      partials[(int64_t)j * p.n_orows + orow] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) proj_fold_kernel(const double* __restrict__ partials, ProjGeo p,
+                                                        double* __restrict__ out) {
+  const int64_t nout = p.kx ? p.nout : p.n_orows;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= nout) return;
+  double acc = 0.0;
+  for (int j = 0; j < p.chunks; ++j) acc += partials[(int64_t)j * nout + gid];
+  const int xk = p.kx ? (int)(gid % p.nx) : 0;
+  const int64_t orow = p.kx ? gid / p.nx : gid;
+  int c, zk, yk;
+  decode_orow(p, orow, c, zk, yk);
+  out[phys_index(p, c, zk, yk, xk)] = acc;
+}
+
+// Threads (x kept) and warps (x summed) a launch aims for: ~1700 threads per SM.
+constexpr int64_t kProjThreads = int64_t(1) << 18;
+constexpr int64_t kProjWarps = kProjThreads / 32;
+
+ProjGeo make_proj(const Geometry& g, int keep) {
+  ProjGeo p{};
+  p.dim = g.dim;
+  p.s = g.s;
+  p.ncos = g.ncoset;
+  p.N = (int)g.N;
+  p.nx = (int)g.nx;
+  p.ny = (int)g.ny;
+  p.nz = (int)g.nz;
+  p.kx = keep & 1;
+  p.ky = (keep >> 1) & 1;
+  p.kz = (keep >> 2) & 1;
+  p.oy = p.ky ? p.ny : 1;
+  p.oz = p.kz ? p.nz : 1;
+  p.ry = p.ky ? 1 : p.ny;
+  p.vol = g.vol;
+  p.n_orows = (int64_t)p.ncos * p.oz * p.oy;
+  p.rrows = (int64_t)(p.kz ? 1 : p.nz) * p.ry;
+  p.nout = p.n_orows * (p.kx ? p.nx : 1);
+  const int64_t units = p.kx ? p.nout : p.n_orows, want = p.kx ? kProjThreads : kProjWarps;
+  int64_t k = (want + units - 1) / units;
+  if (k > p.rrows) k = p.rrows;
+  if (k > 65535) k = 65535;
+  p.chunks = (int)(k < 1 ? 1 : k);
+  return p;
+}
+
+}  // namespace
+
+int64_t projection_partials(const Geometry& g, int keep) {
+  const ProjGeo p = make_proj(g, keep);
+  return p.chunks == 1 ? 0 : (int64_t)p.chunks * (p.kx ? p.nout : p.n_orows);
+}
+
+int64_t projection_outputs(const Geometry& g, int keep) {
+  int64_t n = 1;
+  for (int a = 0; a < 3; ++a)
+    if ((keep >> a) & 1) n *= g.N;
+  return n;
+}
+
+qw_status launch_projection(const Geometry& g, qw_dtype dt, const void* psi, int keep, double* out,
+                            double* partials, cudaStream_t st) {
+  const ProjGeo p = make_proj(g, keep);
+  const int kept = p.kx + p.ky + p.kz;
+  // BCC: physical points of mixed coordinate parity are not sites (two or more kept axes)
+  if (g.dim == 3 && kept >= 2)
+    QW_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * projection_outputs(g, keep), st));
+  const int64_t threads = p.kx ? p.nout : p.n_orows * 32;
+  const dim3 grid((unsigned)((threads + 255) / 256), (unsigned)p.chunks);
+  if (p.kx) {
+    if (dt == QW_C64)
+      proj_x_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
+    else
+      proj_x_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double2*>(psi), p, out, partials);
+  } else {
+    if (dt == QW_C64)
+      proj_w_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
+    else
+      proj_w_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double2*>(psi), p, out, partials);
+  }
+  QW_CHECK_LAUNCH("projection launch");
+  if (p.chunks > 1) {
+    const int64_t n = p.kx ? p.nout : p.n_orows;
+    proj_fold_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partials, p, out);
+    QW_CHECK_LAUNCH("projection fold launch");
+  }
+  return QW_OK;
+}
+
+}  // namespace qw

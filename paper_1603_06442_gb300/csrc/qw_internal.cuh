@@ -156,6 +156,14 @@ qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtyp
 qw_status launch_packet(const Geometry& g, qw_dtype dt, const double* x0, double sigma, const double* k0,
                         const double* chi, void* psi, cudaStream_t st);
 // (sum |psi^|^2, sum psi^dag G/sin(omega) psi^) over the zone into result[0..1].
+// ---- probability projections (projection.cu) ---------------------------------
+// keep: bit 0 x, bit 1 y, bit 2 z.  projection_partials: doubles of chunk partials the
+// launch needs (0: none); projection_outputs: N^(kept axes).
+int64_t projection_partials(const Geometry& g, int keep);
+int64_t projection_outputs(const Geometry& g, int keep);
+qw_status launch_projection(const Geometry& g, qw_dtype dt, const void* psi, int keep, double* out,
+                            double* partials, cudaStream_t st);
+
 qw_status launch_particle_weights(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
                                   const void* psi_hat, double* partials, double* result, cudaStream_t st);
 
@@ -192,4 +200,7 @@ struct qw_plan_s {
   cudaStream_t copy_stream;
   cudaEvent_t ev_copied[2], ev_freed[2], ev_stepped[2];
   double* hstage;  // 2 x 8 doubles (pinned): observables of the two fields in flight
+  // probability projections: chunk partials, grown on demand
+  double* proj_partials;
+  int64_t proj_cap;
 };
