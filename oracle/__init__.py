@@ -14,8 +14,11 @@ Plain, slow, obviously correct numpy in complex128:
                      symbol (Eq. walk-K), the update rule (Eq. upd-rule), layouts.
 * ``spectral``    -- naive DFT, and U^t psi through the DFT with a per-k matrix
                      power (Sec. 4; the plain definition, no closed form).
-* ``observables`` -- norm, mean position (Sec. 5.2, operator X), particle and
+* ``observables`` -- norm, mean position (Sec. 5.2, operator X), position
+                     covariance, probability projections (Sec. 5.3), particle and
                      antiparticle weights (spectral projector of U_k).
+* ``kinematics``  -- drift v = grad omega and diffusion D = grad grad omega of
+                     particle states (Sec. 5.1, second-order dispersive equation).
 * ``states``      -- the paper's eigenvector formulas (Eqs. evecs-W, evecs-D) and
                      particle-state packets (Definition 1, Eq. state-zitter).
 
@@ -24,4 +27,4 @@ facts the paper and the mathematics fix (unitarity, dense spectra, special
 cases, closed forms, small-k limit, Zitterbewegung).  No function is unpinned.
 """
 
-from . import walk, spectral, observables, states  # noqa: F401
+from . import walk, spectral, observables, states, kinematics  # noqa: F401

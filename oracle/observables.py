@@ -5,6 +5,8 @@
                    (Sec. 5.2, X = sum_x x |x><x| (x) I), coordinates in the
                    fixed window [0, N) of the periodic box (lattice coordinates
                    (a, b) in 2D, physical coordinates in 3D).
+* second moments:  the covariance of the position over the density,
+                   sum (x_i - <x_i>)(x_j - <x_j>) |psi(x)|^2 / norm, same window.
 * projections:     the probability density sum_s |psi_s(x)|^2 summed over the
                    axes that are not kept (the projections of a localised
                    state's distribution onto axes and planes, Sec. 5.3), on the
@@ -22,7 +24,7 @@ import numpy as np
 from .walk import site_coordinates
 from .spectral import dft, symbol_grid
 
-__all__ = ["norm", "mean_position", "projection", "particle_weights", "projectors"]
+__all__ = ["norm", "mean_position", "position_covariance", "projection", "particle_weights", "projectors"]
 
 
 def norm(psi):
@@ -37,6 +39,21 @@ def mean_position(dim, psi):
     dens = np.sum(np.abs(psi) ** 2, axis=0)
     tot = np.sum(dens)
     return [float(np.sum(c * dens) / tot) for c in site_coordinates(dim, N)]
+
+
+def position_covariance(dim, psi):
+    """dim x dim covariance of the position under the normalised density."""
+    psi = np.asarray(psi)
+    N = psi.shape[1]
+    dens = np.sum(np.abs(psi) ** 2, axis=0)
+    tot = np.sum(dens)
+    xs = site_coordinates(dim, N)
+    mu = [np.sum(c * dens) / tot for c in xs]
+    cov = np.zeros((dim, dim))
+    for i in range(dim):
+        for j in range(dim):
+            cov[i, j] = np.sum((xs[i] - mu[i]) * (xs[j] - mu[j]) * dens) / tot
+    return cov
 
 
 def projection(dim, psi, keep):
