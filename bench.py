@@ -427,6 +427,18 @@ def projection_measurement(qb, dev, stream):
         res[name] = {"ms": ms, "algorithmic_GBps": gbps, "frac_of_hbm": gbps / peak,
                      "bytes": field_bytes + written}
         del out
+    # position moments up to second order (one read of the field; blocking call: the events
+    # bracket the kernels, the fold and the 80-byte read-back)
+    plan.position_moments(psi, stream)
+    reps = 10
+    s0.record(stream)
+    for _ in range(reps):
+        plan.position_moments(psi, stream)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = s0.elapsed_time(s1) / reps
+    res["position_moments"] = {"ms": ms, "algorithmic_GBps": field_bytes / (ms / 1e3) / 1e9,
+                               "frac_of_hbm": field_bytes / (ms / 1e3) / 1e9 / peak, "bytes": field_bytes}
     res["note"] = ("algorithmic bytes = one read of the field + the FP64 output; the output "
                    "tensor is allocated by the binding per call; peak %s" % kind)
     plan.close()

@@ -163,6 +163,16 @@ qw_status qw_sync(qw_plan plan, void* stream);
  * Errors: QW_EINVAL, QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
 qw_status qw_observables(qw_plan plan, const void* psi_dev, qw_obs* out, void* stream);
 
+/* Position moments up to second order (the mean and covariance that the drift
+ * v = grad omega and diffusion D = grad grad omega of Sec. 5.1's particle states
+ * move and spread).  out (HOST, 10 doubles, caller-owned): norm, the mean
+ * position (x, y, z) and the central second moments (xx, yy, zz, xy, xz, yz)
+ * of the normalised density, on the window and coordinates of qw_observables'
+ * mean position; entries of axes at or above dim are 0.  Sums in FP64 (site
+ * densities in the field's precision).  Blocks the host until `stream` is done.
+ * Errors: QW_EINVAL (null argument), QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
+qw_status qw_position_moments(qw_plan plan, const void* psi_dev, double* out, void* stream);
+
 /* Probability projections (Sec. 5.3: the distribution of a localised state
  * projected onto axes and planes).  The density rho(x) = sum_s |psi_s(x)|^2 of
  * psi_dev, summed over the axes NOT named in `keep` (bit 0 = x, bit 1 = y,

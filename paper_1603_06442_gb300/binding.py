@@ -93,6 +93,8 @@ _SIGS = {
     "qw_evolve_spectral": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "qw_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(qw_obs),
                                       ctypes.c_void_p]),
+    "qw_position_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_void_p]),
     "qw_projection": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                      ctypes.c_void_p]),
     "qw_projection_elems": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int]),
@@ -276,6 +278,15 @@ def qw_observables(plan, psi, stream=None):
     out = qw_obs()
     _check(load().qw_observables(plan, _ptr(psi), ctypes.byref(out), _stream(stream)))
     return out.as_dict()
+
+
+def qw_position_moments(plan, psi, stream=None):
+    """{'norm', 'mean' (3), 'cov' (3x3 nested lists)} of the density."""
+    out = (ctypes.c_double * 10)()
+    _check(load().qw_position_moments(plan, _ptr(psi), out, _stream(stream)))
+    c = list(out)
+    xx, yy, zz, xy, xz, yz = c[4:10]
+    return {"norm": c[0], "mean": c[1:4], "cov": [[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]]}
 
 
 def keep_mask(keep):
@@ -465,6 +476,10 @@ class Plan:
     def observables(self, psi, stream=None):
         self.check_field(psi)
         return qw_observables(self.handle, psi, stream)
+
+    def position_moments(self, psi, stream=None):
+        self.check_field(psi)
+        return qw_position_moments(self.handle, psi, stream)
 
     def projection(self, psi, keep, stream=None):
         """Density summed over the axes not in `keep` (axis set or mask): a CUDA float64

@@ -143,9 +143,9 @@ qw_status qw_plan_create(int dim, int64_t N, double mass, qw_dtype dtype, qw_pla
   qw_status st = QW_OK;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaMalloc(&p->scratch, (size_t)g.elems * p->elem_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&p->red_partials, sizeof(double) * 4 * kObsBlocks);
-  if (e == cudaSuccess) e = cudaMalloc(&p->red_result, sizeof(double) * 8);
-  if (e == cudaSuccess) e = cudaMallocHost(&p->red_host, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&p->red_partials, sizeof(double) * 10 * kObsBlocks);
+  if (e == cudaSuccess) e = cudaMalloc(&p->red_result, sizeof(double) * 16);
+  if (e == cudaSuccess) e = cudaMallocHost(&p->red_host, sizeof(double) * 16);
   if (e == cudaSuccess) e = cudaMalloc(&p->dev_flags, sizeof(int) * 2);
   if (e == cudaSuccess) e = cudaMemset(p->dev_flags, 0, sizeof(int) * 2);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -433,6 +433,32 @@ qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) 
   st = check_flags(p, s);  // waits for the stream
   if (st != QW_OK) return st;
   obs_fill(p, p->red_host, kspace, out);
+  return QW_OK;
+}
+
+qw_status qw_position_moments(qw_plan p, const void* psi, double* out, void* stream) {
+  if (!p || !psi || !out) {
+    set_error("qw_position_moments: null argument");
+    return QW_EINVAL;
+  }
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = launch_position_moments2(p->g, p->dtype, psi, p->red_partials, p->red_result, s);
+  if (st != QW_OK) return st;
+  QW_CHECK_CUDA(cudaMemcpyAsync(p->red_host, p->red_result, 10 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  st = check_flags(p, s);  // waits for the stream
+  if (st != QW_OK) return st;
+  const double* r = p->red_host;
+  const double n = r[0];
+  out[0] = n;
+  double mu[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < 3; ++i) mu[i] = (i < p->g.dim && n > 0) ? r[1 + i] / n : 0.0;
+  for (int i = 0; i < 3; ++i) out[1 + i] = mu[i];
+  // central moments E[X_i X_j] - mu_i mu_j, axes at or above dim are 0
+  const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+  for (int q = 0; q < 6; ++q)
+    out[4 + q] = (ii[q] < p->g.dim && jj[q] < p->g.dim && n > 0) ? r[4 + q] / n - mu[ii[q]] * mu[jj[q]] : 0.0;
   return QW_OK;
 }
 

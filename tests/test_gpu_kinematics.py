@@ -1,0 +1,130 @@
+"""GPU parity of qw_position_moments (mean and covariance of the position) against the oracle,
+and the particle-state kinematics of Sec. 5.1 on GPU-evolved packets: a positive-frequency
+packet drifts by t <v>_{|g|^2} (v = grad omega) and, in 1D, spreads by t^2 Var_{|g|^2}(v).
+
+Tolerances: norm and mean as qw_observables (1e-12 / 1e-6 relative, mean scaled by N);
+covariance absolute 1e-12 N^2 (complex128) / 1e-6 N^2 (complex64: FP32 site densities);
+kinematics: displacement 1e-6 t sites (complex128) / 2e-4 t (complex64), 1D spread 1e-6 / 1e-3
+relative.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1603_06442_gb300 import inputs
+from oracle import walk, observables, kinematics, spectral, states
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def qb(qwlib):
+    from paper_1603_06442_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return binding
+
+
+def to_dev(a, dtype):
+    npdt = np.complex64 if dtype == "c64" else np.complex128
+    return torch.from_numpy(np.ascontiguousarray(a.astype(npdt))).cuda()
+
+
+@pytest.mark.parametrize("dim,N", [(1, 64), (1, 1000), (2, 24), (2, 33), (3, 16), (3, 42), (3, 128)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_position_moments_match_oracle(qb, dim, N, dtype):
+    a = inputs.gaussian_packet(dim, N, [N / 3] * dim, N / 9, [0.2] * dim,
+                               [1, 0] if dim == 1 else [0.6, 0.8j, 0, 0])
+    a = a + 0.2 * inputs.random_field(dim, N, 6)
+    npdt = np.complex64 if dtype == "c64" else np.complex128
+    psi = walk.from_device(dim, N, a.astype(npdt))
+    plan = qb.Plan(dim, N, 0.1, dtype)
+    x = to_dev(a, dtype)
+    got = plan.position_moments(x)
+    obs = plan.observables(x)
+    plan.close()
+    rtol = 1e-12 if dtype == "c128" else 1e-6
+    ctol = (1e-12 if dtype == "c128" else 1e-6) * N * N
+    nrm = observables.norm(psi)
+    assert abs(got["norm"] - nrm) <= rtol * nrm
+    mu = observables.mean_position(dim, psi)
+    cov = observables.position_covariance(dim, psi)
+    for i in range(3):
+        if i < dim:
+            assert abs(got["mean"][i] - mu[i]) <= rtol * N
+            assert abs(got["mean"][i] - obs["x_mean"][i]) <= rtol * N
+        else:
+            assert got["mean"][i] == 0.0
+        for j in range(3):
+            want = cov[i, j] if (i < dim and j < dim) else 0.0
+            assert abs(got["cov"][i][j] - want) <= ctol, (i, j, got["cov"][i][j], want)
+
+
+def mean_velocity(dim, m, N, k0, sigma):
+    k = spectral.k_grid(dim, N).reshape(-1, dim)
+    dk = states.wrapped_dk(dim, k, np.asarray(k0))
+    g2 = np.exp(-2 * sigma * sigma * np.sum(dk * dk, axis=-1))
+    sel = g2 > 1e-30
+    w = g2[sel] / g2[sel].sum()
+    v = np.array([kinematics.drift(dim, m, kk) for kk in k[sel]])
+    vbar = (w[:, None] * v).sum(0)
+    cov_v = np.einsum("i,ij,ik->jk", w, v - vbar, v - vbar)
+    return vbar, cov_v
+
+
+DRIFT = [
+    (1, 1024, 0.2, [0.4], 12.0, 150),
+    (2, 128, 0.3, [0.5, 0.1], 8.0, 40),
+    (3, 96, 0.3, [0.3, 0.2, -0.1], 7.0, 12),
+]
+
+
+@pytest.mark.parametrize("dim,N,m,k0,sigma,t", DRIFT)
+@pytest.mark.parametrize("dtype,path", [("c128", "spectral"), ("c64", "spectral"), ("c64", "stencil")])
+def test_positive_packet_drift_on_gpu(qb, dim, N, m, k0, sigma, t, dtype, path):
+    key = (1, 0) if dim == 1 else (1, 1)
+    psi0 = states.packet(dim, m, N, k0, sigma, [N / 2] * dim, {key: 1.0})
+    vbar, _ = mean_velocity(dim, m, N, k0, sigma)
+    plan = qb.Plan(dim, N, m, dtype)
+    x = to_dev(walk.to_device(dim, N, psi0), dtype)
+    m0 = plan.position_moments(x)
+    if path == "spectral":
+        plan.evolve_spectral(x, t)
+    else:
+        plan.step(x, t)
+    plan.sync()
+    m1 = plan.position_moments(x)
+    plan.close()
+    disp = np.array(m1["mean"][:dim]) - np.array(m0["mean"][:dim])
+    tol = (1e-6 if dtype == "c128" else 2e-4) * t
+    np.testing.assert_allclose(disp, t * vbar, atol=tol)
+    # and the drift at k0 describes it to the packet's spread
+    assert np.max(np.abs(disp / t - kinematics.drift(dim, m, k0))) < 0.05
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_positive_packet_spread_1d_on_gpu(qb, dtype):
+    dim, N, m, k0, sigma = 1, 2048, 0.2, [0.4], 12.0
+    psi0 = states.packet(dim, m, N, k0, sigma, [N / 2], {(1, 0): 1.0})
+    _, cov_v = mean_velocity(dim, m, N, k0, sigma)
+    plan = qb.Plan(dim, N, m, dtype)
+    x = to_dev(walk.to_device(dim, N, psi0), dtype)
+    c0 = plan.position_moments(x)["cov"][0][0]
+    rtol = 1e-6 if dtype == "c128" else 1e-3
+    t_done = 0
+    for t in (100, 400):
+        plan.evolve_spectral(x, t - t_done)
+        t_done = t
+        ct = plan.position_moments(x)["cov"][0][0]
+        want = t * t * cov_v[0, 0]
+        assert abs((ct - c0) - want) <= rtol * want, (t, ct - c0, want)
+    plan.close()
+
+
+def test_position_moments_rejects_null(qb):
+    plan = qb.Plan(1, 8, 0.1, "c64")
+    with pytest.raises(qb.QwError):
+        qb.qw_position_moments(plan.handle, 0)
+    plan.close()
