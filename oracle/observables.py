@@ -7,6 +7,12 @@
                    (a, b) in 2D, physical coordinates in 3D).
 * second moments:  the covariance of the position over the density,
                    sum (x_i - <x_i>)(x_j - <x_j>) |psi(x)|^2 / norm, same window.
+* Foldy-Wouthuysen field (Remark on the Newton-Wigner position): the
+                   coefficients phi_r(k) = <u_r(k)|psi^(k)> of the state on the
+                   paper's eigenvectors (Eq. evecs-D; 1D: the 2x2 walk's),
+                   r = (s, p) in the order (+,+), (+,-), (-,+), (-,-) (1D: +, -),
+                   taken back to position space; its mean position is the
+                   Newton-Wigner position <X_NW> = <W^-1 psi| X |W^-1 psi>.
 * projections:     the probability density sum_s |psi_s(x)|^2 summed over the
                    axes that are not kept (the projections of a localised
                    state's distribution onto axes and planes, Sec. 5.3), on the
@@ -22,9 +28,10 @@
 import numpy as np
 
 from .walk import site_coordinates
-from .spectral import dft, symbol_grid
+from .spectral import dft, idft, symbol_grid, k_grid
+from .states import dirac_eigenvectors
 
-__all__ = ["norm", "mean_position", "position_covariance", "projection", "particle_weights", "projectors"]
+__all__ = ["norm", "mean_position", "position_covariance", "fw_field", "FW_ORDER", "projection", "particle_weights", "projectors"]
 
 
 def norm(psi):
@@ -54,6 +61,21 @@ def position_covariance(dim, psi):
         for j in range(dim):
             cov[i, j] = np.sum((xs[i] - mu[i]) * (xs[j] - mu[j]) * dens) / tot
     return cov
+
+
+FW_ORDER = {1: [(1, 0), (-1, 0)], 2: [(1, 1), (1, -1), (-1, 1), (-1, -1)],
+            3: [(1, 1), (1, -1), (-1, 1), (-1, -1)]}
+
+
+def fw_field(dim, m, psi):
+    """The state in the eigenbasis of D_k per wave vector, back in position space
+    (oracle layout, components in FW_ORDER)."""
+    psi = np.asarray(psi, dtype=complex)
+    N = psi.shape[1]
+    ph = dft(psi, dim)
+    ev = dirac_eigenvectors(dim, m, k_grid(dim, N))
+    out = np.stack([np.einsum("...i,i...->...", np.conj(ev[key]), ph) for key in FW_ORDER[dim]])
+    return idft(out, dim)
 
 
 def projection(dim, psi, keep):
