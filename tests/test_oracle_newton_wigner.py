@@ -57,7 +57,7 @@ def drift_means(dim, m, N, k0, sigma):
 
 @pytest.mark.parametrize("dim,N,m,k0,sigma,ts,tol", [
     (1, 1024, 0.15, [0.01 * np.pi], 20.0, (5, 17, 40), 1e-9),
-    (3, 64, 0.3, [0.0, 0.01 * np.pi, 0.0], 4.0, (3, 7, 11), 1e-7),   # seam and k-grid: 3e-8
+    (3, 96, 0.3, [0.0, 0.01 * np.pi, 0.0], 4.0, (3, 7, 11), 1e-8),
 ])
 def test_newton_wigner_position_does_not_jitter(dim, N, m, k0, sigma, ts, tol):
     cp, cm = np.sqrt(0.7), np.sqrt(0.3)
