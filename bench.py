@@ -439,6 +439,18 @@ def projection_measurement(qb, dev, stream):
     ms = s0.elapsed_time(s1) / reps
     res["position_moments"] = {"ms": ms, "algorithmic_GBps": field_bytes / (ms / 1e3) / 1e9,
                                "frac_of_hbm": field_bytes / (ms / 1e3) / 1e9 / peak, "bytes": field_bytes}
+    # Foldy-Wouthuysen field (Newton-Wigner position): copy, forward FFT, per-k eigenvector
+    # projection, inverse FFT; algorithmic bytes 4 field passes like the spectral evolution
+    f = torch.empty_like(psi)
+    plan.fw_transform(psi, out=f, stream=stream)
+    s0.record(stream)
+    for _ in range(reps):
+        plan.fw_transform(psi, out=f, stream=stream)
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = s0.elapsed_time(s1) / reps
+    res["fw_transform"] = {"ms": ms, "effective_GBps_vs_4_field_passes": 4 * field_bytes / (ms / 1e3) / 1e9}
+    del f
     res["note"] = ("algorithmic bytes = one read of the field + the FP64 output; the output "
                    "tensor is allocated by the binding per call; peak %s" % kind)
     plan.close()

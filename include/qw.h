@@ -163,6 +163,20 @@ qw_status qw_sync(qw_plan plan, void* stream);
  * Errors: QW_EINVAL, QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
 qw_status qw_observables(qw_plan plan, const void* psi_dev, qw_obs* out, void* stream);
 
+/* Foldy-Wouthuysen field (the Remark on the Newton-Wigner position, Eqs. fw, NW):
+ * the coefficients phi_r(k) = u_r(k)^dag psi^(k) of psi_dev on the paper's
+ * eigenvectors of D_k (Eq. evecs-D; 1D: u_+ = (cos th/2, -sin th/2),
+ * u_- = (sin th/2, cos th/2), th = atan2(m, n sin k)), taken back to position
+ * space, written to out_dev (DEVICE, caller-owned, the field's size and layout,
+ * component r in place of spinor component s, r = (s, p) in the order (+,+),
+ * (+,-), (-,+), (-,-); 1D: +, -).  Its mean position (qw_position_moments or
+ * qw_observables on out_dev) is the Newton-Wigner position, which moves by
+ * t <grad omega> on the positive and -t <grad omega> on the negative part and
+ * does not jitter.  out_dev may equal psi_dev (in place).  Needs the spectral
+ * sizes of qw_plan_prepare_spectral.  Asynchronous on `stream`.
+ * Errors: QW_EINVAL (null argument, axis length not 2^a 3^b), QW_ENOMEM, QW_ECUDA. */
+qw_status qw_fw_transform(qw_plan plan, const void* psi_dev, void* out_dev, void* stream);
+
 /* Position moments up to second order (the mean and covariance that the drift
  * v = grad omega and diffusion D = grad grad omega of Sec. 5.1's particle states
  * move and spread).  out (HOST, 10 doubles, caller-owned): norm, the mean

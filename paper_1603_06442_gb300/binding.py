@@ -93,6 +93,7 @@ _SIGS = {
     "qw_evolve_spectral": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "qw_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(qw_obs),
                                       ctypes.c_void_p]),
+    "qw_fw_transform": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "qw_position_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                            ctypes.c_void_p]),
     "qw_projection": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
@@ -278,6 +279,10 @@ def qw_observables(plan, psi, stream=None):
     out = qw_obs()
     _check(load().qw_observables(plan, _ptr(psi), ctypes.byref(out), _stream(stream)))
     return out.as_dict()
+
+
+def qw_fw_transform(plan, psi, out, stream=None):
+    _check(load().qw_fw_transform(plan, _ptr(psi), _ptr(out), _stream(stream)))
 
 
 def qw_position_moments(plan, psi, stream=None):
@@ -476,6 +481,16 @@ class Plan:
     def observables(self, psi, stream=None):
         self.check_field(psi)
         return qw_observables(self.handle, psi, stream)
+
+    def fw_transform(self, psi, out=None, stream=None):
+        """Foldy-Wouthuysen field of psi (a new CUDA tensor unless `out` is given)."""
+        import torch
+        self.check_field(psi)
+        if out is None:
+            out = torch.empty_like(psi)
+        self.check_field(out)
+        qw_fw_transform(self.handle, psi, out, stream)
+        return out
 
     def position_moments(self, psi, stream=None):
         self.check_field(psi)

@@ -436,6 +436,23 @@ qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) 
   return QW_OK;
 }
 
+qw_status qw_fw_transform(qw_plan p, const void* psi, void* out, void* stream) {
+  if (!p || !psi || !out) {
+    set_error("qw_fw_transform: null argument");
+    return QW_EINVAL;
+  }
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  st = prepare_spectral(p);
+  if (st != QW_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (out != psi)
+    QW_CHECK_CUDA(cudaMemcpyAsync(out, psi, (size_t)p->g.elems * p->elem_bytes, cudaMemcpyDeviceToDevice, s));
+  if ((st = fft_forward(p->fft, p->g.dim, out, s)) != QW_OK) return st;
+  if ((st = launch_fw_pointwise(p->g, spec_axes(p->g, p->fft), p->dtype, p->n, p->mass, out, s)) != QW_OK) return st;
+  return fft_inverse(p->fft, p->g.dim, out, s);
+}
+
 qw_status qw_position_moments(qw_plan p, const void* psi, double* out, void* stream) {
   if (!p || !psi || !out) {
     set_error("qw_position_moments: null argument");

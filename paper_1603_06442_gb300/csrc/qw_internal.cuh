@@ -149,6 +149,10 @@ qw_status launch_evolve_fused_x(const Geometry& g, const SpecAxes& ax, const Fft
 int64_t fused_x_grid(const Geometry& g);
 qw_status launch_weights_fused_x(const Geometry& g, const SpecAxes& ax, const FftPlan& f, double n, double m,
                                  const void* data, double* partials, double* result, cudaStream_t st);
+// Per-wave-vector Foldy-Wouthuysen coefficients of a forward spectrum, in place (with the
+// inverse transform's 1/|V| scale folded in).
+qw_status launch_fw_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m, void* psi_hat,
+                              cudaStream_t st);
 qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
                                   const double* omega, int64_t t, void* psi_hat, cudaStream_t st,
                                   const double* norm0 = nullptr);

@@ -101,6 +101,126 @@ __global__ void __launch_bounds__(256) evolve_kernel(int dim, AxesDev a, int64_t
   }
 }
 
+// Foldy-Wouthuysen coefficients of one wave vector (the Remark on the Newton-Wigner
+// position): w_r = u_r(k)^dag v on the paper's eigenvectors of D_k (Eq. evecs-D),
+// r = (s, p) in the order (+,+), (+,-), (-,+), (-,-):
+//   u_{s,p} = (A, -p B e^{i phi}, -s C, s p D) / 2,  A = sqrt((1 - p vW)(1 + s p vD)),
+//   B = sqrt((1 + p vW)(1 + s p vD)), C = sqrt((1 - p vW)(1 - s p vD)), D = sqrt((1 + p vW)(1 - s p vD)),
+// vW = -n~_z / |n~|, e^{i phi} = -(n~_x + i n~_y) / |(n~_x, n~_y)| (phi = Arg(n~_y - i n~_x) - pi/2),
+// vD = n |n~| / sqrt(m^2 + n^2 |n~|^2); vW = 0, phi = 0, vD = 0 where their ratios are 0/0.
+// 1D (the decoupled 2x2 walk): u_+ = (cos th/2, -sin th/2), u_- = (sin th/2, cos th/2),
+// th = atan2(m, n sin k).
+template <typename T, int S>
+__device__ __forceinline__ void fw_apply(T u, T nx, T ny, T nz, T n, T m, typename Cx2<T>::t (&v)[S]) {
+  using V = typename Cx2<T>::t;
+  (void)u;
+  if (S == 2) {
+    const T th = atan2(m, n * nz);
+    const T c = cos((T)0.5 * th), sn = sin((T)0.5 * th);
+    const V a = v[0], b = v[1];
+    v[0].x = c * a.x - sn * b.x;
+    v[0].y = c * a.y - sn * b.y;
+    v[1].x = sn * a.x + c * b.x;
+    v[1].y = sn * a.y + c * b.y;
+    return;
+  }
+  const T tiny = sizeof(T) == 8 ? (T)1e-12 : (T)1e-6;
+  const T r = sqrt(nx * nx + ny * ny + nz * nz);
+  T vW = r < tiny ? (T)0 : -nz / r;
+  vW = vW > (T)1 ? (T)1 : (vW < (T)-1 ? (T)-1 : vW);
+  const T wa = sqrt(nx * nx + ny * ny);
+  const T ec = wa > tiny ? -nx / wa : (T)1, es = wa > tiny ? -ny / wa : (T)0;
+  const T den = sqrt(m * m + n * n * r * r);
+  T vD = den > tiny ? n * r / den : (T)0;
+  vD = vD > (T)1 ? (T)1 : (vD < (T)-1 ? (T)-1 : vD);
+  // e^{-i phi} v1, e^{-i phi} v3
+  V t1, t3;
+  t1.x = ec * v[1].x + es * v[1].y;
+  t1.y = ec * v[1].y - es * v[1].x;
+  t3.x = ec * v[3].x + es * v[3].y;
+  t3.y = ec * v[3].y - es * v[3].x;
+  V w[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T sg = q < 2 ? (T)1 : (T)-1, pp = (q & 1) ? (T)-1 : (T)1;
+    const T A = (T)0.5 * sqrt(((T)1 - pp * vW) * ((T)1 + sg * pp * vD));
+    const T B = (T)0.5 * sqrt(((T)1 + pp * vW) * ((T)1 + sg * pp * vD));
+    const T C = (T)0.5 * sqrt(((T)1 - pp * vW) * ((T)1 - sg * pp * vD));
+    const T D = (T)0.5 * sqrt(((T)1 + pp * vW) * ((T)1 - sg * pp * vD));
+    w[q].x = A * v[0].x - pp * B * t1.x - sg * C * v[2].x + sg * pp * D * t3.x;
+    w[q].y = A * v[0].y - pp * B * t1.y - sg * C * v[2].y + sg * pp * D * t3.y;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = w[q];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) fw_kernel(int dim, AxesDev a, int64_t count, Mass ms, T scale,
+                                                 typename Cx2<T>::t* __restrict__ data) {
+  using V = typename Cx2<T>::t;
+  int64_t x, y, z;
+  if (!grid_pos(a, x, y, z)) return;
+  const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
+  const int P = planes_of(dim);
+  const T n = sizeof(T) == 8 ? (T)ms.n : (T)ms.nf, m = sizeof(T) == 8 ? (T)ms.m : (T)ms.mf;
+  V v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (q < P) v[q] = data[q * count + idx];
+  int64_t f[3], fs;
+  wave_vectors(dim, x, y, z, a, f, fs);
+  if (dim == 1) {
+    V w[2] = {v[0], v[1]};
+    T u, nx, ny, nz;
+    symbol_tab<T>(1, a, f[0], f[1], f[2], 0, u, nx, ny, nz);
+    fw_apply<T, 2>(u, nx, ny, nz, n, m, w);
+    v[0] = make_vec(w[0], scale);
+    v[1] = make_vec(w[1], scale);
+  } else if (dim == 2) {
+    V w[4] = {v[0], v[1], v[2], v[3]};
+    T u, nx, ny, nz;
+    symbol_tab<T>(2, a, f[0], f[1], f[2], 0, u, nx, ny, nz);
+    fw_apply<T, 4>(u, nx, ny, nz, n, m, w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = make_vec(w[q], scale);
+  } else {
+    // BCC: the two wave vectors q0, q1 of the cell from the coset mix, as in evolve_point
+    T ar, ai;
+    coset_phase<T>(fs, a.len[0], ar, ai);
+    V c0[4], c1[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      V b;
+      b.x = ar * v[4 + q].x + ai * v[4 + q].y;
+      b.y = ar * v[4 + q].y - ai * v[4 + q].x;
+      c0[q].x = (T)0.5 * (v[q].x + b.x);
+      c0[q].y = (T)0.5 * (v[q].y + b.y);
+      c1[q].x = (T)0.5 * (v[q].x - b.x);
+      c1[q].y = (T)0.5 * (v[q].y - b.y);
+    }
+    T u, nx, ny, nz;
+    symbol_tab<T>(3, a, f[0], f[1], f[2], 0, u, nx, ny, nz);
+    fw_apply<T, 4>(u, nx, ny, nz, n, m, c0);
+    symbol_tab<T>(3, a, f[0], f[1], f[2], 1, u, nx, ny, nz);
+    fw_apply<T, 4>(u, nx, ny, nz, n, m, c1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      V s0, d, s1;
+      s0.x = c0[q].x + c1[q].x;
+      s0.y = c0[q].y + c1[q].y;
+      d.x = c0[q].x - c1[q].x;
+      d.y = c0[q].y - c1[q].y;
+      s1.x = ar * d.x - ai * d.y;
+      s1.y = ar * d.y + ai * d.x;
+      v[q] = make_vec(s0, scale);
+      v[4 + q] = make_vec(s1, scale);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (q < P) data[q * count + idx] = v[q];
+}
+
 // launch_fused<R1, R2> is instantiated in fused_x_*.cu
 QW_FUSED_LENGTHS(QW_FUSED_X_EXTERN)
 
@@ -207,6 +327,20 @@ qw_status launch_evolve_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtyp
     evolve_kernel<double><<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), count, make_mass(n, m), omega,
                                                           make_time(t), inv, norm0, static_cast<double2*>(psi_hat));
   QW_CHECK_LAUNCH("evolve launch");
+  return QW_OK;
+}
+
+qw_status launch_fw_pointwise(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m, void* psi_hat,
+                              cudaStream_t st) {
+  const int64_t count = kcount(g);
+  const double inv = 1.0 / (double)g.vol;
+  if (dt == QW_C64)
+    fw_kernel<float><<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), count, make_mass(n, m), (float)inv,
+                                               static_cast<float2*>(psi_hat));
+  else
+    fw_kernel<double><<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), count, make_mass(n, m), inv,
+                                                static_cast<double2*>(psi_hat));
+  QW_CHECK_LAUNCH("Foldy-Wouthuysen launch");
   return QW_OK;
 }
 
