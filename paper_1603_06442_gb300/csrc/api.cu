@@ -143,7 +143,7 @@ qw_status qw_plan_create(int dim, int64_t N, double mass, qw_dtype dtype, qw_pla
   qw_status st = QW_OK;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaMalloc(&p->scratch, (size_t)g.elems * p->elem_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&p->red_partials, sizeof(double) * 10 * kObsBlocks);
+  if (e == cudaSuccess) e = cudaMalloc(&p->red_partials, sizeof(double) * 10 * kMom2MaxBlocks);
   if (e == cudaSuccess) e = cudaMalloc(&p->red_result, sizeof(double) * 16);
   if (e == cudaSuccess) e = cudaMallocHost(&p->red_host, sizeof(double) * 16);
   if (e == cudaSuccess) e = cudaMalloc(&p->dev_flags, sizeof(int) * 2);

@@ -77,66 +77,82 @@ __global__ void __launch_bounds__(kObsThreads) fold_partials_kernel(const double
   }
 }
 
-// Second moments (the position covariance of Sec. 5.1's particle-state kinematics): per
-// segment of SEG x-cells the density sums n = sum d, m1 = sum j d, m2 = sum j^2 d (j < SEG)
-// in the field's precision, then, with X = X0 + sc j, Y and Z fixed on the segment, the ten
-// FP64 sums  n, S_x, S_y, S_z, S_xx, S_yy, S_zz, S_xy, S_xz, S_yz.
+// Second moments (the position covariance of Sec. 5.1's particle-state kinematics): the
+// ten FP64 sums n, S_x, S_y, S_z, S_xx, S_yy, S_zz, S_xy, S_xz, S_yz of the density over the
+// position coordinates.  A thread owns one x column of one coset (X fixed) and a chunk of
+// its (z, y) rows (the threads of a warp read consecutive x); it sums d, Y d, Z d, Y^2 d,
+// Z^2 d, Y Z d over groups of four rows in the field's precision, then in FP64, and adds
+// the X-weighted terms once per column.  One partial per block, folded in a fixed order.
 constexpr int kMom2 = 10;
-template <typename R, int SEG>
+template <typename R>
 __global__ void __launch_bounds__(kObsThreads) moments2_kernel(const typename Cplx<R>::T* __restrict__ psi,
-                                                               Geometry g, double* __restrict__ partials) {
+                                                               Geometry g, int chunks, double* __restrict__ partials) {
   using C = typename Cplx<R>::T;
-  const int64_t segs_per_row = g.nx / SEG;
-  const int64_t rows = (int64_t)g.ncoset * g.nz * g.ny;
-  const int64_t nseg = rows * segs_per_row;
-  const double sc = (g.dim == 3) ? 2.0 : 1.0;
+  const int64_t units = (int64_t)g.ncoset * g.nx;
+  const int64_t rows = g.nz * g.ny;
+  const int j = blockIdx.y;
+  const int64_t r0 = j * rows / chunks, r1 = (j + 1) * rows / chunks;
+  const int ny = (int)g.ny;
+  const R sc = g.dim == 3 ? (R)2 : (R)1;
   double acc[kMom2];
 #pragma unroll
-  for (int j = 0; j < kMom2; ++j) acc[j] = 0.0;
-  for (int64_t sidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sidx < nseg;
-       sidx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = sidx / segs_per_row;
-    const int64_t x0 = (sidx - row * segs_per_row) * SEG;
-    const int64_t y = row % g.ny;
-    const int64_t zc = row / g.ny;
-    const int64_t z = zc % g.nz;
-    const int c = (int)(zc / g.nz);
-    const C* base = psi + (int64_t)c * g.s * g.vol + (z * g.ny + y) * g.nx + x0;
-    R nf = 0, m1 = 0, m2 = 0;
-#pragma unroll
-    for (int j = 0; j < SEG; ++j) {
-      R d = 0;
-      for (int s = 0; s < g.s; ++s) {
-        C v = __ldg(base + (int64_t)s * g.vol + j);
-        d = fma(v.x, v.x, d);
-        d = fma(v.y, v.y, d);
+  for (int q = 0; q < kMom2; ++q) acc[q] = 0.0;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(u / g.nx);
+    const int64_t x = u - (int64_t)c * g.nx;
+    const R off = g.dim == 3 ? (R)c : (R)0;
+    const C* col = psi + (int64_t)c * g.s * g.vol + x;
+    int z = (int)(r0 / ny), y = (int)(r0 - (int64_t)z * ny);
+    double n = 0.0, sy = 0.0, sz = 0.0, syy = 0.0, szz = 0.0, syz = 0.0;
+    for (int64_t r = r0; r < r1;) {
+      R gn = 0, gy = 0, gz = 0, gyy = 0, gzz = 0, gyz = 0;
+      const int64_t rend = r + 4 < r1 ? r + 4 : r1;
+      for (; r < rend; ++r) {
+        const C* q = col + ((int64_t)z * ny + y) * g.nx;
+        R d = 0;
+        for (int s = 0; s < g.s; ++s) {
+          const C v = q[(int64_t)s * g.vol];
+          d = fma(v.x, v.x, d);
+          d = fma(v.y, v.y, d);
+        }
+        const R Y = g.dim >= 2 ? sc * (R)y + off : (R)0, Z = g.dim >= 3 ? sc * (R)z + off : (R)0;
+        const R yd = Y * d, zd = Z * d;
+        gn += d;
+        gy += yd;
+        gz += zd;
+        gyy = fma(Y, yd, gyy);
+        gzz = fma(Z, zd, gzz);
+        gyz = fma(Y, zd, gyz);
+        if (++y == ny) {
+          y = 0;
+          ++z;
+        }
       }
-      nf += d;
-      m1 = fma((R)j, d, m1);
-      m2 = fma((R)(j * j), d, m2);
+      n += (double)gn;
+      sy += (double)gy;
+      sz += (double)gz;
+      syy += (double)gyy;
+      szz += (double)gzz;
+      syz += (double)gyz;
     }
-    const double n = (double)nf, M1 = (double)m1, M2 = (double)m2;
-    const double off = (double)c;
-    const double X0 = sc * (double)x0 + off;
-    const double Y = g.dim >= 2 ? sc * (double)y + off : 0.0;
-    const double Z = g.dim >= 3 ? sc * (double)z + off : 0.0;
-    const double sx = fma(sc, M1, X0 * n);                       // sum X d
-    const double sxx = fma(sc * sc, M2, X0 * fma(2.0 * sc, M1, X0 * n));  // sum X^2 d
+    const double X = (double)(sc * (R)x + off);
     acc[0] += n;
-    acc[1] += sx;
-    acc[2] += Y * n;
-    acc[3] += Z * n;
-    acc[4] += sxx;
-    acc[5] += Y * Y * n;
-    acc[6] += Z * Z * n;
-    acc[7] += Y * sx;
-    acc[8] += Z * sx;
-    acc[9] += Y * Z * n;
+    acc[1] += X * n;
+    acc[2] += sy;
+    acc[3] += sz;
+    acc[4] += X * X * n;
+    acc[5] += syy;
+    acc[6] += szz;
+    acc[7] += X * sy;
+    acc[8] += X * sz;
+    acc[9] += syz;
   }
   block_sum<kMom2, kObsThreads>(acc);
   if (threadIdx.x == 0) {
+    const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
-    for (int j = 0; j < kMom2; ++j) partials[(int64_t)blockIdx.x * kMom2 + j] = acc[j];
+    for (int q = 0; q < kMom2; ++q) partials[b * kMom2 + q] = acc[q];
   }
 }
 
@@ -157,25 +173,27 @@ __global__ void __launch_bounds__(kObsThreads) fold_moments2_kernel(const double
 }
 
 template <typename R>
-static void launch_moments2_t(const Geometry& g, const void* psi, double* partials, cudaStream_t st) {
+static int launch_moments2_t(const Geometry& g, const void* psi, double* partials, cudaStream_t st) {
   using C = typename Cplx<R>::T;
-  const C* p = static_cast<const C*>(psi);
-  if (g.nx % 16 == 0)
-    moments2_kernel<R, 16><<<kObsBlocks, kObsThreads, 0, st>>>(p, g, partials);
-  else if (g.nx % 4 == 0)
-    moments2_kernel<R, 4><<<kObsBlocks, kObsThreads, 0, st>>>(p, g, partials);
-  else
-    moments2_kernel<R, 1><<<kObsBlocks, kObsThreads, 0, st>>>(p, g, partials);
+  const int64_t units = (int64_t)g.ncoset * g.nx, rows = g.nz * g.ny;
+  int64_t bx = (units + kObsThreads - 1) / kObsThreads;
+  if (bx > kMom2MaxBlocks / 2) bx = kMom2MaxBlocks / 2;
+  // ~2^18 threads in all: chunks of the rows when the columns are few
+  int64_t chunks = ((int64_t(1) << 18) + bx * kObsThreads - 1) / (bx * kObsThreads);
+  if (chunks > rows) chunks = rows;
+  if (chunks * bx > kMom2MaxBlocks) chunks = kMom2MaxBlocks / bx;
+  if (chunks < 1) chunks = 1;
+  moments2_kernel<R><<<dim3((unsigned)bx, (unsigned)chunks), kObsThreads, 0, st>>>(static_cast<const C*>(psi), g,
+                                                                                   (int)chunks, partials);
+  return (int)(bx * chunks);
 }
 
 qw_status launch_position_moments2(const Geometry& g, qw_dtype dt, const void* psi, double* partials,
                                    double* result, cudaStream_t st) {
-  if (dt == QW_C64)
-    launch_moments2_t<float>(g, psi, partials, st);
-  else
-    launch_moments2_t<double>(g, psi, partials, st);
+  const int nblk = (dt == QW_C64) ? launch_moments2_t<float>(g, psi, partials, st)
+                                  : launch_moments2_t<double>(g, psi, partials, st);
   QW_CHECK_LAUNCH("second moments launch");
-  fold_moments2_kernel<<<1, kObsThreads, 0, st>>>(partials, kObsBlocks, result);
+  fold_moments2_kernel<<<1, kObsThreads, 0, st>>>(partials, nblk, result);
   QW_CHECK_LAUNCH("second moments fold launch");
   return QW_OK;
 }

@@ -112,7 +112,8 @@ __device__ __forceinline__ void block_sum(double (&acc)[NV]) {
 constexpr int kObsBlocks = 608;  // 4 x 152 SMs
 constexpr int kObsThreads = 256;
 // Ten FP64 sums (n, S_x, S_y, S_z, S_xx, S_yy, S_zz, S_xy, S_xz, S_yz) of the density over
-// the position coordinates into result; partials: 10 * kObsBlocks doubles.
+// the position coordinates into result; partials: 10 * kMom2MaxBlocks doubles.
+constexpr int kMom2MaxBlocks = 4096;
 qw_status launch_position_moments2(const Geometry& g, qw_dtype dt, const void* psi, double* partials,
                                    double* result, cudaStream_t st);
 qw_status launch_position_moments(const Geometry& g, qw_dtype dt, const void* psi, double* partials,
@@ -199,7 +200,7 @@ struct qw_plan_s {
                         // plans hold nu = omega / 2 pi as FP32 (hi, lo) pairs instead
   double* spec_partials;  // 2 * kObsBlocks doubles for the particle-weight reduction
   double* xw_partials;    // 2 doubles per CTA of the x-pass weights (when the x pass is fused)
-  double* red_partials; // 10 * kObsBlocks doubles
+  double* red_partials; // 10 * kMom2MaxBlocks doubles (>= 4 * kObsBlocks)
   double* red_result;   // 16 doubles (device)
   double* red_host;     // 16 doubles (pinned host)
   // host-field runs (qw_run_host): two device fields, a copy stream and its events,
