@@ -65,6 +65,39 @@ __device__ __forceinline__ Row3 srow_at(const float* row, int tx) {
   return r;
 }
 
+// psi1 rows are stored split by cell parity: the even cells (0, 2, ..., 66) of a row in
+// floats [0, HALF), the odd cells in [HALF, 2 HALF).  A warp's three-cell windows of psi1
+// then load as three 8-byte loads with consecutive addresses across the lanes (no bank
+// conflicts), where the interleaved psi0 rows need an 8-byte load at a 16-byte lane stride.
+constexpr int HALF = ROWF / 2;
+
+// Cells [c0, c0 + 3) of one psi1 row, c0 = 2 tx + OFF (OFF = 1 or 2 in step 2).
+template <int OFF>
+__device__ __forceinline__ Row3 srow_eo(const float* row, int tx) {
+  static_assert(OFF == 1 || OFF == 2, "psi1 windows start at an odd or even cell");
+  const float2* ev = reinterpret_cast<const float2*>(row);
+  const float2* od = reinterpret_cast<const float2*>(row + HALF);
+  Row3 r;
+  if constexpr (OFF == 2) {  // c0 = 2 (tx + 1)
+    r.lo = ev[tx + 1];
+    r.mid = od[tx + 1];
+    r.hi = ev[tx + 2];
+  } else {  // c0 = 2 tx + 1
+    r.lo = od[tx];
+    r.mid = ev[tx + 1];
+    r.hi = od[tx + 1];
+  }
+  return r;
+}
+
+template <int OFF, bool EO>
+__device__ __forceinline__ Row3 srow(const float* row, int tx) {
+  if constexpr (EO)
+    return srow_eo<OFF>(row, tx);
+  else
+    return srow_at<OFF>(row, tx);
+}
+
 // One step for the two cells of output coset C at box row R, box columns
 // Q0 = 2 tx + QOFF and Q0 + 1 (QOFF even: 16-byte aligned).  Sources: the other
 // coset at the h_z = +1 layer (la: components 0, 1, 3) and the h_z = -1 layer
@@ -75,7 +108,8 @@ __device__ __forceinline__ Row3 srow_at(const float* row, int tx) {
 // thread's next step (one layer further in z), at the same rows and columns, and
 // both read components 0 and 1 there.  carry keeps those two Row3 pairs in
 // registers between the steps; with first = true they are loaded from la instead.
-template <int C, int QOFF>
+// EO: the sources are psi1 rows (parity-split layout) instead of psi0 rows.
+template <int C, int QOFF, bool EO = false>
 __device__ __forceinline__ void pair_step(Row3 (&carry)[2][2], bool first, const float* la, const float* lb,
                                           const float* own, int R, int tx, const Coef32& cf, float4 (&res)[4]) {
   constexpr int OFF = QOFF - 1 + C;
@@ -84,14 +118,14 @@ __device__ __forceinline__ void pair_step(Row3 (&carry)[2][2], bool first, const
   for (int iy = 0; iy < 2; ++iy) {
     const float* base = la + (R - 1 + C + iy) * ROWF;
     if (first) {
-      carry[iy][0] = srow_at<OFF>(base, tx);
-      carry[iy][1] = srow_at<OFF>(base + CS2, tx);
+      carry[iy][0] = srow<OFF, EO>(base, tx);
+      carry[iy][1] = srow<OFF, EO>(base + CS2, tx);
     }
-    d[iy] = srow_at<OFF>(base + 3 * CS2, tx);
+    d[iy] = srow<OFF, EO>(base + 3 * CS2, tx);
     const float* bb = lb + (R - 1 + C + iy) * ROWF;
-    a2[iy] = srow_at<OFF>(bb, tx);
-    b2[iy] = srow_at<OFF>(bb + CS2, tx);
-    c2[iy] = srow_at<OFF>(bb + 2 * CS2, tx);
+    a2[iy] = srow<OFF, EO>(bb, tx);
+    b2[iy] = srow<OFF, EO>(bb + CS2, tx);
+    c2[iy] = srow<OFF, EO>(bb + 2 * CS2, tx);
   }
   const Row3 a[2] = {carry[0][0], carry[1][0]}, b[2] = {carry[0][1], carry[1][1]};
   float2 S[2][4];
@@ -102,10 +136,20 @@ __device__ __forceinline__ void pair_step(Row3 (&carry)[2][2], bool first, const
     carry[iy][0] = a2[iy];
     carry[iy][1] = b2[iy];
   }
-  const float* ob = own + R * ROWF + 2 * (2 * tx + QOFF);
   float4 o[4];
+  if constexpr (EO) {  // cells 2 tx + QOFF, + 1: even and odd halves of the row
+    const float* ob = own + R * ROWF + 2 * (tx + QOFF / 2);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) o[q] = *reinterpret_cast<const float4*>(ob + q * CS2);
+    for (int q = 0; q < 4; ++q) {
+      const float2 e = *reinterpret_cast<const float2*>(ob + q * CS2);
+      const float2 od = *reinterpret_cast<const float2*>(ob + q * CS2 + HALF);
+      o[q] = make_float4(e.x, e.y, od.x, od.y);
+    }
+  } else {
+    const float* ob = own + R * ROWF + 2 * (2 * tx + QOFF);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = *reinterpret_cast<const float4*>(ob + q * CS2);
+  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const float4 w = o[q ^ 2];
@@ -115,11 +159,16 @@ __device__ __forceinline__ void pair_step(Row3 (&carry)[2][2], bool first, const
   }
 }
 
+// psi1 cells 2 tx + QOFF (even) and 2 tx + QOFF + 1 (odd) of row R, parity-split layout.
 template <int QOFF>
 __device__ __forceinline__ void store_smem(float* dst, int R, int tx, const float4 (&res)[4]) {
-  float* d = dst + R * ROWF + 2 * (2 * tx + QOFF);
+  static_assert(QOFF % 2 == 0, "psi1 pairs start at an even cell");
+  float* d = dst + R * ROWF + 2 * (tx + QOFF / 2);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) *reinterpret_cast<float4*>(d + q * CS2) = res[q];
+  for (int q = 0; q < 4; ++q) {
+    *reinterpret_cast<float2*>(d + q * CS2) = make_float2(res[q].x, res[q].y);
+    *reinterpret_cast<float2*>(d + q * CS2 + HALF) = make_float2(res[q].z, res[q].w);
+  }
 }
 
 // psi1 of both cosets on the region step 2 reads:
@@ -282,10 +331,10 @@ __global__ void __launch_bounds__(NT2, 1)
         float4* d0 = reinterpret_cast<float4*>(out + orow) + tx;
         float4* d1 = reinterpret_cast<float4*>(out + 4 * vol + orow) + tx;
         float4 res[4];
-        pair_step<0, 2>(q0, i == zs, buf1(1, i - 1), buf1(1, i), buf1(0, i), ty + 1, tx, cf, res);
+        pair_step<0, 2, true>(q0, i == zs, buf1(1, i - 1), buf1(1, i), buf1(0, i), ty + 1, tx, cf, res);
 #pragma unroll
         for (int q = 0; q < 4; ++q) d0[q * v4] = res[q];
-        pair_step<1, 2>(q1, i == zs, buf1(0, i), buf1(0, i + 1), buf1(1, i), ty + 1, tx, cf, res);
+        pair_step<1, 2, true>(q1, i == zs, buf1(0, i), buf1(0, i + 1), buf1(1, i), ty + 1, tx, cf, res);
 #pragma unroll
         for (int q = 0; q < 4; ++q) d1[q * v4] = res[q];
       }
