@@ -490,7 +490,7 @@ qw_status qw_projection(qw_plan p, const void* psi, int keep, double* out, void*
   }
   qw_status st = use_device(p);
   if (st != QW_OK) return st;
-  const int64_t need = projection_partials(p->g, keep);
+  const int64_t need = projection_partials(p->g, keep, p->dtype);
   if (need > p->proj_cap) {
     if (p->proj_partials) QW_CHECK_CUDA(cudaFree(p->proj_partials));
     p->proj_partials = nullptr;

@@ -26,6 +26,7 @@ struct ProjGeo {
   int oy, oz;            // output-row extents: ny or 1, nz or 1
   int ry;                // reduced-row extent along y: 1 (kept) or ny
   int chunks;
+  int pair;              // x kept, complex64, nx even: a thread owns two adjacent x (16-byte loads)
   int64_t vol;
   int64_t n_orows;       // ncos * oz * oy
   int64_t rrows;         // reduced rows per output row
@@ -123,6 +124,48 @@ __global__ void __launch_bounds__(256) proj_x_kernel(const typename Cx<R>::T* __
     partials[(int64_t)j * p.nout + gid] = acc;
 }
 
+// proj_x_kernel for complex64 with two adjacent x per thread (x even): one 16-byte load per
+// component and row instead of two 8-byte ones.
+__global__ void __launch_bounds__(256) proj_x2_kernel(const float2* __restrict__ psi, ProjGeo p,
+                                                      double* __restrict__ out, double* __restrict__ partials) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= p.nout / 2) return;
+  const int64_t o = 2 * gid;
+  const int x = (int)(o % p.nx);
+  const int64_t orow = o / p.nx;
+  int c, zk, yk;
+  decode_orow(p, orow, c, zk, yk);
+  const int j = blockIdx.y;
+  const int64_t r0 = j * p.rrows / p.chunks, r1 = (j + 1) * p.rrows / p.chunks;
+  double a0 = 0.0, a1 = 0.0;
+  RowWalk w(p, zk, yk, r0);
+  for (int64_t r = r0; r < r1;) {
+    float g0 = 0.f, g1 = 0.f;
+    const int64_t rend = r + 4 < r1 ? r + 4 : r1;
+    for (; r < rend; ++r) {
+      const float2* q = psi + w.offset(p, c) + x;
+      float d0 = 0.f, d1 = 0.f;
+      for (int s = 0; s < p.s; ++s) {
+        const float4 v = *reinterpret_cast<const float4*>(q + (int64_t)s * p.vol);
+        d0 = fmaf(v.x, v.x, fmaf(v.y, v.y, d0));
+        d1 = fmaf(v.z, v.z, fmaf(v.w, v.w, d1));
+      }
+      g0 += d0;
+      g1 += d1;
+      w.next(p);
+    }
+    a0 += (double)g0;
+    a1 += (double)g1;
+  }
+  if (p.chunks == 1) {
+    out[phys_index(p, c, zk, yk, x)] = a0;
+    out[phys_index(p, c, zk, yk, x + 1)] = a1;
+  } else {
+    partials[(int64_t)j * p.nout + o] = a0;
+    partials[(int64_t)j * p.nout + o + 1] = a1;
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) proj_w_kernel(const typename Cx<R>::T* __restrict__ psi, ProjGeo p,
                                                      double* __restrict__ out, double* __restrict__ partials) {
@@ -169,7 +212,7 @@ __global__ void __launch_bounds__(256) proj_fold_kernel(const double* __restrict
 constexpr int64_t kProjThreads = int64_t(1) << 18;
 constexpr int64_t kProjWarps = kProjThreads / 32;
 
-ProjGeo make_proj(const Geometry& g, int keep) {
+ProjGeo make_proj(const Geometry& g, int keep, qw_dtype dt) {
   ProjGeo p{};
   p.dim = g.dim;
   p.s = g.s;
@@ -188,7 +231,9 @@ ProjGeo make_proj(const Geometry& g, int keep) {
   p.n_orows = (int64_t)p.ncos * p.oz * p.oy;
   p.rrows = (int64_t)(p.kz ? 1 : p.nz) * p.ry;
   p.nout = p.n_orows * (p.kx ? p.nx : 1);
-  const int64_t units = p.kx ? p.nout : p.n_orows, want = p.kx ? kProjThreads : kProjWarps;
+  p.pair = (p.kx && dt == QW_C64 && p.nx % 2 == 0) ? 1 : 0;
+  const int64_t units = p.kx ? (p.pair ? p.nout / 2 : p.nout) : p.n_orows;
+  const int64_t want = p.kx ? kProjThreads : kProjWarps;
   int64_t k = (want + units - 1) / units;
   if (k > p.rrows) k = p.rrows;
   if (k > 65535) k = 65535;
@@ -198,8 +243,8 @@ ProjGeo make_proj(const Geometry& g, int keep) {
 
 }  // namespace
 
-int64_t projection_partials(const Geometry& g, int keep) {
-  const ProjGeo p = make_proj(g, keep);
+int64_t projection_partials(const Geometry& g, int keep, qw_dtype dt) {
+  const ProjGeo p = make_proj(g, keep, dt);
   return p.chunks == 1 ? 0 : (int64_t)p.chunks * (p.kx ? p.nout : p.n_orows);
 }
 
@@ -212,14 +257,16 @@ int64_t projection_outputs(const Geometry& g, int keep) {
 
 qw_status launch_projection(const Geometry& g, qw_dtype dt, const void* psi, int keep, double* out,
                             double* partials, cudaStream_t st) {
-  const ProjGeo p = make_proj(g, keep);
+  const ProjGeo p = make_proj(g, keep, dt);
   const int kept = p.kx + p.ky + p.kz;
   // BCC: physical points of mixed coordinate parity are not sites (two or more kept axes)
   if (g.dim == 3 && kept >= 2)
     QW_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * projection_outputs(g, keep), st));
-  const int64_t threads = p.kx ? p.nout : p.n_orows * 32;
+  const int64_t threads = p.kx ? (p.pair ? p.nout / 2 : p.nout) : p.n_orows * 32;
   const dim3 grid((unsigned)((threads + 255) / 256), (unsigned)p.chunks);
-  if (p.kx) {
+  if (p.pair) {
+    proj_x2_kernel<<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
+  } else if (p.kx) {
     if (dt == QW_C64)
       proj_x_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
     else

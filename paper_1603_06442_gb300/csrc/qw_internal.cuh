@@ -168,7 +168,7 @@ qw_status launch_packet(const Geometry& g, qw_dtype dt, const double* x0, double
 // ---- probability projections (projection.cu) ---------------------------------
 // keep: bit 0 x, bit 1 y, bit 2 z.  projection_partials: doubles of chunk partials the
 // launch needs (0: none); projection_outputs: N^(kept axes).
-int64_t projection_partials(const Geometry& g, int keep);
+int64_t projection_partials(const Geometry& g, int keep, qw_dtype dt);
 int64_t projection_outputs(const Geometry& g, int keep);
 qw_status launch_projection(const Geometry& g, qw_dtype dt, const void* psi, int keep, double* out,
                             double* partials, cudaStream_t st);
