@@ -221,11 +221,12 @@ def run_ours(args, rank, world, local):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    # warm-up (the first qw_run_host call also allocates the plan's two host-run device fields)
+    # warm-up (the first qw_run_host call also allocates the plan's two host-run device fields;
+    # two fields pass through both of them)
     for _ in range(args.warmup):
         plan.step(psi, S, stream)
         plan.observables(psi, stream)
-    plan.run_host([host], S, stream=stream)
+    plan.run_host([host, host], S, stream=stream)
     barrier()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),

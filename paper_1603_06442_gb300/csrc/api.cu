@@ -512,7 +512,12 @@ static qw_status host_run_setup(qw_plan_s* p) {
   const size_t bytes = (size_t)p->g.elems * p->elem_bytes;
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-    if (!p->hbuf[b]) e = cudaMalloc(&p->hbuf[b], bytes);
+    // written once here, so that a run's first copy into each buffer is not the first
+    // write into freshly allocated device memory
+    if (!p->hbuf[b]) {
+      e = cudaMalloc(&p->hbuf[b], bytes);
+      if (e == cudaSuccess) e = cudaMemset(p->hbuf[b], 0, bytes);
+    }
     if (e == cudaSuccess && !p->ev_copied[b]) e = cudaEventCreateWithFlags(&p->ev_copied[b], cudaEventDisableTiming);
     if (e == cudaSuccess && !p->ev_freed[b]) e = cudaEventCreateWithFlags(&p->ev_freed[b], cudaEventDisableTiming);
     if (e == cudaSuccess && !p->ev_stepped[b])
