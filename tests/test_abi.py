@@ -44,3 +44,22 @@ def test_argument_errors_without_gpu(qwlib):
     assert qwlib.qw_plan_create(1, 8, 0.5, 9, ctypes.byref(h)) == binding.QW_EINVAL
     assert qwlib.qw_step(None, None, 1, None) == binding.QW_EINVAL
     assert qwlib.qw_plan_field_elems(None) == -1
+
+
+def test_new_entry_points_reject_null_plans_without_gpu(qwlib):
+    import ctypes
+    obs = (binding.qw_obs * 1)()
+    out10 = (ctypes.c_double * 10)()
+    assert qwlib.qw_run_host(None, None, None, 0, 1, obs, None) == binding.QW_EINVAL
+    assert qwlib.qw_projection(None, None, 1, None, None) == binding.QW_EINVAL
+    assert qwlib.qw_projection_elems(None, 1) == -1
+    assert qwlib.qw_position_moments(None, None, out10, None) == binding.QW_EINVAL
+    assert qwlib.qw_fw_transform(None, None, None, None) == binding.QW_EINVAL
+    assert b"null" in qwlib.qw_last_error()
+
+
+def test_keep_masks():
+    assert binding.keep_mask({0}) == 1
+    assert binding.keep_mask([0, 2]) == 5
+    assert binding.keep_mask((1, 2, 0)) == 7
+    assert binding.keep_mask(6) == 6
