@@ -169,6 +169,34 @@ def oracle_cpu_baseline(seconds=12.0):
             "sample": "BCC N=64 box (%d sites), %d oracle update steps in FP64 numpy, %.1f s" % (sites, steps, dt)}
 
 
+def _oracle_worker(seconds):
+    return oracle_cpu_baseline(seconds)
+
+
+def _single_thread_env():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def oracle_cpu_baseline_all_cores(seconds=12.0):
+    """The same oracle sample in one process per host core at once (spawned: the parent may
+    hold a CUDA context), summed: the oracle's all-core throughput on this host."""
+    import multiprocessing as mp
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(n, initializer=_single_thread_env)
+    try:
+        res = pool.map_async(_oracle_worker, [seconds] * n).get(timeout=4 * seconds + 120)
+    except mp.TimeoutError:
+        pool.terminate()
+        return {"value": None, "unit": "site-steps/s", "cores": n, "sample": "timed out"}
+    finally:
+        pool.close()
+        pool.join()
+    return {"value": float(sum(r["value"] for r in res)), "unit": "site-steps/s", "cores": n,
+            "sample": "%d processes, each the single-core sample for %.1f s" % (n, seconds)}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -318,6 +346,7 @@ def run_ours(args, rank, world, local):
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = oracle_cpu_baseline()
+        line["cpu_baseline"]["all_cores"] = oracle_cpu_baseline_all_cores()
     if extra:
         line["extra"] = extra
     plan.close()
