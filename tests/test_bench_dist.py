@@ -69,3 +69,10 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(3.25, 1, "cpu") == 3.25
     assert bench.job_value(10, 2, 3, 1, 1000.0) == 60.0
+
+
+def test_all_core_oracle_baseline_runs():
+    """The all-core leg spawns one process per core, each running the single-core sample."""
+    import bench
+    r = bench.oracle_cpu_baseline_all_cores(seconds=0.3)
+    assert r["cores"] >= 1 and r["value"] > 0
