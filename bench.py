@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--stencil", default=None, help="force a stencil variant (plain, vec, tma)")
     ap.add_argument("--only", default=None, choices=["spectral", "batched", "served", "projection"],
                     help="run one secondary workload alone and print its JSON (profiling runs)")
-    ap.add_argument("--requests", type=int, default=1000, help="served workload: number of requests")
+    ap.add_argument("--requests", type=int, default=2000, help="served workload: number of requests")
     ap.add_argument("--walks", type=int, default=256, help="batched workload: number of walks")
     ap.add_argument("--substeps", type=int, default=None, help="override stencil steps per bench step")
     args = ap.parse_args()
@@ -487,26 +487,7 @@ def projection_measurement(qb, dev, stream):
     return res
 
 
-def fp64_plain_rates(qb, dev, stream):
-    """FP64 plain-form (complex128 stencil) site-steps/s per dimension on this GPU."""
-    import torch
-    rates = {}
-    for dim, N in ((1, 1 << 22), (2, 1024), (3, 256)):
-        plan = qb.Plan(dim, N, 0.1, "c128")
-        x = torch.zeros(plan.elems, dtype=torch.complex128, device=dev)
-        x[::3] = 1e-3
-        plan.step(x, 2, stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        plan.step(x, 6, stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        rates[dim] = plan.sites * 6 / (e0.elapsed_time(e1) / 1e3)
-        plan.close()
-    return rates
-
-
-def served_measurement(qb, dev, stream, n_req=1000, rate=200.0, budget_gb=150, slots=8):
+def served_measurement(qb, dev, stream, n_req=2000, rate=200.0, budget_gb=150, slots=8):
     """Poisson arrivals (200/s) of walk requests: dim U{1,2,3}, sites log-U[1e4, 1e8] snapped to
     2^a 3^b boxes, m U[0, 0.5], t log-U[10, 1e5]; packets of width N/16 at the box centre; each asks
     for norm, <x> and particle weight.  Spectral path, complex64 with FP64 phase and reductions."""
@@ -520,16 +501,15 @@ def served_measurement(qb, dev, stream, n_req=1000, rate=200.0, budget_gb=150, s
         d, N = r["dim"], r["N"]
         reqs.append(qb.make_request(d, N, r["mass"], r["t"], x0=[N / 2] * d, sigma=max(N / 16, 1.0),
                                     k0=[0.2] * d, chi=chi[d]))
-    # warm the per-geometry FFT plans outside the measurement
-    warm = set()
-    wt = []
-    for r, req in zip(stream_reqs, reqs):
+    # no warm-up of the per-size FFT plans: a box size seen for the first time builds its
+    # tables on the device inside its request (reported apart below)
+    seen, first = set(), []
+    for r in stream_reqs:
         key = (r["dim"], r["N"])
-        if key not in warm:
-            warm.add(key)
-            wt.append(qb.qw_submit(srv, req))
-    _drain(qb, srv, wt)
+        first.append(key not in seen)
+        seen.add(key)
     lat, out, pend = [], [], {}
+    lat_of = {}
     t0 = _t.perf_counter()
     i = 0
     while i < len(reqs) or pend:
@@ -544,6 +524,7 @@ def served_measurement(qb, dev, stream, n_req=1000, rate=200.0, budget_gb=150, s
             done, obs, l = qb.qw_poll(srv, tk)
             if done:
                 lat.append(l)
+                lat_of[pend[tk]] = l
                 out.append(obs)
                 del pend[tk]
         _t.sleep(0.0002)
@@ -551,25 +532,80 @@ def served_measurement(qb, dev, stream, n_req=1000, rate=200.0, budget_gb=150, s
     st = qb.qw_server_stats(srv)
     qb.qw_server_destroy(srv)
     site_t = 0.0
-    fp64 = fp64_plain_rates(qb, dev, stream)
+    fp64 = fp64_plain_sample(qb, dev, stream, stream_reqs)
     est = []
     for r in stream_reqs:
         d, N = r["dim"], r["N"]
         sites = N if d == 1 else (N * N if d == 2 else N ** 3 // 4)
         site_t += sites * r["t"]
-        est.append(sites * r["t"] / fp64[d])
+        est.append(fp64["fit"][d]["fixed_s"] + sites * r["t"] / fp64["fit"][d]["site_steps_per_s"])
+    lat_first = np.array([lat_of[i] for i in lat_of if first[i]])
+    lat_rest = np.array([lat_of[i] for i in lat_of if not first[i]])
     lat = np.array(lat)
     est = np.array(est)
+    pct = lambda a, q: float(np.percentile(a, q) * 1e3) if len(a) else None
     return {"requests": len(reqs), "arrival_rate_per_s": rate, "slots": slots, "budget_GB": budget_gb,
-            "latency_p50_ms": float(np.percentile(lat, 50) * 1e3), "latency_p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "latency_p50_ms": pct(lat, 50), "latency_p99_ms": pct(lat, 99),
             "latency_mean_ms": float(lat.mean() * 1e3), "wall_s": wall, "completed_per_s": len(lat) / wall,
+            "first_seen_sizes": {"requests": int(len(lat_first)), "latency_p50_ms": pct(lat_first, 50),
+                                 "latency_p99_ms": pct(lat_first, 99)},
+            "repeat_sizes": {"requests": int(len(lat_rest)), "latency_p50_ms": pct(lat_rest, 50),
+                             "latency_p99_ms": pct(lat_rest, 99)},
             "equivalent_site_steps_per_s": site_t / wall, "peak_pool_GB": st["peak_bytes"] / 2 ** 30,
             "max_norm_drift": float(max(abs(o["norm"] - 1) for o in out)),
             "fp64_plain_unbatched": {"service_p50_ms": float(np.percentile(est, 50) * 1e3),
                                      "service_p99_ms": float(np.percentile(est, 99) * 1e3),
-                                     "rates_site_steps_per_s": {str(k): v for k, v in fp64.items()},
-                                     "note": "per-request service time of the FP64 stencil (sites*t / measured "
-                                             "FP64 rate on this GPU), no queueing: extrapolated, not run"}}
+                                     "measured_sample": fp64["sample"],
+                                     "fit": {str(k): v for k, v in fp64["fit"].items()},
+                                     "note": "every request of a seeded sample with sites*t <= %.0e run end to end "
+                                             "in the FP64 plain form (plan, copy in, t stencil steps, observables); "
+                                             "per-dimension cost model fixed_s + sites*t/rate fitted to it and "
+                                             "applied to every request of the stream, no queueing"
+                                             % fp64["max_site_steps"]}}
+
+
+def fp64_plain_sample(qb, dev, stream, stream_reqs, per_dim=4, max_site_steps=2e9):
+    """The unbatched FP64 plain form, measured: the first `per_dim` requests of each dimension
+    with sites*t <= max_site_steps run alone (complex128 plan, host field copied in, t stencil
+    steps, observables read back), timed end to end; a per-dimension model fixed + sites*t/rate
+    is fitted by least squares to these samples and to one long run per dimension."""
+    import time as _t
+    import torch
+    from paper_1603_06442_gb300 import inputs
+    chi = {1: [1, 0], 2: [0.5, 0.5, 0.5j, -0.5j], 3: [0.5, 0.5, 0.5j, -0.5j]}
+    sample, fit = [], {}
+    for d in (1, 2, 3):
+        picked = []
+        for r in stream_reqs:
+            N = r["N"]
+            sites = N if d == 1 else (N * N if d == 2 else N ** 3 // 4)
+            if r["dim"] == d and sites * r["t"] <= max_site_steps:
+                picked.append((N, r["mass"], r["t"], sites))
+            if len(picked) == per_dim:
+                break
+        # one long run per dimension anchors the rate
+        picked.append({1: (1 << 22, 0.1, 400, 1 << 22), 2: (1024, 0.1, 1500, 1 << 20),
+                       3: (256, 0.1, 300, 256 ** 3 // 4)}[d])
+        xs, ys = [], []
+        for N, m, t, sites in picked:
+            a = inputs.gaussian_packet(d, N, [N / 2] * d, max(N / 16, 1.0), [0.2] * d, chi[d])
+            host = torch.from_numpy(a.astype(np.complex128)).pin_memory()
+            torch.cuda.synchronize(dev)
+            t0 = _t.perf_counter()
+            plan = qb.Plan(d, N, m, "c128")
+            x = host.to(dev, non_blocking=True)
+            plan.step(x, t, stream)
+            plan.observables(x, stream)
+            torch.cuda.synchronize(dev)
+            el = _t.perf_counter() - t0
+            plan.close()
+            sample.append({"dim": d, "N": N, "t": t, "site_steps": sites * t, "seconds": el})
+            xs.append(sites * t)
+            ys.append(el)
+        A = np.vstack([np.ones(len(xs)), np.array(xs, dtype=float)]).T
+        (c0, c1), *_ = np.linalg.lstsq(A, np.array(ys), rcond=None)
+        fit[d] = {"fixed_s": max(float(c0), 0.0), "site_steps_per_s": 1.0 / float(c1) if c1 > 0 else float("inf")}
+    return {"sample": sample, "fit": fit, "max_site_steps": max_site_steps}
 
 
 def _drain(qb, srv, tickets):

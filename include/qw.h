@@ -23,7 +23,10 @@
  * Element type: QW_C64 = two float32 (8 bytes), QW_C128 = two float64 (16 bytes).
  * Field pointers are DEVICE pointers (cudaMalloc / torch CUDA tensors) unless a
  * name says _host; they must be aligned to the element size and hold
- * qw_plan_field_elems(plan) elements.  The caller owns them.
+ * qw_plan_field_elems(plan) elements.  The caller owns them.  Kernels that move
+ * 16-byte vectors (the VEC/TMA/TMA2 stencils, paired projections) run only on
+ * 16-byte aligned fields; a complex64 field that is merely 8-byte aligned gets
+ * the scalar kernels (same results).
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  * stream).  Calls are asynchronous on that stream unless stated otherwise.
  * Errors: every call returns a qw_status and never aborts; a failed CUDA call
@@ -58,8 +61,8 @@ typedef enum { QW_C64 = 0, QW_C128 = 1 } qw_dtype;
  * complex64, N/2 % 64 == 0; two cells per thread, 16-byte loads.  TMA: BCC,
  * complex64, N/2 % 64 == 0; z-marching CTAs with TMA-staged shared-memory tiles.
  * TMA2: as TMA with two steps fused per pass over HBM (temporal fusion; an odd
- * remaining step runs as TMA).  AUTO restores the default order
- * TMA > TMA2 > VEC > PLAIN; qw_plan_autotune measures and keeps the fastest. */
+ * remaining step runs as TMA).  AUTO restores the default: the first supported
+ * of TMA2 > TMA > VEC > PLAIN; qw_plan_autotune measures and keeps the fastest. */
 typedef enum {
   QW_STENCIL_AUTO = 0,
   QW_STENCIL_PLAIN = 1,
@@ -344,12 +347,16 @@ qw_status qw_server_destroy(qw_server server);
  * every GPU loading libqw.so holds until the process exits; the kernel is the
  * VEC variant where it applies, else PLAIN (never the TMA variant).
  * The first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.
+ * device current) and caches it for the process; make that first call before
+ * any stream capture.  The cached address does not survive cudaDeviceReset:
+ * after a reset of a device, do not call qw_step_static on it again in the
+ * same process.  The device that is current, the stream's device and the
+ * field's device must be the same one (a stream of another device: QW_EINVAL).
  * All calls on a device share the one array, and it keeps the last call's
  * contents: calls whose work overlaps on the GPU (other streams, other host
  * threads) race on it and must be serialised by the caller.
- * Errors: QW_EINVAL (bad arguments, or a field larger than 64 MiB -- use a
- * plan for those), QW_ECUDA. */
+ * Errors: QW_EINVAL (bad arguments, a stream of another device, or a field
+ * larger than 64 MiB -- use a plan for those), QW_ECUDA. */
 qw_status qw_step_static(int dim, int64_t N, double mass, qw_dtype dtype, void* psi_dev, int64_t nsteps,
                          void* stream);
 

@@ -5,8 +5,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <set>
 #include <string>
+#include <tuple>
 
 #include "qw_internal.cuh"
 
@@ -26,6 +29,19 @@ void set_error(const char* fmt, ...) {
 qw_status cuda_fail(cudaError_t e, const char* what) {
   set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
   return e == cudaErrorMemoryAllocation ? QW_ENOMEM : QW_ECUDA;
+}
+
+qw_status smem_attr_once(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<const void*, int, int>> done;
+  int dev = 0;
+  QW_CHECK_CUDA(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(func, dev, bytes);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(key)) return QW_OK;
+  QW_CHECK_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert(key);
+  return QW_OK;
 }
 
 bool make_geometry(int dim, int64_t N, Geometry* g) {
@@ -220,19 +236,22 @@ qw_status qw_step(qw_plan p, void* psi, int64_t nsteps, void* stream) {
   qw_status st = use_device(p);
   if (st != QW_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the VEC, TMA and TMA2 kernels move 16-byte vectors: a complex64 field that is only
+  // 8-byte aligned (e.g. a view one element into an allocation) takes the PLAIN kernel
+  const int variant = aligned16(psi) ? p->stencil : QW_STENCIL_PLAIN;
   void* cur = psi;
   void* nxt = p->scratch;
   for (int64_t i = 0; i < nsteps;) {
     int done = 1;
-    if (p->stencil == QW_STENCIL_TMA2 && nsteps - i >= 2) {
+    if (variant == QW_STENCIL_TMA2 && nsteps - i >= 2) {
       st = launch_step_tma2(p->g, p->n, p->mass, cur, nxt, p->tma2_items, p->tma2_nitems, p->dev_flags,
                             p->dev_flags + 1, s);
       done = 2;
-    } else if (p->stencil == QW_STENCIL_TMA || p->stencil == QW_STENCIL_TMA2) {
+    } else if (variant == QW_STENCIL_TMA || variant == QW_STENCIL_TMA2) {
       st = launch_step_tma(p->g, p->n, p->mass, cur, nxt, p->tma_items, p->tma_nitems, p->dev_flags,
                            p->dev_flags + 1, s);
     } else {
-      st = launch_step(p->g, p->dtype, p->stencil, p->n, p->mass, cur, nxt, s);
+      st = launch_step(p->g, p->dtype, variant, p->n, p->mass, cur, nxt, s);
     }
     if (st != QW_OK) return st;
     void* t = cur;

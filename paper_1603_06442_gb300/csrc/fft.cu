@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <vector>
 
 #include "qw_fft.cuh"
@@ -263,7 +264,6 @@ static qw_status launch_2f(const FftPass& p, void* data, const void* src, cudaSt
   using V = typename Cx<T>::t;
   constexpr int L = R1 * R2, TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
   const size_t smem = (size_t)L * ((C % 2 == 0) ? C + 1 : C) * sizeof(V);
-  static bool attr[2] = {false, false};
   const int64_t nlines = p.O * p.S;
   const int64_t grid = (nlines + C - 1) / C;
   if (grid > 0x7fffffff) {
@@ -271,20 +271,14 @@ static qw_status launch_2f(const FftPass& p, void* data, const void* src, cudaSt
     return QW_EINVAL;
   }
   if (p.S == 1) {
-    if (!attr[0]) {
-      QW_CHECK_CUDA(cudaFuncSetAttribute(fft2f_kernel<T, INV, R1, R2, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr[0] = true;
-    }
+    const qw_status sa = smem_attr(fft2f_kernel<T, INV, R1, R2, true>, (int)smem);
+    if (sa != QW_OK) return sa;
     fft2f_kernel<T, INV, R1, R2, true><<<(unsigned)grid, 256, smem, st>>>(
         static_cast<V*>(data), static_cast<const V*>(src), p, static_cast<const V*>(p.tw_line), static_cast<const V*>(p.tw_hi),
         static_cast<const V*>(p.tw_lo));
   } else {
-    if (!attr[1]) {
-      QW_CHECK_CUDA(cudaFuncSetAttribute(fft2f_kernel<T, INV, R1, R2, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr[1] = true;
-    }
+    const qw_status sa = smem_attr(fft2f_kernel<T, INV, R1, R2, false>, (int)smem);
+    if (sa != QW_OK) return sa;
     fft2f_kernel<T, INV, R1, R2, false><<<(unsigned)grid, 256, smem, st>>>(
         static_cast<V*>(data), static_cast<const V*>(src), p, static_cast<const V*>(p.tw_line), static_cast<const V*>(p.tw_hi),
         static_cast<const V*>(p.tw_lo));
@@ -383,27 +377,92 @@ static bool split_axis(int64_t L, int maxline, std::vector<int>* parts) {
   return !parts->empty();
 }
 
-template <typename T>
-static void host_table(std::vector<typename Cx<T>::t>* out, int64_t N, int64_t count, int64_t mult) {
-  out->resize(count);
-  for (int64_t m = 0; m < count; ++m) {
-    // exp(-2 pi i (m * mult mod N) / N), exact integer reduction before the angle
-    const int64_t e = (m * mult) % N;
-    const double ang = -2.0 * M_PI * (double)e / (double)N;
-    (*out)[m].x = (T)std::cos(ang);
-    (*out)[m].y = (T)std::sin(ang);
+// ---------------------------------------------------------------- tables
+// Every table of a plan holds (cos a, sin a) of the angles a_m, m < count:
+//   a_m = m * step                            (step != 0: the anchors of the omega refinement)
+//   a_m = sign * 2 pi ((m * mult) mod P) / P  (otherwise; exact integer reduction first)
+// stored as float2, double2, or float4 double-float pairs (cos hi, cos lo, sin hi, sin lo).
+enum TableKind { TAB_F2 = 0, TAB_D2 = 1, TAB_DF4 = 2 };
+struct TableSpec {
+  int kind;
+  int64_t count, mult, period;
+  double step, sign;
+};
+
+static size_t table_elem_bytes(int kind) { return kind == TAB_F2 ? 8 : 16; }
+
+__host__ __device__ inline double table_angle(const TableSpec& sp, int64_t m) {
+  if (sp.step != 0.0) return (double)m * sp.step;
+  const int64_t e = (m * sp.mult) % sp.period;
+  return sp.sign * 2.0 * 3.14159265358979323846 * (double)e / (double)sp.period;
+}
+
+__host__ __device__ inline void table_store(const TableSpec& sp, void* out, int64_t m, double c, double s) {
+  if (sp.kind == TAB_F2) {
+    static_cast<float2*>(out)[m] = make_float2((float)c, (float)s);
+  } else if (sp.kind == TAB_D2) {
+    static_cast<double2*>(out)[m] = make_double2(c, s);
+  } else {  // hi = RN(v), lo = RN(v - hi)
+    const float ch = (float)c, sh = (float)s;
+    static_cast<float4*>(out)[m] = make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
   }
 }
 
-template <typename T>
-static qw_status upload(const std::vector<typename Cx<T>::t>& h, void** dev) {
-  QW_CHECK_CUDA(cudaMalloc(dev, h.size() * sizeof(h[0])));
-  QW_CHECK_CUDA(cudaMemcpy(*dev, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice));
+__global__ void table_kernel(TableSpec sp, void* out) {
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < sp.count;
+       m += (int64_t)gridDim.x * blockDim.x) {
+    const double a = table_angle(sp, m);
+    table_store(sp, out, m, cos(a), sin(a));
+  }
+}
+
+// One table into *dev.  dst == nullptr: computed on the host and copied into a cudaMalloc'd
+// buffer (synchronous).  Otherwise carved from the caller's region (256-byte aligned) and
+// generated on the device on dst->st (asynchronous, no allocation); with dst->base == nullptr
+// only the bytes are counted.
+static qw_status make_table(TableDst* dst, const TableSpec& sp, void** dev) {
+  const size_t bytes = (size_t)sp.count * table_elem_bytes(sp.kind);
+  if (!dst) {
+    std::vector<unsigned char> h(bytes);
+    for (int64_t m = 0; m < sp.count; ++m) {
+      const double a = table_angle(sp, m);
+      table_store(sp, h.data(), m, std::cos(a), std::sin(a));
+    }
+    QW_CHECK_CUDA(cudaMalloc(dev, bytes));
+    QW_CHECK_CUDA(cudaMemcpy(*dev, h.data(), bytes, cudaMemcpyHostToDevice));
+    return QW_OK;
+  }
+  const size_t off = (dst->used + 255) & ~size_t(255);
+  dst->used = off + bytes;
+  if (!dst->base) {
+    *dev = nullptr;
+    return QW_OK;
+  }
+  if (dst->used > dst->cap) {
+    set_error("FFT tables need more than the %zu bytes given", dst->cap);
+    return QW_ENOMEM;
+  }
+  *dev = dst->base + off;
+  const int64_t blocks = std::min<int64_t>((sp.count + 255) / 256, 4096);
+  table_kernel<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, dst->st>>>(sp, *dev);
+  QW_CHECK_LAUNCH("table kernel launch");
   return QW_OK;
 }
 
+static TableSpec cis_spec(int kind, int64_t count, int64_t mult, int64_t period, double sign) {
+  TableSpec sp;
+  sp.kind = kind;
+  sp.count = count;
+  sp.mult = mult;
+  sp.period = period;
+  sp.step = 0.0;
+  sp.sign = sign;
+  return sp;
+}
+
 template <typename T>
-static qw_status build_pass(FftPass* p, int L, int64_t S, int64_t O, int64_t tw_N, int64_t tw_div, bool twiddle) {
+static qw_status build_pass(FftPass* p, int L, int64_t S, int64_t O, int64_t tw_N, int64_t tw_div, bool twiddle,
+                            TableDst* dst) {
   p->L = L;
   p->S = S;
   p->O = O;
@@ -429,25 +488,22 @@ static qw_status build_pass(FftPass* p, int L, int64_t S, int64_t O, int64_t tw_
   p->tw_N = tw_N;
   p->tw_div = tw_div;
   p->tlo_bits = 12;
-  // per-line table omega_L^m, and the two-level table of omega_{tw_N}
-  std::vector<typename Cx<T>::t> h;
-  host_table<T>(&h, L, L, 1);
-  qw_status st = upload<T>(h, &p->tw_line);
+  // per-line table omega_L^m = exp(-2 pi i m / L), and the two-level table of omega_{tw_N}
+  const int kind = sizeof(T) == 4 ? TAB_F2 : TAB_D2;
+  qw_status st = make_table(dst, cis_spec(kind, L, 1, L, -1.0), &p->tw_line);
   if (st != QW_OK) return st;
   if (twiddle) {
     const int64_t T_lo = int64_t(1) << p->tlo_bits;
-    host_table<T>(&h, tw_N, T_lo, 1);
-    st = upload<T>(h, &p->tw_lo);
+    st = make_table(dst, cis_spec(kind, T_lo, 1, tw_N, -1.0), &p->tw_lo);
     if (st != QW_OK) return st;
-    host_table<T>(&h, tw_N, (tw_N + T_lo - 1) / T_lo, T_lo);
-    st = upload<T>(h, &p->tw_hi);
+    st = make_table(dst, cis_spec(kind, (tw_N + T_lo - 1) / T_lo, T_lo, tw_N, -1.0), &p->tw_hi);
     if (st != QW_OK) return st;
   }
   return QW_OK;
 }
 
 template <typename T>
-static qw_status fft_plan_t(FftPlan* f, const Geometry& g) {
+static qw_status fft_plan_t(FftPlan* f, const Geometry& g, TableDst* dst) {
   const int maxline = (sizeof(T) == 4) ? kMaxLineF32 : kMaxLineF64;
   f->npass = 0;
   const int P = g.ncoset * g.s;
@@ -480,7 +536,7 @@ static qw_status fft_plan_t(FftPlan* f, const Geometry& g) {
       const int64_t stride = seg / Lq;
       const int64_t O = outer_total * before;
       const bool tw = (q + 1 < parts.size());
-      qw_status st = build_pass<T>(&f->pass[f->npass], (int)Lq, stride, O, seg / base, base, tw);
+      qw_status st = build_pass<T>(&f->pass[f->npass], (int)Lq, stride, O, seg / base, base, tw, dst);
       if (st != QW_OK) return st;
       f->npass++;
       seg = stride;
@@ -491,8 +547,9 @@ static qw_status fft_plan_t(FftPlan* f, const Geometry& g) {
   return QW_OK;
 }
 
-static qw_status trig_tables(FftPlan* f, const Geometry& g) {
+static qw_status trig_tables(FftPlan* f, const Geometry& g, TableDst* dst) {
   const int64_t ext[3] = {g.nx, g.ny, g.nz};
+  qw_status st;
   for (int ax = 0; ax < g.dim; ++ax) {
     int64_t len, period;  // angle = 2 pi q / period for q < len
     if (g.dim == 1) {
@@ -506,83 +563,52 @@ static qw_status trig_tables(FftPlan* f, const Geometry& g) {
       len = ext[ax];
       period = 2 * ext[ax];
     }
-    std::vector<double2> h(len);
-    std::vector<float2> h32(len);
-    for (int64_t q = 0; q < len; ++q) {
-      const double ang = 2.0 * M_PI * (double)(q % period) / (double)period;
-      h[q].x = std::cos(ang);
-      h[q].y = std::sin(ang);
-      h32[q].x = (float)h[q].x;
-      h32[q].y = (float)h[q].y;
-    }
-    QW_CHECK_CUDA(cudaMalloc(&f->trig[ax], len * sizeof(double2)));
-    QW_CHECK_CUDA(cudaMemcpy(f->trig[ax], h.data(), len * sizeof(double2), cudaMemcpyHostToDevice));
-    QW_CHECK_CUDA(cudaMalloc(&f->trig32[ax], len * sizeof(float2)));
-    QW_CHECK_CUDA(cudaMemcpy(f->trig32[ax], h32.data(), len * sizeof(float2), cudaMemcpyHostToDevice));
+    if ((st = make_table(dst, cis_spec(TAB_D2, len, 1, period, 1.0), &f->trig[ax])) != QW_OK) return st;
+    if ((st = make_table(dst, cis_spec(TAB_F2, len, 1, period, 1.0), &f->trig32[ax])) != QW_OK) return st;
   }
-  std::vector<double2> ha(kAngleTab + 1);
-  for (int j = 0; j <= kAngleTab; ++j) {
-    const double th = (double)j * kAngleStep;  // the same product the device forms
-    ha[j].x = std::cos(th);
-    ha[j].y = std::sin(th);
-  }
-  QW_CHECK_CUDA(cudaMalloc(&f->angle, ha.size() * sizeof(double2)));
-  QW_CHECK_CUDA(cudaMemcpy(f->angle, ha.data(), ha.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  // anchors theta_j = j * kAngleStep, j <= kAngleTab (the same product the device forms)
+  TableSpec anchors = cis_spec(TAB_D2, kAngleTab + 1, 1, 1, 1.0);
+  anchors.step = kAngleStep;
+  if ((st = make_table(dst, anchors, &f->angle)) != QW_OK) return st;
   // double-float tables: hi = RN(v), lo = RN(v - hi)
-  auto df4 = [](double c, double s) {
-    float4 r;
-    r.x = (float)c;
-    r.y = (float)(c - (double)r.x);
-    r.z = (float)s;
-    r.w = (float)(s - (double)r.z);
-    return r;
-  };
-  auto upload4 = [](const std::vector<float4>& h, void** dev) -> qw_status {
-    QW_CHECK_CUDA(cudaMalloc(dev, h.size() * sizeof(float4)));
-    QW_CHECK_CUDA(cudaMemcpy(*dev, h.data(), h.size() * sizeof(float4), cudaMemcpyHostToDevice));
-    return QW_OK;
-  };
-  qw_status st;
   if (g.dim == 1) {
+    // the chain in two levels: angle 2 pi (kDfFine q1 + q0) / N
     const int64_t N = g.nx, B = kDfFine, nc = (N + B - 1) / B;
-    std::vector<float4> fine(B), coarse(nc);
-    for (int64_t q = 0; q < B; ++q) {
-      const double ang = 2.0 * M_PI * (double)(q % N) / (double)N;
-      fine[q] = df4(std::cos(ang), std::sin(ang));
-    }
-    for (int64_t q = 0; q < nc; ++q) {
-      const double ang = 2.0 * M_PI * (double)((q * B) % N) / (double)N;
-      coarse[q] = df4(std::cos(ang), std::sin(ang));
-    }
-    if ((st = upload4(fine, &f->trigdf[0])) != QW_OK) return st;
-    if ((st = upload4(coarse, &f->trigdf[1])) != QW_OK) return st;
+    if ((st = make_table(dst, cis_spec(TAB_DF4, B, 1, N, 1.0), &f->trigdf[0])) != QW_OK) return st;
+    if ((st = make_table(dst, cis_spec(TAB_DF4, nc, B, N, 1.0), &f->trigdf[1])) != QW_OK) return st;
   } else {
     for (int ax = 0; ax < (g.dim == 2 ? 1 : 3); ++ax) {
       // the same angles as trig[ax]: 2D pi q / N (q < 2N), BCC pi q / M (q < M)
       const int64_t len = g.dim == 2 ? 2 * g.nx : ext[ax];
       const int64_t period = g.dim == 2 ? 2 * g.nx : 2 * ext[ax];
-      std::vector<float4> h(len);
-      for (int64_t q = 0; q < len; ++q) {
-        const double ang = 2.0 * M_PI * (double)(q % period) / (double)period;
-        h[q] = df4(std::cos(ang), std::sin(ang));
-      }
-      if ((st = upload4(h, &f->trigdf[ax])) != QW_OK) return st;
+      if ((st = make_table(dst, cis_spec(TAB_DF4, len, 1, period, 1.0), &f->trigdf[ax])) != QW_OK) return st;
     }
   }
-  std::vector<float4> hd(kAngleTab + 1);
-  for (int j = 0; j <= kAngleTab; ++j) hd[j] = df4(ha[j].x, ha[j].y);
-  return upload4(hd, &f->angdf);
+  anchors.kind = TAB_DF4;
+  return make_table(dst, anchors, &f->angdf);
 }
 
-qw_status fft_plan_create(FftPlan* f, const Geometry& g, qw_dtype dt) {
+qw_status fft_plan_create(FftPlan* f, const Geometry& g, qw_dtype dt, TableDst* dst) {
   *f = FftPlan();
   f->dtype = dt;
-  qw_status st = dt == QW_C64 ? fft_plan_t<float>(f, g) : fft_plan_t<double>(f, g);
+  f->external_tables = dst != nullptr;
+  qw_status st = dt == QW_C64 ? fft_plan_t<float>(f, g, dst) : fft_plan_t<double>(f, g, dst);
   if (st != QW_OK) return st;
-  return trig_tables(f, g);
+  return trig_tables(f, g, dst);
+}
+
+size_t fft_plan_table_bytes(const Geometry& g, qw_dtype dt) {
+  TableDst count;  // base == nullptr: count only
+  FftPlan f;
+  if (fft_plan_create(&f, g, dt, &count) != QW_OK) return 0;
+  return count.used;
 }
 
 void fft_plan_destroy(FftPlan* f) {
+  if (f->external_tables) {  // the tables live in the caller's region
+    *f = FftPlan();
+    return;
+  }
   for (int a = 0; a < 3; ++a) {
     if (f->trig[a]) cudaFree(f->trig[a]);
     if (f->trig32[a]) cudaFree(f->trig32[a]);
@@ -614,12 +640,8 @@ static qw_status run_pass(const FftPass& p, void* data, cudaStream_t st, const v
     const size_t bytes = (size_t)(p.O * p.S) * p.L * sizeof(V);
     QW_CHECK_CUDA(cudaMemcpyAsync(data, src, bytes, cudaMemcpyDeviceToDevice, st));
   }
-  static bool attr[2] = {false, false};
-  if (!attr[INV]) {
-    QW_CHECK_CUDA(cudaFuncSetAttribute(fft_pass_kernel<T, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kFftSmemBytes + 64));
-    attr[INV] = true;
-  }
+  const qw_status sa = smem_attr(fft_pass_kernel<T, INV>, kFftSmemBytes + 64);
+  if (sa != QW_OK) return sa;
   const int64_t nlines = p.O * p.S;
   const int64_t grid = (nlines + p.C - 1) / p.C;
   if (grid > 0x7fffffff) {

@@ -212,7 +212,9 @@ __global__ void __launch_bounds__(256) proj_fold_kernel(const double* __restrict
 constexpr int64_t kProjThreads = int64_t(1) << 18;
 constexpr int64_t kProjWarps = kProjThreads / 32;
 
-ProjGeo make_proj(const Geometry& g, int keep, qw_dtype dt) {
+// al16: the field is 16-byte aligned (complex64 pairs of x are loaded as one vector).  The
+// partial count with al16 = true bounds the one without (pairs halve the work units).
+ProjGeo make_proj(const Geometry& g, int keep, qw_dtype dt, bool al16 = true) {
   ProjGeo p{};
   p.dim = g.dim;
   p.s = g.s;
@@ -231,7 +233,7 @@ ProjGeo make_proj(const Geometry& g, int keep, qw_dtype dt) {
   p.n_orows = (int64_t)p.ncos * p.oz * p.oy;
   p.rrows = (int64_t)(p.kz ? 1 : p.nz) * p.ry;
   p.nout = p.n_orows * (p.kx ? p.nx : 1);
-  p.pair = (p.kx && dt == QW_C64 && p.nx % 2 == 0) ? 1 : 0;
+  p.pair = (p.kx && dt == QW_C64 && p.nx % 2 == 0 && al16) ? 1 : 0;
   const int64_t units = p.kx ? (p.pair ? p.nout / 2 : p.nout) : p.n_orows;
   const int64_t want = p.kx ? kProjThreads : kProjWarps;
   int64_t k = (want + units - 1) / units;
@@ -257,7 +259,7 @@ int64_t projection_outputs(const Geometry& g, int keep) {
 
 qw_status launch_projection(const Geometry& g, qw_dtype dt, const void* psi, int keep, double* out,
                             double* partials, cudaStream_t st) {
-  const ProjGeo p = make_proj(g, keep, dt);
+  const ProjGeo p = make_proj(g, keep, dt, aligned16(psi));
   const int kept = p.kx + p.ky + p.kz;
   // BCC: physical points of mixed coordinate parity are not sites (two or more kept axes)
   if (g.dim == 3 && kept >= 2)

@@ -60,6 +60,17 @@ struct FftPlan {
   // from trigdf[1][q1] (coarse) and trigdf[0][q0] (fine).
   void* trigdf[3] = {nullptr, nullptr, nullptr};
   void* angdf = nullptr;
+  bool external_tables = false;  // tables carved from a caller's region (not freed here)
+};
+
+// Destination of a plan's tables when they are not cudaMalloc'd: a region of device
+// memory owned by the caller, filled in order on `st` by a table kernel (no allocation,
+// no host work, asynchronous).  base == nullptr counts the bytes only.
+struct TableDst {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  cudaStream_t st = nullptr;
 };
 
 constexpr int kDfFine = 4096;
@@ -68,7 +79,10 @@ constexpr int kAngleTab = 1024;
 constexpr double kAngleStep = 3.14159265358979323846 / kAngleTab;
 
 bool fft_size_ok(int64_t L);
-qw_status fft_plan_create(FftPlan* f, const Geometry& g, qw_dtype dt);
+// dst == nullptr: tables cudaMalloc'd and computed on the host (synchronous).
+qw_status fft_plan_create(FftPlan* f, const Geometry& g, qw_dtype dt, TableDst* dst = nullptr);
+// Device bytes of a plan's tables in a TableDst region (0 if the geometry has no plan).
+size_t fft_plan_table_bytes(const Geometry& g, qw_dtype dt);
 void fft_plan_destroy(FftPlan* f);
 // Forward over all axes (x, then y, then z) / inverse (z, y, x); unnormalised.
 qw_status fft_forward(const FftPlan& f, int dim, void* data, cudaStream_t st);

@@ -15,6 +15,15 @@ namespace qw {
 void set_error(const char* fmt, ...);
 qw_status cuda_fail(cudaError_t e, const char* what);
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device, once
+// per (kernel, device, bytes).  Thread-safe: the server's scheduler thread and callers'
+// threads launch the same kernels, possibly on different devices.
+qw_status smem_attr_once(const void* func, int bytes);
+template <typename K>
+inline qw_status smem_attr(K* kernel, int bytes) {
+  return smem_attr_once(reinterpret_cast<const void*>(kernel), bytes);
+}
+
 #define QW_CHECK_CUDA(call)                                        \
   do {                                                             \
     cudaError_t qw_e_ = (call);                                    \
@@ -47,6 +56,10 @@ struct Geometry {
 };
 
 bool make_geometry(int dim, int64_t N, Geometry* g);
+
+// Fields need only element alignment (8 bytes in complex64); kernels that move 16-byte
+// vectors are chosen only for fields that are 16-byte aligned.
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Mass coefficients of one step.  With the Weyl sums S carrying the factor 4
 // of the +-1 +- i entries, one output is  nq * S + i m * psi_other  with

@@ -666,12 +666,8 @@ qw_status launch_fused(const Geometry& g, const SpecAxes& ax, double n, double m
   const int64_t nrows = g.vol / L;
   const int64_t grid = (nrows + RW - 1) / RW;
   const size_t smem = (size_t)L * CP * sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    QW_CHECK_CUDA(cudaFuncSetAttribute(fused_x_kernel<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-    attr = true;
-  }
+  const qw_status sa = smem_attr(fused_x_kernel<R1, R2>, (int)smem);
+  if (sa != QW_OK) return sa;
   fused_x_kernel<R1, R2><<<(unsigned)grid, 256, smem, st>>>(
       g.dim, to_dev(ax), g.vol, make_mass(n, m), omega, make_time(t), (float)(1.0 / (double)g.vol), norm0,
       static_cast<float2*>(psi), static_cast<const float2*>(tw_line));
@@ -767,12 +763,8 @@ qw_status launch_weights_x(const Geometry& g, const SpecAxes& ax, double n, doub
   constexpr int L = R1 * R2, TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
   constexpr int CP = (C % 2 == 0) ? C + 1 : C;
   const size_t smem = (size_t)L * CP * sizeof(float2);
-  static bool attr = false;
-  if (!attr) {
-    QW_CHECK_CUDA(cudaFuncSetAttribute(weights_x_kernel<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem));
-    attr = true;
-  }
+  const qw_status sa = smem_attr(weights_x_kernel<R1, R2>, (int)smem);
+  if (sa != QW_OK) return sa;
   weights_x_kernel<R1, R2><<<(unsigned)fused_x_ctas<R1, R2>(g), 256, smem, st>>>(
       g.dim, to_dev(ax), g.vol, make_mass(n, m), static_cast<const float2*>(data),
       static_cast<const float2*>(tw_line), partials);

@@ -6,6 +6,9 @@
 //   * admission: the head of the FIFO is admitted as soon as an execution slot
 //     (a CUDA stream) is free and its fields fit in the device pool, whose size
 //     is the server's HBM budget (allocated once: the loop never calls cudaMalloc);
+//     the FFT tables of each box size are carved from the same pool (generated on
+//     the device, counted in bytes_in_use), cached while the pool has room, and
+//     evicted least recently used first when an admission needs the space;
 //   * an admitted request runs on its slot's stream: initial state (Gaussian
 //     packet built on the device, or the caller's field copied at submit), its
 //     norm, forward FFT, D_k^t (normalised; omega_k in FP64 inside the kernel),
@@ -95,6 +98,16 @@ struct Request {
   Clock::time_point t_submit;
   Geometry g;
   size_t bytes_field = 0, bytes_omega = 0;
+  size_t bytes_tables = 0;  // FFT tables of this box size, if not cached at admission
+};
+
+// FFT plan of one box size whose tables live in the pool.
+struct CachedFft {
+  FftPlan plan;
+  size_t off = 0, bytes = 0;
+  int users = 0;              // admitted requests using it
+  uint64_t last_use = 0;
+  cudaEvent_t ready = nullptr;  // recorded after the table kernels on the creating stream
 };
 
 struct Slot {
@@ -106,6 +119,7 @@ struct Slot {
   bool busy = false;
   std::unique_ptr<Request> r;
   size_t off = 0, bytes = 0;
+  CachedFft* fft = nullptr;
 };
 
 struct Result {
@@ -133,7 +147,8 @@ struct qw_server_s {
   uint64_t next_ticket = 1;
   bool stop = false;
   std::thread worker;
-  std::map<std::pair<int, int64_t>, std::unique_ptr<FftPlan>> ffts;  // per geometry (complex64)
+  std::map<std::pair<int, int64_t>, std::unique_ptr<CachedFft>> ffts;  // per box size (complex64)
+  uint64_t use_clock = 0;
   uint64_t admitted = 0, completed = 0;
 };
 
@@ -145,22 +160,68 @@ static size_t request_bytes(const Geometry& g, size_t* field, size_t* omega) {
   return ((*field + 255) & ~size_t(255)) + ((*omega + 255) & ~size_t(255));
 }
 
-static FftPlan* fft_for(qw_server_s* S, const Geometry& g, qw_status* st) {
-  auto key = std::make_pair(g.dim, g.N);
+// Drop the least recently used cached plan that no admitted request uses (not `keep`);
+// false if there is none.  Called with the server lock held.
+static bool evict_one_fft(qw_server_s* S, const CachedFft* keep) {
+  auto victim = S->ffts.end();
+  for (auto it = S->ffts.begin(); it != S->ffts.end(); ++it) {
+    if (it->second->users > 0 || it->second.get() == keep) continue;
+    if (victim == S->ffts.end() || it->second->last_use < victim->second->last_use) victim = it;
+  }
+  if (victim == S->ffts.end()) return false;
+  S->pool.release(victim->second->off, victim->second->bytes);
+  if (victim->second->ready) cudaEventDestroy(victim->second->ready);
+  S->ffts.erase(victim);
+  return true;
+}
+
+// Pool space for the head request: its field, plus its box size's FFT tables when they
+// are not cached.  Evicts idle cached plans while the pool is short.  On success the
+// slot holds the field's offset and the plan (created, tables generated on the slot's
+// stream, when new); false leaves the request pending.  Called with the server lock held.
+static bool admit_memory(qw_server_s* S, Request& R, Slot& sl, qw_status* st) {
+  *st = QW_OK;
+  const auto key = std::make_pair(R.g.dim, R.g.N);
   auto it = S->ffts.find(key);
-  if (it != S->ffts.end()) {
-    *st = QW_OK;
-    return it->second.get();
+  CachedFft* cf = it == S->ffts.end() ? nullptr : it->second.get();
+  const size_t need = R.bytes_field + R.bytes_omega + 512;
+  size_t off = 0, toff = 0;
+  for (;;) {
+    if (S->pool.alloc(need, &off)) {
+      if (cf || S->pool.alloc(R.bytes_tables, &toff)) break;
+      S->pool.release(off, need);
+    }
+    if (!evict_one_fft(S, cf)) return false;
   }
-  std::unique_ptr<FftPlan> f(new FftPlan());
-  *st = fft_plan_create(f.get(), g, QW_C64);
-  if (*st != QW_OK) {
-    fft_plan_destroy(f.get());
-    return nullptr;
+  if (!cf) {
+    std::unique_ptr<CachedFft> c(new (std::nothrow) CachedFft());
+    cudaError_t e = c ? cudaEventCreateWithFlags(&c->ready, cudaEventDisableTiming) : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) {
+      TableDst dst;
+      dst.base = static_cast<char*>(S->pool_base) + toff;
+      dst.cap = R.bytes_tables;
+      dst.st = sl.stream;
+      *st = fft_plan_create(&c->plan, R.g, QW_C64, &dst);
+      if (*st == QW_OK) e = cudaEventRecord(c->ready, sl.stream);
+    }
+    if (e != cudaSuccess && *st == QW_OK) *st = cuda_fail(e, "served request: FFT tables");
+    if (*st != QW_OK) {
+      if (c && c->ready) cudaEventDestroy(c->ready);
+      S->pool.release(toff, R.bytes_tables);
+      S->pool.release(off, need);
+      return true;  // admitted as failed: the caller finishes it with *st
+    }
+    c->off = toff;
+    c->bytes = R.bytes_tables;
+    cf = c.get();
+    S->ffts[key] = std::move(c);
   }
-  FftPlan* raw = f.get();
-  S->ffts[key] = std::move(f);
-  return raw;
+  cf->users++;
+  cf->last_use = ++S->use_clock;
+  sl.fft = cf;
+  sl.off = off;
+  sl.bytes = need;
+  return true;
 }
 
 // Enqueue the whole request on the slot's stream.
@@ -172,8 +233,9 @@ static qw_status launch_request(qw_server_s* S, Slot& sl) {
   void* psi = base;
   const double m = R.req.mass, n = std::sqrt(1.0 - m * m);
   qw_status st;
-  FftPlan* f = fft_for(S, g, &st);
-  if (!f) return st;
+  const FftPlan* f = &sl.fft->plan;
+  // tables generated on another slot's stream must be complete first
+  QW_CHECK_CUDA(cudaStreamWaitEvent(s, sl.fft->ready, 0));
   const SpecAxes ax = spec_axes(g, *f);
   if (!R.psi0.empty()) {
     QW_CHECK_CUDA(cudaMemcpyAsync(psi, R.psi0.data(), R.bytes_field, cudaMemcpyHostToDevice, s));
@@ -212,12 +274,15 @@ static void finish_slot(qw_server_s* S, Slot& sl, qw_status st) {
     res.state = T_FAILED;
     res.error = qw_last_error();
   }
-  S->pool.release(sl.off, sl.bytes);
   {
     std::lock_guard<std::mutex> lock(S->mu);
+    if (sl.bytes) S->pool.release(sl.off, sl.bytes);
+    if (sl.fft) sl.fft->users--;
     S->results[R.ticket] = res;
     S->completed++;
   }
+  sl.fft = nullptr;
+  sl.bytes = 0;
   sl.r.reset();
   sl.busy = false;
 }
@@ -244,23 +309,20 @@ static void worker_loop(qw_server_s* S) {
         }
       if (!free_slot) break;
       std::unique_ptr<Request> r;
+      qw_status st = QW_OK;
       {
         std::lock_guard<std::mutex> lock(S->mu);
         if (S->pending.empty()) break;
-        const size_t need = S->pending.front()->bytes_field + S->pending.front()->bytes_omega + 512;
-        size_t off = 0;
-        if (!S->pool.alloc(need, &off)) break;
+        if (!admit_memory(S, *S->pending.front(), *free_slot, &st)) break;
         r = std::move(S->pending.front());
         S->pending.pop_front();
-        free_slot->off = off;
-        free_slot->bytes = need;
         S->results[r->ticket].state = T_RUNNING;
         S->admitted++;
       }
       idle = false;
       free_slot->r = std::move(r);
       free_slot->busy = true;
-      qw_status st = launch_request(S, *free_slot);
+      if (st == QW_OK) st = launch_request(S, *free_slot);
       if (st != QW_OK) {
         cudaStreamSynchronize(free_slot->stream);
         finish_slot(S, *free_slot, st);
@@ -337,7 +399,9 @@ qw_status qw_submit(qw_server S, const qw_request* req, uint64_t* ticket) {
     set_error("qw_submit: no field and no packet width");
     return QW_EINVAL;
   }
-  const size_t need = request_bytes(r->g, &r->bytes_field, &r->bytes_omega) + 512;
+  // the box size's FFT tables (host-side planning only; nothing touches the GPU here)
+  r->bytes_tables = fft_plan_table_bytes(r->g, QW_C64);
+  const size_t need = request_bytes(r->g, &r->bytes_field, &r->bytes_omega) + 512 + ((r->bytes_tables + 255) & ~size_t(255));
   if (need > S->budget) {
     set_error("qw_submit: request needs %zu bytes, more than the server's HBM budget of %zu", need, S->budget);
     return QW_EINVAL;
@@ -426,7 +490,10 @@ qw_status qw_server_destroy(qw_server S) {
     if (sl.d_part) cudaFree(sl.d_part);
     if (sl.h_res) cudaFreeHost(sl.h_res);
   }
-  for (auto& kv : S->ffts) fft_plan_destroy(kv.second.get());
+  for (auto& kv : S->ffts) {
+    fft_plan_destroy(&kv.second->plan);
+    if (kv.second->ready) cudaEventDestroy(kv.second->ready);
+  }
   if (S->pool_base) cudaFree(S->pool_base);
   delete S;
   return QW_OK;

@@ -176,23 +176,19 @@ __global__ void __launch_bounds__(NT, 2)
 
 }  // namespace zm
 
-static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-
-static qw_status get_encoder();
-
-PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() { return get_encoder() == QW_OK ? g_encode : nullptr; }
-
-static qw_status get_encoder() {
-  if (g_encode) return QW_OK;
+// The driver's tensor-map encoder, looked up once (thread-safe static initialisation).
+static PFN_cuTensorMapEncodeTiled_v12000 lookup_encoder() {
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
-    set_error("cuTensorMapEncodeTiled unavailable");
-    return QW_ECUDA;
-  }
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  return QW_OK;
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return nullptr;
+  return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 enc = lookup_encoder();
+  if (!enc) set_error("cuTensorMapEncodeTiled unavailable");
+  return enc;
 }
 
 bool tma_step_supported(const Geometry& g) {
@@ -226,27 +222,24 @@ std::vector<int4> tma_item_table(const Geometry& g, int resident, int ty) {
 
 qw_status launch_step_tma(const Geometry& g, double n, double m, const void* in, void* out, const int4* items,
                           int nitems, int* err, int* next_item, cudaStream_t st) {
-  qw_status s = get_encoder();
-  if (s != QW_OK) return s;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encoder();
+  if (!enc) return QW_ECUDA;
+  qw_status s;
   const int M = (int)g.nx;
   CUtensorMap map;
   cuuint64_t dims[4] = {(cuuint64_t)2 * M, (cuuint64_t)M, (cuuint64_t)M, 8};
   cuuint64_t strides[3] = {(cuuint64_t)2 * M * 4, (cuuint64_t)2 * M * M * 4, (cuuint64_t)2 * M * M * M * 4};
   cuuint32_t box[4] = {zm::ROWF, zm::BY, 1, 4};
   cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = g_encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(in), dims, strides, box, estr,
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(in), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
     return QW_ECUDA;
   }
-  static bool attr_done = false;
-  if (!attr_done) {
-    QW_CHECK_CUDA(cudaFuncSetAttribute(zm::step3d_c64_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       zm::SMEM_BYTES));
-    attr_done = true;
-  }
+  s = smem_attr(zm::step3d_c64_tma_kernel, zm::SMEM_BYTES);
+  if (s != QW_OK) return s;
   int dev = 0, nsm = 0;
   QW_CHECK_CUDA(cudaGetDevice(&dev));
   QW_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

@@ -378,12 +378,8 @@ qw_status launch_step_tma2(const Geometry& g, double n, double m, const void* in
     set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
     return QW_ECUDA;
   }
-  static bool attr_done = false;
-  if (!attr_done) {
-    QW_CHECK_CUDA(cudaFuncSetAttribute(zm2::step3d_c64_tma2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       zm2::SMEM2_BYTES));
-    attr_done = true;
-  }
+  const qw_status sa = smem_attr(zm2::step3d_c64_tma2_kernel, zm2::SMEM2_BYTES);
+  if (sa != QW_OK) return sa;
   int dev = 0, nsm = 0;
   QW_CHECK_CUDA(cudaGetDevice(&dev));
   QW_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

@@ -68,12 +68,23 @@ extern "C" qw_status qw_step_static(int dim, int64_t N, double mass, qw_dtype dt
   if (nsteps == 0) return QW_OK;
   int dev = 0;
   QW_CHECK_CUDA(cudaGetDevice(&dev));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the scratch address below belongs to the current device: the stream must too
+  int sdev = -1;
+  QW_CHECK_CUDA(cudaStreamGetDevice(s, &sdev));
+  if (sdev != dev) {
+    set_error("qw_step_static: the stream belongs to device %d but device %d is current; make the field's "
+              "and the stream's device current first",
+              sdev, dev);
+    return QW_EINVAL;
+  }
   void* scratch = nullptr;
   qw_status st = static_scratch(dev, &scratch);
   if (st != QW_OK) return st;
-  const int variant = stencil_supported(g, dtype, QW_STENCIL_VEC) ? QW_STENCIL_VEC : QW_STENCIL_PLAIN;
+  // VEC moves 16-byte vectors: only for 16-byte aligned fields (the scratch array is)
+  const int variant =
+      (stencil_supported(g, dtype, QW_STENCIL_VEC) && aligned16(psi)) ? QW_STENCIL_VEC : QW_STENCIL_PLAIN;
   const double n = std::sqrt(1.0 - mass * mass);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* cur = psi;
   void* nxt = scratch;
   for (int64_t i = 0; i < nsteps; ++i) {

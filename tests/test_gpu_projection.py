@@ -148,3 +148,25 @@ def test_projection_rejects_bad_masks(qb):
     assert qb.qw_projection_elems(plan.handle, 3) == 64
     assert qb.qw_projection_elems(plan.handle, 4) == -1
     plan.close()
+
+
+def test_misaligned_complex64_projection_matches_aligned(qb):
+    """The paired (16-byte) x projection is only used on 16-byte aligned complex64 fields;
+    an 8-byte aligned view gets the scalar kernel and the same sums."""
+    dim, N = 3, 64
+    a = inputs.random_field(dim, N, seed=12).astype(np.complex64)
+    plan = qb.Plan(dim, N, 0.1, "c64")
+    buf = torch.zeros(a.size + 1, dtype=torch.complex64, device="cuda")
+    x_off = buf[1:]
+    x_off.copy_(torch.from_numpy(a))
+    assert x_off.data_ptr() % 16 == 8
+    x = torch.from_numpy(a).cuda()
+    psi = walk.from_device(dim, N, a.astype(np.complex128))
+    for keep in (1, 3, 5, 7):
+        p_al = plan.projection(x, keep).cpu().numpy()
+        p_off = plan.projection(x_off, keep).cpu().numpy()
+        ref = expected(dim, psi, keep)
+        scale = np.abs(ref).max()
+        assert np.abs(p_off - ref).max() <= 2e-6 * scale, keep
+        assert np.abs(p_al - ref).max() <= 2e-6 * scale, keep
+    plan.close()

@@ -166,3 +166,26 @@ def test_refusals_and_queue_full(qb):
     with pytest.raises(qb.QwError):       # retired ticket
         qb.qw_poll(srv, tickets[0])
     qb.qw_server_destroy(srv)
+
+
+def test_fft_tables_in_the_pool_evicted_lru(qb):
+    """The FFT tables of each box size are carved from the server's pool and counted in its
+    budget; when an admission needs the room, idle tables are evicted least recently used
+    first, and a size whose tables were evicted gets them rebuilt with identical results.
+    1D boxes: A = 2^20 (field 16 MiB + tables ~24 MiB), B = 3^12, C = 3 * 2^19 (~60 MiB with
+    tables) in a 72 MiB pool: C must evict A's and B's tables, the second A must evict C's."""
+    budget = 72 << 20
+    srv = qb.qw_server_create(budget, slots=2, max_pending=16)
+    seq = [(1 << 20, 0.2, 777), (3 ** 12, 0.1, 55), (3 << 19, 0.3, 1234), (1 << 20, 0.2, 777)]
+    out = []
+    for N, m, t in seq:
+        tk = qb.qw_submit(srv, qb.make_request(1, N, m, t, x0=[N / 2], sigma=N / 64, k0=[0.3], chi=CHI[1]))
+        out.append(wait_all(qb, srv, [tk])[tk][0])
+        st = qb.qw_server_stats(srv)
+        assert st["running"] == 0 and 0 < st["bytes_in_use"] <= budget   # cached tables are counted
+    st = qb.qw_server_stats(srv)
+    qb.qw_server_destroy(srv)
+    assert st["peak_bytes"] <= budget
+    assert out[3] == out[0]     # rebuilt tables, same answer
+    for o in out:
+        assert abs(o["norm"] - 1.0) < 1e-5
