@@ -631,7 +631,7 @@ def batched_measurement(qb, dev, stream, runs=3, n_walks=256):
                                    [0.5, 0.5, 0.5j, -0.5j])
         fields.append(torch.from_numpy(a.astype(np.complex64)).to(dev))
     b = qb.Batch([(w["dim"], w["N"], w["mass"], w["t"], x) for w, x in zip(mix, fields)])
-    tile, budget, tuned_rate = b.autotune(rounds_cap=256, stream=stream)
+    best, tuned_rate = b.autotune(rounds_cap=256, stream=stream)
     site_steps = 0
     for w in mix:
         sites = w["N"] ** 2 if w["dim"] == 2 else w["N"] ** 3 // 4
@@ -653,9 +653,13 @@ def batched_measurement(qb, dev, stream, runs=3, n_walks=256):
     return {"walks": len(mix), "site_steps_per_run": site_steps, "ms_per_run": ms,
             "site_steps_per_s": rate, "algorithmic_GBps_at_64B": rate * 64 / 1e9,
             "frac_of_hbm_at_64B": rate * 64 / 1e9 / peak,
-            "note": "walks are grouped under the autotuned footprint budget; groups within an L2-sized "
-                    "budget run L2-resident, larger budgets trade that for more parallel tiles",
-            "autotuned_tile_sites": tile, "autotuned_l2_budget_MiB": budget / 2 ** 20,
+            "note": "one persistent launch; a round advances a tile by the autotuned fusion depth of its "
+                    "lattice (1: per-site update from HBM; >= 2: tile + halo in shared memory, one HBM read "
+                    "and write per round); algorithmic bytes are the unfused 64 B per site-step",
+            "autotuned_fusion_depth": {"1d": best["depth"][0], "2d": best["depth"][1], "bcc": best["depth"][2]},
+            "autotuned_box": {"2d": best["box"][1][:2], "bcc": best["box"][2]},
+            "autotuned_tile_sites": best["tile_sites"], "autotuned_l2_budget_MiB": best["l2_budget_bytes"] / 2 ** 20,
+            "autotune_rate_at_256_steps": tuned_rate,
             "max_norm_drift_after_%d_runs" % (runs + 1): worst_norm,
             "launches_per_run": 1, "graph": True}
 

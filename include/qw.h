@@ -134,9 +134,12 @@ qw_status qw_plan_autotune(qw_plan plan, void* stream, double* best_rate);
 qw_status qw_step(qw_plan plan, void* psi_dev, int64_t nsteps, void* stream);
 
 /* Build the spectral-path state of the plan: FFT pass plans and twiddle
- * tables, and the FP64 table of omega_k = atan2(sin omega_k, n u_k) (Sec. 3.2,
+ * tables, and the table of omega_k = atan2(sin omega_k, n u_k) (Sec. 3.2,
  * cos omega_k = n u_k) for every stored wave vector (one per site in 1D/2D,
- * two per cell on the BCC lattice: 8 bytes per site).  Synchronous; done
+ * two per cell on the BCC lattice): complex128 plans hold omega_k as a
+ * double-double (16 bytes per site, ~1e-31 accurate, so that the phase
+ * omega_k t keeps ~1e-16 at any t), complex64 plans omega_k / 2 pi as a pair of
+ * FP32 numbers (8 bytes per site).  Synchronous; done
  * implicitly by the first qw_evolve_spectral / qw_observables call.
  * Needs every axis length (N, or N/2 for dim 3) of the form 2^a 3^b.
  * Errors: QW_EINVAL (axis length not 2^a 3^b), QW_ENOMEM, QW_ECUDA. */
@@ -147,7 +150,8 @@ qw_status qw_plan_prepare_spectral(qw_plan plan);
  * per-wave-vector product with D_k^t = cos(omega_k t) I - i sin(omega_k t) G_k/sin(omega_k)
  * (D_k = cos(omega_k) I - i G_k, Sec. 3.2), with the BCC two-coset reduction of
  * Eqs. bcc-dft / bcc-idft, and the inverse DFT.  omega_k t is reduced modulo
- * 2 pi in FP64; the cost does not depend on t.  Asynchronous on `stream`
+ * 2 pi (complex128: from the double-double omega_k, so the phase keeps
+ * ~1e-16 at any t); the cost does not depend on t.  Asynchronous on `stream`
  * (after the first call's synchronous preparation).  Same result as t calls
  * of the update rule, up to rounding.
  * Errors: QW_EINVAL (null plan/pointer, t < 0, axis length not 2^a 3^b),
@@ -190,7 +194,7 @@ qw_status qw_fw_transform(qw_plan plan, const void* psi_dev, void* out_dev, void
  * Errors: QW_EINVAL (null argument), QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
 qw_status qw_position_moments(qw_plan plan, const void* psi_dev, double* out, void* stream);
 
-/* Probability projections (Sec. 5.3: the distribution of a localised state
+/* Probability projections (Sec. 5.2: the distribution of a localised state
  * projected onto axes and planes).  The density rho(x) = sum_s |psi_s(x)|^2 of
  * psi_dev, summed over the axes NOT named in `keep` (bit 0 = x, bit 1 = y,
  * bit 2 = z; only axes below dim; at least one), on the physical grid of the
@@ -229,8 +233,9 @@ qw_status qw_run_host(qw_plan plan, const void* const* psi_host, void* const* ps
 /* ---------------------------------------------------------------- batches
  * Many independent walks of uneven size advanced together by one persistent
  * kernel launch, replayed from a CUDA graph (complex64 only).  Each walk is the
- * update rule (Eq. upd-rule) applied t times to its own field, exactly as
- * qw_step with the PLAIN kernel would. */
+ * update rule (Eq. upd-rule) applied t times to its own field, with the same
+ * per-site arithmetic as qw_step's PLAIN kernel (bit-identical results, fused
+ * or not). */
 typedef struct {
   int dim;          /* 1, 2 or 3 */
   int64_t N;        /* box side (even for dim 3) */
@@ -243,25 +248,62 @@ typedef struct qw_batch_s* qw_batch;
 
 /* Create a batch over n walks (descriptors copied).  Allocates a partner
  * field per walk, the schedule tables and counters on the current device.
- * Errors: QW_EINVAL (bad descriptor), QW_ENOMEM, QW_ECUDA. */
+ * Default tiling: depth 2 on every lattice, boxes 1024, 32x16 and 8x8x4 cells,
+ * one group (16 GiB); qw_batch_autotune measures better ones.
+ * Errors: QW_EINVAL (bad descriptor, a walk of 2^31 complex values or more),
+ * QW_ENOMEM, QW_ECUDA. */
 qw_status qw_batch_create(const qw_walk* walks, int n, qw_batch* out);
 qw_status qw_batch_destroy(qw_batch batch);
 
-/* Tile size (sites per work item) and the L2 share a group of walks may
- * occupy (two buffers per walk); rebuilds the schedule.  Errors: QW_EINVAL. */
-qw_status qw_batch_set_tiling(qw_batch batch, int64_t tile_sites, int64_t l2_budget_bytes);
-qw_status qw_batch_get_tiling(qw_batch batch, int64_t* tile_sites, int64_t* l2_budget_bytes, int64_t* items);
+/* How a batch cuts its walks into work items.  A round advances one tile of a walk
+ * by `depth` steps (its fusion depth, per lattice dimension):
+ *   depth 1: every site updated from global memory; tiles are whole x rows (x
+ *            segments on the chain) of about tile_sites sites;
+ *   depth 2..4: temporal fusion; the tile is a box of box[dim-1] = (x, y, z)
+ *            cells (both cosets on the BCC lattice; unused axes ignored), which
+ *            is read with a halo of `depth` cells per side (depth/2 rounded up on
+ *            the BCC lattice) into shared memory, advanced there by `depth`
+ *            steps and written once: one read and one write of the field per
+ *            `depth` steps instead of per step.
+ * Walks whose two buffers fit l2_budget_bytes together form a group; groups
+ * run one after the other (small budgets keep a group's walks in L2). */
+typedef struct {
+  int64_t tile_sites;       /* depth-1 walks: sites per tile, 32 .. 4M */
+  int64_t l2_budget_bytes;  /* footprint of one group of walks, >= 1 MiB */
+  int depth[3];             /* fusion depth of 1D, 2D and BCC walks: 1 .. 4 */
+  int box[3][3];            /* fused tiles of 1D, 2D and BCC walks: (x, y, z) extents in cells */
+} qw_batch_tiling;
 
-/* Autotuner: times the batch kernel for every tile size in {1K, 2K, 4K, 8K,
- * 16K} sites and footprint budget in {24, 48, 96, 192 MiB, 1, 16 GiB} (walks
- * whose two buffers fit one budget form a group; small budgets keep a group in
- * L2, large ones give more parallel tiles) on stand-in fields of the same sizes
- * (zero-filled scratch, allocated and freed here; the walks' fields are not
- * touched), with the step counts scaled so that the longest walk runs
- * rounds_cap steps (the mix keeps its shape), and keeps the fastest setting.  Optional outputs: chosen tile, budget and the measured
- * site-steps/s.  Synchronous.  Errors: QW_EINVAL, QW_ENOMEM, QW_ECUDA. */
-qw_status qw_batch_autotune(qw_batch batch, int64_t rounds_cap, void* stream, int64_t* best_tile,
-                            int64_t* best_budget, double* best_rate);
+/* Set the tiling (rebuilds the schedule and drops the captured graph).
+ * Errors: QW_EINVAL (value out of range, or a walk whose fused tile, the box
+ * clipped to the walk plus its halo, needs more than 227 KB of shared memory for
+ * its two buffers), QW_ENOMEM, QW_ECUDA. */
+qw_status qw_batch_set_tiling(qw_batch batch, const qw_batch_tiling* tiling);
+
+/* The current tiling and the number of work items of one run (either may be NULL). */
+qw_status qw_batch_get_tiling(qw_batch batch, qw_batch_tiling* tiling, int64_t* items);
+
+/* Autotuner of the batched kernel: times one launch of the batch per candidate
+ * tiling on stand-in fields of the same sizes (zero-filled scratch, allocated and
+ * freed here; the walks' fields are not touched), with the step counts scaled so
+ * that the longest walk runs rounds_cap steps (the mix keeps its shape), and keeps
+ * the fastest.  Candidates: depth 1 with tile_sites in {1K, 2K, 4K, 8K}; fusion
+ * depth {2, 4} for 1D/2D walks with 2D boxes {32x16, 64x8, 32x32, 64x16} and depth
+ * {1, 2} for BCC walks with boxes {8x8x4, 8x8x6, 16x8x4, 8x8x8}; then the group
+ * budget in {48, 96, 192 MiB, 1 GiB} against one group (16 GiB).  Optional
+ * outputs: the chosen tiling and its measured site-steps/s.  Synchronous.
+ * Errors: QW_EINVAL, QW_ENOMEM, QW_ECUDA. */
+qw_status qw_batch_autotune(qw_batch batch, int64_t rounds_cap, void* stream, qw_batch_tiling* best,
+                            double* best_rate);
+
+/* Fault injection for tests of the bounded dependency waits.  walk >= 0: the
+ * first tile of that walk (caller's order) never publishes the rounds it
+ * completes, so the rounds that depend on it wait, give up after spin_limit
+ * polls (about 100 ns each), and qw_batch_sync returns QW_ETIMEOUT; the launch
+ * ends early and the walks' fields hold partial results.  walk < 0 restores
+ * normal operation (spin_limit ignored).  Drops the captured graph.
+ * Errors: QW_EINVAL (walk >= n, or spin_limit < 1 with walk >= 0). */
+qw_status qw_batch_debug_stall(qw_batch batch, int walk, int64_t spin_limit);
 
 /* Advance every walk by its t steps, in place, in one persistent launch
  * (captured into a CUDA graph on the first call, replayed afterwards).

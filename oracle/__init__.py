@@ -15,7 +15,7 @@ Plain, slow, obviously correct numpy in complex128:
 * ``spectral``    -- naive DFT, and U^t psi through the DFT with a per-k matrix
                      power (Sec. 4; the plain definition, no closed form).
 * ``observables`` -- norm, mean position (Sec. 5.2, operator X), position
-                     covariance, probability projections (Sec. 5.3), particle and
+                     covariance, probability projections (Sec. 5.2), particle and
                      antiparticle weights (spectral projector of U_k).
 * ``kinematics``  -- drift v = grad omega and diffusion D = grad grad omega of
                      particle states (Sec. 5.1, second-order dispersive equation).

@@ -10,13 +10,24 @@ the Weyl symbols (Eqs. weyl1d, weyl2d, weyl3d) written out below; k is the wave 
 the lattice wave numbers (k1, k2) conjugate to the lattice coordinates (a, b) (2D), and the
 Cartesian wave vector conjugate to the physical BCC coordinates (3D), i.e. the coordinates of
 the position observables.  Undefined where S = 0 (omega = 0 or pi: m = 0 and n~_k = 0).
+
+The accuracy of that second-order description is the overlap of Eq. overlap: a packet
+psi^(k, 0) = g(k) u_+(k) evolves exactly to exp(-i omega_k t) psi^(k, 0), and the truncated
+equation (Eq. diff-eq-2) gives exp(-i (omega' + v.K + K.D.K / 2) t) psi^(k, 0) with K = k - k',
+so their overlap is |sum_k |g|^2 exp(-i R_k t)| / sum_k |g|^2 with R_k the Taylor remainder
+of omega beyond second order; the Proposition bounds it below by 1 - eps - gamma Sigma^3 t
+(n = 2) up to O(Sigma^5) t.
 """
+
+import itertools
+import math
 
 import numpy as np
 
 from .walk import mass_n
 
-__all__ = ["u_derivatives", "drift", "diffusion"]
+__all__ = ["u_derivatives", "drift", "diffusion", "third_derivatives", "fidelity_bound",
+           "drift_diffusion_overlap"]
 
 
 def u_derivatives(dim, k):
@@ -64,3 +75,59 @@ def diffusion(dim, m, k):
     S = np.sqrt(max(0.0, 1.0 - (n * u) ** 2))
     v = -n * g / S
     return -(n * H + n * u * np.outer(v, v)) / S
+
+
+def third_derivatives(dim, m, k, h=1e-5):
+    """T[i, j, l] = d_i d_j d_l omega_k at k: central differences (step h) of the analytic
+    diffusion tensor above, symmetrised over the index order (error O(h^2))."""
+    k = np.asarray(k, dtype=float).reshape(dim)
+    T = np.zeros((dim, dim, dim))
+    for l in range(dim):
+        e = np.zeros(dim)
+        e[l] = h
+        T[:, :, l] = (diffusion(dim, m, k + e) - diffusion(dim, m, k - e)) / (2.0 * h)
+    return sum(np.transpose(T, p) for p in itertools.permutations(range(3))) / 6.0
+
+
+def fidelity_bound(dim, m, k0, weight, dk, sigma_box, t):
+    """Lower bound of the overlap of the exact evolution with the second-order (n = 2)
+    dispersive approximation (Sec. 5.1, Proposition "dispersive differential equation",
+    Eq. overlap), without its O(Sigma^5) t term:
+
+        1 - eps - gamma Sigma^3 t,
+        eps   = 1 - (share of |g|^2 in the box |k_i - k'_i| <= sigma_i)   (Definition 1),
+        gamma = 3 (1 - eps) sum_{|alpha| = 3} |omega^(alpha)_k'| / alpha!,  Sigma = max sigma_i.
+
+    weight: |g(k)|^2 on the wave-vector grid (any normalisation); dk: k - k' on that grid,
+    shape weight.shape + (dim,); sigma_box: the box half-widths (dim,); t: scalar or array."""
+    w = np.asarray(weight, dtype=float)
+    w = w / w.sum()
+    sig = np.broadcast_to(np.asarray(sigma_box, dtype=float), (dim,))
+    inside = np.all(np.abs(dk) <= sig, axis=-1)
+    eps = 1.0 - float(w[inside].sum())
+    T = third_derivatives(dim, m, k0)
+    acc = 0.0
+    for alpha in itertools.product(range(4), repeat=dim):
+        if sum(alpha) != 3:
+            continue
+        idx = tuple(i for i, a in enumerate(alpha) for _ in range(a))
+        acc += abs(T[idx]) / float(np.prod([math.factorial(a) for a in alpha]))
+    gamma = 3.0 * (1.0 - eps) * acc
+    Sigma = float(sig.max())
+    return 1.0 - eps - gamma * Sigma ** 3 * np.asarray(t, dtype=float)
+
+
+def drift_diffusion_overlap(dim, m, k0, weight, dk, omega, t):
+    """|<psi~(t)|psi(t)>| for a positive-frequency packet with spectral weights |g(k)|^2: the
+    exact phases omega_k against the second-order ones omega' + v.K + K.D.K / 2 (K = dk).
+    omega: omega_k on the grid; t: scalar or array."""
+    w = np.asarray(weight, dtype=float).ravel()
+    w = w / w.sum()
+    K = np.asarray(dk, dtype=float).reshape(-1, dim)
+    k0 = np.asarray(k0, dtype=float).reshape(dim)
+    om0 = float(np.arccos(mass_n(m) * u_derivatives(dim, k0)[0]))
+    v, D = drift(dim, m, k0), diffusion(dim, m, k0)
+    R = np.asarray(omega, dtype=float).ravel() - (om0 + K @ v + 0.5 * np.einsum("ki,ij,kj->k", K, D, K))
+    tt = np.atleast_1d(np.asarray(t, dtype=float))
+    out = np.array([abs(np.sum(w * np.exp(-1j * R * x))) for x in tt])
+    return out if np.ndim(t) else float(out[0])

@@ -15,7 +15,7 @@
                    Newton-Wigner position <X_NW> = <W^-1 psi| X |W^-1 psi>.
 * projections:     the probability density sum_s |psi_s(x)|^2 summed over the
                    axes that are not kept (the projections of a localised
-                   state's distribution onto axes and planes, Sec. 5.3), on the
+                   state's distribution onto axes and planes, Sec. 5.2), on the
                    same window and coordinates as the mean position.
 * particle weight: the weight of the positive-frequency part, i.e. of the
                    eigenspace of U_k with eigenvalue exp(-i omega_k) (Eq. eigen-D,

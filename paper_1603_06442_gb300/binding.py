@@ -46,6 +46,26 @@ class qw_request(ctypes.Structure):
                 ("k0", ctypes.c_double * 3), ("chi", ctypes.c_double * 8)]
 
 
+class qw_batch_tiling(ctypes.Structure):
+    _fields_ = [("tile_sites", ctypes.c_int64), ("l2_budget_bytes", ctypes.c_int64), ("depth", ctypes.c_int * 3),
+                ("box", (ctypes.c_int * 3) * 3)]
+
+    def as_dict(self):
+        return {"tile_sites": self.tile_sites, "l2_budget_bytes": self.l2_budget_bytes,
+                "depth": list(self.depth), "box": [list(b) for b in self.box]}
+
+    @classmethod
+    def from_dict(cls, d):
+        t = cls()
+        t.tile_sites = int(d["tile_sites"])
+        t.l2_budget_bytes = int(d["l2_budget_bytes"])
+        for i in range(3):
+            t.depth[i] = int(d["depth"][i])
+            for a in range(3):
+                t.box[i][a] = int(d["box"][i][a])
+        return t
+
+
 class qw_server_stats_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("pending", "running", "admitted", "completed", "bytes_in_use",
                                               "peak_bytes", "budget_bytes")]
@@ -79,13 +99,13 @@ _SIGS = {
     "qw_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "qw_batch_create": (ctypes.c_int, [ctypes.POINTER(qw_walk), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "qw_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
-    "qw_batch_set_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
-    "qw_batch_get_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
-                                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "qw_batch_set_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qw_batch_tiling)]),
+    "qw_batch_get_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qw_batch_tiling),
+                                           ctypes.POINTER(ctypes.c_int64)]),
     "qw_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "qw_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
-                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
-                                         ctypes.POINTER(ctypes.c_double)]),
+                                         ctypes.POINTER(qw_batch_tiling), ctypes.POINTER(ctypes.c_double)]),
+    "qw_batch_debug_stall": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
     "qw_batch_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "qw_batch_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qw_obs), ctypes.c_void_p]),
     "qw_step_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
@@ -352,14 +372,17 @@ def qw_batch_destroy(batch):
     _check(load().qw_batch_destroy(batch))
 
 
-def qw_batch_set_tiling(batch, tile_sites, l2_budget_bytes):
-    _check(load().qw_batch_set_tiling(batch, int(tile_sites), int(l2_budget_bytes)))
+def qw_batch_set_tiling(batch, tiling):
+    """tiling: dict with tile_sites, l2_budget_bytes, depth (3 ints) and box (3 x 3 ints)."""
+    t = qw_batch_tiling.from_dict(tiling)
+    _check(load().qw_batch_set_tiling(batch, ctypes.byref(t)))
 
 
 def qw_batch_get_tiling(batch):
-    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    _check(load().qw_batch_get_tiling(batch, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-    return a.value, b.value, c.value
+    """(tiling dict, work items of one run)."""
+    t, items = qw_batch_tiling(), ctypes.c_int64()
+    _check(load().qw_batch_get_tiling(batch, ctypes.byref(t), ctypes.byref(items)))
+    return t.as_dict(), items.value
 
 
 def qw_batch_run(batch, stream=None):
@@ -367,10 +390,14 @@ def qw_batch_run(batch, stream=None):
 
 
 def qw_batch_autotune(batch, rounds_cap=32, stream=None):
-    a, b, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
-    _check(load().qw_batch_autotune(batch, int(rounds_cap), _stream(stream), ctypes.byref(a), ctypes.byref(b),
-                                    ctypes.byref(r)))
-    return a.value, b.value, r.value
+    """(chosen tiling dict, its measured site-steps/s)."""
+    t, r = qw_batch_tiling(), ctypes.c_double()
+    _check(load().qw_batch_autotune(batch, int(rounds_cap), _stream(stream), ctypes.byref(t), ctypes.byref(r)))
+    return t.as_dict(), r.value
+
+
+def qw_batch_debug_stall(batch, walk, spin_limit=0):
+    _check(load().qw_batch_debug_stall(batch, int(walk), int(spin_limit)))
 
 
 def qw_batch_sync(batch, stream=None):
@@ -399,11 +426,14 @@ class Batch:
     def autotune(self, rounds_cap=32, stream=None):
         return qw_batch_autotune(self.handle, rounds_cap, stream)
 
-    def set_tiling(self, tile_sites, l2_budget_bytes):
-        qw_batch_set_tiling(self.handle, tile_sites, l2_budget_bytes)
+    def set_tiling(self, tiling):
+        qw_batch_set_tiling(self.handle, tiling)
 
     def tiling(self):
         return qw_batch_get_tiling(self.handle)
+
+    def debug_stall(self, walk, spin_limit=0):
+        qw_batch_debug_stall(self.handle, walk, spin_limit)
 
     def observables(self, stream=None):
         return qw_batch_observables(self.handle, len(self.walks), stream)

@@ -5,11 +5,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
-#include <set>
 #include <string>
-#include <tuple>
+#include <utility>
 
 #include "qw_internal.cuh"
 
@@ -32,15 +32,17 @@ qw_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 qw_status smem_attr_once(const void* func, int bytes) {
+  // the attribute is an upper bound: it is only ever raised, to the largest size requested
   static std::mutex mu;
-  static std::set<std::tuple<const void*, int, int>> done;
+  static std::map<std::pair<const void*, int>, int> limit;
   int dev = 0;
   QW_CHECK_CUDA(cudaGetDevice(&dev));
-  const auto key = std::make_tuple(func, dev, bytes);
+  const auto key = std::make_pair(func, dev);
   std::lock_guard<std::mutex> lock(mu);
-  if (done.count(key)) return QW_OK;
+  auto it = limit.find(key);
+  if (it != limit.end() && it->second >= bytes) return QW_OK;
   QW_CHECK_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  done.insert(key);
+  limit[key] = bytes;
   return QW_OK;
 }
 
@@ -99,7 +101,9 @@ static qw_status prepare_spectral(qw_plan_s* p) {
     return st;
   }
   const int nq = p->g.dim == 3 ? 2 : 1;
-  QW_CHECK_CUDA(cudaMalloc(&p->omega, sizeof(double) * nq * p->g.vol));
+  // 8 bytes per stored wave vector (complex64: the split nu pair), 16 for complex128
+  // (omega as a double-double)
+  QW_CHECK_CUDA(cudaMalloc(&p->omega, (p->dtype == QW_C64 ? 8 : 16) * nq * p->g.vol));
   QW_CHECK_CUDA(cudaMalloc(&p->spec_partials, sizeof(double) * 2 * kObsBlocks));
   if (fused_x_supported(p->g, p->fft, p->dtype))
     QW_CHECK_CUDA(cudaMalloc(&p->xw_partials, sizeof(double) * 2 * fused_x_grid(p->g)));

@@ -1,23 +1,33 @@
 // Many independent walks of uneven size in one persistent launch (complex64).
 //
-// Work items are (walk, round, tile): round s < t_w of walk w applies the
-// update rule (Eq. upd-rule, same per-site arithmetic as the plain kernels)
-// to one tile of rows, from the walk's buffer s % 2 into (s + 1) % 2; for odd
-// t_w a last round copies the result back into the caller's field.  Items are
-// numbered in a fixed order and claimed through one atomic counter:
+// Every walk is cut into tiles: boxes of cells (x, y, z extents; on the BCC
+// lattice a tile holds both cosets of its cells; the last tile of an axis may be
+// shorter).  Work items are (walk, round, tile).  A round of walk w advances
+// every tile of w by up to T_w steps of the update rule (Eq. upd-rule, the same
+// per-site arithmetic as the plain kernels), from the walk's buffer r % 2 into
+// (r + 1) % 2; when the number of stepping rounds is odd a last round copies
+// the result back into the caller's field.  The fusion depth T_w is set per
+// lattice dimension:
+//   * T = 1: each cell is updated from global memory (the plain per-site update);
+//   * T >= 2 (temporal fusion): the tile and a halo of H cells per side (H = T on
+//     the chain and the square lattice, ceil(T/2) on the BCC lattice, where one
+//     step reaches one cell of the other coset) are copied into shared memory by
+//     cp.async; T steps run there over shrinking regions, and only the last one
+//     is written to global memory: one read and one write of the field per T steps.
+// Items are numbered in a fixed order and claimed through one atomic counter:
 //   * walks are cut into groups whose two buffers fit in a share of L2;
 //     groups follow one another, so a group's walks are evolved while cached;
 //   * inside a group, rounds come in order and each round lists the tiles of
-//     every walk still running (walks sorted by length, so that set is a prefix).
-// Before working on round s of tile i of walk w a CTA waits (bounded) until the
-// tiles within the stencil's reach of tile i (cyclically, the box is periodic)
-// have finished round s-1: per-tile round counters, release/acquire (the lanes
-// of warp 0 acquire the counters, then a CTA barrier orders the tile's loads).  That
-// covers both the data tile i reads (written in round s-1) and the buffer it
-// overwrites (read by its neighbours in round s-1), and lets consecutive rounds
-// of a walk overlap as a wavefront instead of meeting at a barrier.  Every item
-// waits only on items earlier in the order, and an item is only claimed by a
-// running CTA, so the launch always makes progress.
+//     every walk still running (walks sorted by rounds, so that set is a prefix).
+// Before round r of tile i of walk w a CTA waits (bounded) until every tile
+// that meets tile i grown by H cells per axis (cyclically: the box is periodic)
+// has finished round r - 1: per-tile round counters, release/acquire (the lanes
+// of warp 0 acquire the counters, then a CTA barrier orders the tile's loads).
+// That covers both the data the round reads (written in round r - 1) and the
+// buffer it overwrites (read by its neighbours in round r - 1), and lets
+// consecutive rounds of a walk overlap as a wavefront instead of meeting at a
+// barrier.  Every item waits only on items earlier in the order, and an item is
+// only claimed by a running CTA, so the launch always makes progress.
 // The launch (counter resets + kernel) is captured once into a CUDA graph and
 // replayed by every qw_batch_run.
 #include <cuda/atomic>
@@ -35,17 +45,19 @@ namespace qw {
 
 struct BatchWalk {
   int dim;
+  int depth;          // steps per round: 1 = per-site update from global memory, >= 2 = fused
+  int halo;           // H: cells per side beyond the tile that one round depends on
+  int ncos, ncomp;    // cosets (2 on the BCC lattice) and spinor components
+  int n[3];           // cells per axis (nx, ny, nz)
+  int ext[3];         // tile extents along x, y, z (cells)
+  int nt[3];          // tiles per axis
   int ntiles;
-  int reach;              // tiles on each side a tile depends on (cyclic)
-  int64_t tile_base;      // first entry of this walk in the per-tile round counters
-  int64_t nx;             // row length (N in 1D/2D, M = N/2 on the BCC lattice)
-  int64_t ny;             // rows per plane layer (1 in 1D, N in 2D, M in 3D)
-  int64_t rows;           // rows of one step (1, N, 2 M^2)
-  int64_t rows_per_tile;
-  int64_t t;
-  int64_t rounds;         // t, plus one copy round when t is odd
-  int64_t vol;            // complex values per component plane
-  float2* buf[2];         // buf[0] = caller's field, buf[1] = partner
+  int vol;            // cells of one coset-component plane (walks hold < 2^31 values)
+  int64_t tile_base;  // first entry of this walk in the per-tile round counters
+  int64_t t;          // steps per run
+  int64_t nstep;      // stepping rounds: ceil(t / depth)
+  int64_t rounds;     // nstep, plus one copy round when nstep is odd
+  float2* buf[2];     // buf[0] = caller's field, buf[1] = partner
   Coef32 cf;
 };
 
@@ -65,7 +77,15 @@ struct BatchCtl {
   int err;
 };
 
+// Fault injection for tests: the tile whose completions are never published (-1: none)
+// and the number of polls after which a dependency wait gives up.
+struct BatchDebug {
+  int64_t stall_tile;
+  long long spin_limit;
+};
+
 constexpr long long kBatchSpin = 1ll << 24;
+constexpr int kBatchThreads = 256;
 
 // Largest i in [0, n) with a[i] <= v (a ascending, a[0] <= v), searched by the 32 lanes
 // of a warp together: each round cuts the range into 32 slices and keeps the last
@@ -84,12 +104,184 @@ __device__ __forceinline__ int64_t warp_upper_index(const int64_t* __restrict__ 
   return lo;
 }
 
-__global__ void __launch_bounds__(256, 6) batch_kernel(const BatchWalk* __restrict__ walks,
-                                                    const BatchGroup* __restrict__ groups,
-                                                    const int64_t* __restrict__ group_item0, int ngroups,
-                                                    const int64_t* __restrict__ tile_prefix,
-                                                    const int64_t* __restrict__ round_prefix, int64_t total_items,
-                                                    unsigned int* __restrict__ done, BatchCtl* __restrict__ ctl) {
+// Calls f(x, y, z) for this thread's cells of the box [lo, hi) (per axis): cells
+// tid, tid + NT, ... in x-fastest order, advanced without a division per cell.
+template <int NT, typename F>
+__device__ __forceinline__ void for_box(const int (&lo)[3], const int (&hi)[3], int tid, F&& f) {
+  const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
+  const int n = bx * by * bz;
+  if (tid >= n) return;
+  int x = tid % bx, r = tid / bx;
+  int y = r % by, z = r / by;
+  const int dx = NT % bx, dr = NT / bx;
+  const int dy = dr % by, dz = dr / by;
+  for (int k = tid; k < n; k += NT) {
+    f(lo[0] + x, lo[1] + y, lo[2] + z);
+    x += dx;
+    y += dy;
+    z += dz;
+    if (x >= bx) {
+      x -= bx;
+      ++y;
+    }
+    if (y >= by) {
+      y -= by;
+      ++z;
+    }
+  }
+}
+
+__device__ __forceinline__ int wrap_into(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// Region of coset c computed at step k of a fused round of `steps` steps, in the tile's
+// local frame [0, e + 2H) per axis (axes >= dim: [0, 1)).  The last step covers the tile
+// [H, H + e); going back one step, a BCC coset-0 cell needs coset 1 at m - 1 .. m and a
+// coset-1 cell coset 0 at m .. m + 1 (the own cell of each too), so with j = steps - k:
+// coset 0 [H - floor(j/2), H + e + ceil(j/2)), coset 1 [H - ceil(j/2), H + e + floor(j/2));
+// on the chain and the square lattice every step reaches one cell: [H - j, H + e + j).
+__device__ __forceinline__ void step_region(const BatchWalk& W, const int (&e)[3], int steps, int k, int c,
+                                            int (&lo)[3], int (&hi)[3]) {
+  const int j = steps - k, H = W.halo;
+  for (int a = 0; a < 3; ++a) {
+    if (a >= W.dim) {
+      lo[a] = 0;
+      hi[a] = 1;
+    } else if (W.dim == 3) {
+      const int jl = c == 0 ? j / 2 : (j + 1) / 2, jh = c == 0 ? (j + 1) / 2 : j / 2;
+      lo[a] = H - jl;
+      hi[a] = H + e[a] + jh;
+    } else {
+      lo[a] = H - j;
+      hi[a] = H + e[a] + j;
+    }
+  }
+}
+
+// cp.async of one 8-byte element into shared memory (all copies of a thread in flight).
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// One fused round of `steps` steps of tile (t0, t1, t2) of walk W: load the tile and its
+// halo from `in` into shared buffer A, step there (A -> B -> A ...), write the last step
+// to `out`.  Shared layout: [coset][component][z][y][x] with extents E = e + 2H per axis.
+__device__ void fused_round(const BatchWalk& W, const int (&t3)[3], int steps, const float2* in, float2* out,
+                            float2* smA, float2* smB) {
+  const int tid = threadIdx.x;
+  int s0[3], e[3], E[3];
+  for (int a = 0; a < 3; ++a) {
+    s0[a] = t3[a] * W.ext[a];
+    e[a] = min(W.ext[a], W.n[a] - s0[a]);
+    E[a] = a < W.dim ? e[a] + 2 * W.halo : 1;
+  }
+  const int H = W.halo;
+  const int sy = E[0], sz = E[0] * E[1], P = sz * E[2];  // pitches, component stride
+  const int nx = W.n[0], ny = W.n[1], nz = W.n[2];
+  // ---- load: warp w copies rows w, w + 8, ... (a row: one (coset, component, z, y)), lanes
+  // walk x with the periodic wrap
+  {
+    const int rows = W.ncos * W.ncomp * E[2] * E[1];
+    const int lane = tid & 31;
+    int gx0 = wrap_into(s0[0] - (W.dim >= 1 ? H : 0) + lane, nx);
+    for (int row = tid >> 5; row < rows; row += kBatchThreads / 32) {
+      const int y = row % E[1], r2 = row / E[1];
+      const int z = r2 % E[2], cq = r2 / E[2];
+      const int gy = W.dim >= 2 ? wrap_into(s0[1] - H + y, ny) : 0;
+      const int gz = W.dim >= 3 ? wrap_into(s0[2] - H + z, nz) : 0;
+      const float2* src = in + (int64_t)cq * W.vol + ((int64_t)gz * ny + gy) * nx;
+      float2* dst = smA + (int64_t)cq * P + z * sz + y * sy;
+      int gx = gx0;
+      for (int x = lane; x < E[0]; x += 32) {
+        cp_async8(dst + x, src + gx);
+        gx += 32;
+        while (gx >= nx) gx -= nx;
+      }
+    }
+    cp_async_all();
+  }
+  __syncthreads();
+  float2* cur = smA;
+  float2* nxt = smB;
+  for (int k = 1; k <= steps; ++k) {
+    const bool last = k == steps;
+    for (int c = 0; c < W.ncos; ++c) {
+      int lo[3], hi[3];
+      step_region(W, e, steps, k, c, lo, hi);
+      const float2* own_base = cur + c * 4 * P;
+      for_box<kBatchThreads>(lo, hi, tid, [&](int x, int y, int z) {
+        const int i = z * sz + y * sy + x;
+        float2* dst;
+        int ds;
+        if (last) {  // the tile's own cells: [H, H + e) maps to [s0, s0 + e), no wrap
+          const int gx = s0[0] - H + x;
+          const int gy = W.dim >= 2 ? s0[1] - H + y : 0;
+          const int gz = W.dim >= 3 ? s0[2] - H + z : 0;
+          dst = out + (int64_t)c * W.ncomp * W.vol + ((int64_t)gz * ny + gy) * nx + gx;
+          ds = W.vol;
+        } else {
+          dst = nxt + c * 4 * P + i;
+          ds = P;
+        }
+        if (W.dim == 1) {
+          core_1d<false>(cur + i - 1, cur + i + 1, cur + i, P, dst, ds, W.cf);
+        } else if (W.dim == 2) {
+          core_2d<false>(cur + i - 1, cur + i + 1, cur + i - sy, cur + i + sy, cur + i, P, dst, ds, W.cf);
+        } else {
+          core_3d<false>(cur + (1 - c) * 4 * P, sz, sy, z - 1 + c, z + c, y - 1 + c, y + c, x - 1 + c, x + c, P,
+                         own_base + i, dst, ds, W.cf);
+        }
+      });
+    }
+    if (!last) {
+      __syncthreads();
+      float2* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    }
+  }
+}
+
+// The plain round of tile (t0, t1, t2): every cell of the tile (both cosets) updated once
+// from global memory, or (copy round) copied from buf[1] to buf[0].
+__device__ void plain_round(const BatchWalk& W, const int (&t3)[3], bool copy, const float2* in, float2* out) {
+  int lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = t3[a] * W.ext[a];
+    hi[a] = min(W.n[a], lo[a] + W.ext[a]);
+  }
+  const int nx = W.n[0], ny = W.n[1];
+  for (int c = 0; c < W.ncos; ++c) {
+    for_box<kBatchThreads>(lo, hi, threadIdx.x, [&](int x, int y, int z) {
+      if (copy) {
+        const int64_t base = (int64_t)c * W.ncomp * W.vol + ((int64_t)z * ny + y) * nx + x;
+        for (int q = 0; q < W.ncomp; ++q) out[base + (int64_t)q * W.vol] = in[base + (int64_t)q * W.vol];
+      } else if (W.dim == 1) {
+        site_update_1d<float, false, int>(in, out, nx, x, W.cf);
+      } else if (W.dim == 2) {
+        site_update_2d<float, false, int>(in, out, nx, x, y, W.cf);
+      } else {
+        site_update_3d<float, false, int>(in, out, nx, c, z, y, x, W.cf);
+      }
+    });
+  }
+}
+
+// FUSED = false: every walk has depth 1 (no shared memory, high occupancy);
+// FUSED = true: walks of depth >= 2 run fused rounds in dynamic shared memory.
+template <bool FUSED>
+__global__ void __launch_bounds__(kBatchThreads, FUSED ? 2 : 6)
+    batch_kernel(const BatchWalk* __restrict__ walks, const BatchGroup* __restrict__ groups,
+                 const int64_t* __restrict__ group_item0, int ngroups, const int64_t* __restrict__ tile_prefix,
+                 const int64_t* __restrict__ round_prefix, int64_t total_items, unsigned int* __restrict__ done,
+                 BatchCtl* __restrict__ ctl, BatchDebug dbg) {
+  extern __shared__ float2 smem_dyn[];
   __shared__ int64_t s_next, s_round;
   __shared__ int s_abort, s_walk, s_tile;
   const int tid = threadIdx.x;
@@ -104,7 +296,7 @@ __global__ void __launch_bounds__(256, 6) batch_kernel(const BatchWalk* __restri
     const int64_t item = s_next;
     if (item >= total_items || s_abort) break;
     // ---- warp 0: decode (group, round, walk, tile) with warp-cooperative searches, then
-    // wait for round s-1 of the tiles within reach, the lanes polling the tiles'
+    // wait for round s-1 of the tiles the round depends on, the lanes polling the tiles'
     // counters in parallel; the other warps wait at the barrier
     if (tid < 32) {
       const int g = (int)warp_upper_index(group_item0, ngroups, item, tid);
@@ -123,18 +315,38 @@ __global__ void __launch_bounds__(256, 6) batch_kernel(const BatchWalk* __restri
         s_tile = tile;
       }
       if (s > 0) {
-        const int ntiles = walks[wi].ntiles, reach = walks[wi].reach;
-        const int64_t tbase = walks[wi].tile_base;
-        const int span = 2 * reach + 1 >= ntiles ? ntiles : 2 * reach + 1;
-        const int first = 2 * reach + 1 >= ntiles ? 0 : tile - reach;
+        const BatchWalk& W = walks[wi];
+        // per axis: the cyclic range of tiles meeting [start - H, start + e + H)
+        int first[3], cnt[3];
+        const int t3[3] = {tile % W.nt[0], (tile / W.nt[0]) % W.nt[1], tile / (W.nt[0] * W.nt[1])};
+        for (int a = 0; a < 3; ++a) {
+          const int na = W.n[a], ea = W.ext[a], nta = W.nt[a];
+          const int st = t3[a] * ea, e = min(ea, na - st);
+          const int len = e + 2 * (a < W.dim ? W.halo : 0);
+          if (len >= na) {
+            first[a] = 0;
+            cnt[a] = nta;
+          } else {
+            // cells lo .. lo + len - 1 (mod na): tiles lo / ea .. the end, then from tile 0 on
+            // when the interval wraps past na - 1
+            const int lo = wrap_into(st - (a < W.dim ? W.halo : 0), na), last = lo + len - 1;
+            first[a] = lo / ea;
+            const int c = last < na ? last / ea - first[a] + 1 : (nta - first[a]) + (last - na) / ea + 1;
+            cnt[a] = min(c, nta);
+          }
+        }
+        const int total = cnt[0] * cnt[1] * cnt[2];
+        const long long limit = dbg.spin_limit;
         long long spins = 0;
         bool gave_up = false;
-        for (int d = tid; d < span && !gave_up; d += 32) {
-          int j = first + d;
-          j = j < 0 ? j + ntiles : (j >= ntiles ? j - ntiles : j);
-          cuda::atomic_ref<unsigned int, cuda::thread_scope_device> c(done[tbase + j]);
+        for (int d = tid; d < total && !gave_up; d += 32) {
+          const int i0 = d % cnt[0], r = d / cnt[0];
+          const int i1 = r % cnt[1], i2 = r / cnt[1];
+          const int j = (first[0] + i0) % W.nt[0] +
+                        W.nt[0] * ((first[1] + i1) % W.nt[1] + W.nt[1] * ((first[2] + i2) % W.nt[2]));
+          cuda::atomic_ref<unsigned int, cuda::thread_scope_device> c(done[W.tile_base + j]);
           while (c.load(cuda::memory_order_acquire) < (unsigned int)s) {
-            if (++spins > kBatchSpin ||
+            if (++spins > limit ||
                 cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).load(cuda::memory_order_relaxed)) {
               cuda::atomic_ref<int, cuda::thread_scope_device>(ctl->abort).store(1, cuda::memory_order_relaxed);
               atomicExch(&ctl->err, 1);
@@ -144,72 +356,39 @@ __global__ void __launch_bounds__(256, 6) batch_kernel(const BatchWalk* __restri
             __nanosleep(64);
           }
         }
-        if (gave_up) s_abort = 1;
+        if (__any_sync(0xffffffffu, gave_up) && tid == 0) s_abort = 1;
       }
     }
     __syncthreads();
     if (s_abort) break;
     const int64_t s = s_round;
     const int tile = s_tile;
-    const BatchWalk W = walks[s_walk];
+    const BatchWalk& W = walks[s_walk];
     // claim the next item now (every thread read s_next before the barrier above): the
     // atomic's round trip overlaps this item's work, and the claimed item is started by
     // this CTA right after this one, so every claimed item still gets done
     if (tid == 0) s_next = (int64_t)atomicAdd(&ctl->next, 1ull);
-    // ---- the tile's rows
-    const int64_t r0 = (int64_t)tile * W.rows_per_tile;
-    const int64_t r1 = min(W.rows, r0 + W.rows_per_tile);
-    const int nx32 = (int)W.nx, ny32 = (int)W.ny;   // tiles and rows fit 32-bit indices
-    const int nsite = (int)((r1 - r0) * W.nx);
-    if (s < W.t) {
-      // (buffers picked by selects: a dynamically indexed member array would put W in local memory)
-      const float2* in = (s & 1) ? W.buf[1] : W.buf[0];
-      float2* out = (s & 1) ? W.buf[0] : W.buf[1];
-      // site k = tid + 256 i of the tile: (row, x) advanced by (256 / nx, 256 % nx) per
-      // iteration, so no division per site; 32-bit indices (walks hold < 2^31 values)
-      const int r0i = (int)r0;
-      int kr = tid / nx32, x = tid - kr * nx32;
-      const int dr = 256 / nx32, dx = 256 - dr * nx32;
-      for (int k = tid; k < nsite; k += 256) {
-        const int row = r0i + kr;
-        if (W.dim == 1) {
-          site_update_1d<float, false, int>(in, out, nx32, x, W.cf);
-        } else if (W.dim == 2) {
-          site_update_2d<float, false, int>(in, out, nx32, x, row, W.cf);
-        } else {
-          // rows interleave the cosets: row = 2 (z M + y) + c
-          const int c = row & 1;
-          const int zy = row >> 1;
-          const int z = zy / ny32;
-          site_update_3d<float, false, int>(in, out, nx32, c, z, zy - z * ny32, x, W.cf);
-        }
-        x += dx;
-        kr += dr;
-        if (x >= nx32) {
-          x -= nx32;
-          ++kr;
-        }
+    const int t3[3] = {tile % W.nt[0], (tile / W.nt[0]) % W.nt[1], tile / (W.nt[0] * W.nt[1])};
+    // (buffers picked by selects: a dynamically indexed member array would go to local memory)
+    float2* b0 = W.buf[0];
+    float2* b1 = W.buf[1];
+    if (s < W.nstep) {
+      const float2* in = (s & 1) ? b1 : b0;
+      float2* out = (s & 1) ? b0 : b1;
+      const int steps = (int)min((int64_t)W.depth, W.t - s * W.depth);
+      if (FUSED && W.depth > 1) {
+        const int P = (W.ncos * W.ncomp) * (W.ext[0] + 2 * W.halo) * (W.dim >= 2 ? W.ext[1] + 2 * W.halo : 1) *
+                      (W.dim >= 3 ? W.ext[2] + 2 * W.halo : 1);
+        fused_round(W, t3, steps, in, out, smem_dyn, smem_dyn + P);
+      } else {
+        plain_round(W, t3, false, in, out);
       }
     } else {
-      // copy round (odd t): the result sits in buf[1]
-      const float2* src = W.buf[1];
-      float2* dst = W.buf[0];
-      const int s_comp = W.dim == 1 ? 2 : 4;
-      for (int k = tid; k < nsite; k += blockDim.x) {
-        const int kr = k / nx32;
-        const int64_t row = r0 + kr, x = k - kr * nx32;
-        int64_t base;
-        if (W.dim == 3) {
-          const int c = (int)(row & 1);
-          base = (int64_t)c * 4 * W.vol + (row >> 1) * W.nx + x;
-        } else {
-          base = row * W.nx + x;
-        }
-        for (int q = 0; q < s_comp; ++q) dst[base + q * W.vol] = src[base + q * W.vol];
-      }
+      plain_round(W, t3, true, b1, b0);  // copy round: the result sits in buf[1]
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && W.tile_base + tile != dbg.stall_tile) {
+      __threadfence();
       cuda::atomic_ref<unsigned int, cuda::thread_scope_device>(done[W.tile_base + tile])
           .store((unsigned int)(s + 1), cuda::memory_order_release);
     }
@@ -236,9 +415,13 @@ struct qw_batch_s {
   BatchCtl* d_ctl = nullptr;
   int ngroups = 0;
   int64_t total_items = 0;
-  int64_t tile_sites = 4096;
-  int64_t l2_budget = 48ll << 20;
+  qw_batch_tiling tiling;
+  bool fused = false;      // some walk has depth >= 2: the fused kernel runs the launch
+  size_t smem = 0;         // its dynamic shared memory
   int grid = 0;
+  BatchDebug dbg = {-1, kBatchSpin};
+  int stall_walk = -1;     // caller's index of the walk whose first tile is stalled
+  std::vector<int64_t> first_tile;  // per original walk: its first per-tile counter
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   // observables
@@ -248,6 +431,52 @@ struct qw_batch_s {
 };
 
 namespace qw {
+
+static qw_batch_tiling default_tiling() {
+  qw_batch_tiling t;
+  t.tile_sites = 4096;
+  t.l2_budget_bytes = int64_t(16) << 30;
+  t.depth[0] = 2;
+  t.depth[1] = 2;
+  t.depth[2] = 2;
+  const int box[3][3] = {{1024, 1, 1}, {32, 16, 1}, {8, 8, 4}};
+  for (int d = 0; d < 3; ++d)
+    for (int a = 0; a < 3; ++a) t.box[d][a] = box[d][a];
+  return t;
+}
+
+static int halo_of(int dim, int depth) { return dim == 3 ? (depth + 1) / 2 : depth; }
+
+// Shared memory of one fused round of a dim-dimensional walk with tile extents `box`
+// (two buffers).
+static size_t fused_smem(int dim, int depth, const int* box) {
+  const int H = halo_of(dim, depth);
+  size_t cells = 1;
+  for (int a = 0; a < dim; ++a) cells *= (size_t)(box[a] + 2 * H);
+  const int planes = dim == 1 ? 2 : (dim == 2 ? 4 : 8);  // cosets x components
+  return 2 * cells * planes * sizeof(float2);
+}
+
+constexpr size_t kMaxBatchSmem = 227 * 1024;
+
+static qw_status check_tiling(const qw_batch_tiling& t) {
+  if (t.tile_sites < 32 || t.tile_sites > (1 << 22) || t.l2_budget_bytes < (1 << 20)) {
+    set_error("qw_batch tiling: tile_sites in [32, 4M] and budget >= 1 MiB");
+    return QW_EINVAL;
+  }
+  for (int d = 0; d < 3; ++d) {
+    if (t.depth[d] < 1 || t.depth[d] > 4) {
+      set_error("qw_batch tiling: fusion depth of dim %d is %d (1..4)", d + 1, t.depth[d]);
+      return QW_EINVAL;
+    }
+    for (int a = 0; a <= d; ++a)
+      if (t.box[d][a] < 1 || t.box[d][a] > 4096) {
+        set_error("qw_batch tiling: box extent %d of dim %d out of range", t.box[d][a], d + 1);
+        return QW_EINVAL;
+      }
+  }
+  return QW_OK;
+}
 
 static void free_schedule(qw_batch_s* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -274,8 +503,51 @@ static int64_t field_bytes(const qw_walk& w) {
   return g.elems * 8;
 }
 
-// Build the walk table, groups and prefix arrays for the current tile size and
-// L2 budget, and upload them.
+// The walk's entry of the schedule under tiling t (tiles, depth, rounds).
+static BatchWalk make_walk(const qw_walk& d, void* partner, const qw_batch_tiling& t) {
+  Geometry g;
+  make_geometry(d.dim, d.N, &g);
+  BatchWalk W;
+  W.dim = d.dim;
+  W.depth = t.depth[d.dim - 1];
+  W.ncos = g.ncoset;
+  W.ncomp = g.s;
+  W.n[0] = (int)g.nx;
+  W.n[1] = (int)g.ny;
+  W.n[2] = (int)g.nz;
+  if (W.depth == 1) {
+    // whole x rows (x segments on the chain), about tile_sites sites per tile
+    W.halo = 1;
+    if (d.dim == 1) {
+      W.ext[0] = (int)std::min<int64_t>(g.nx, t.tile_sites);
+      W.ext[1] = W.ext[2] = 1;
+    } else {
+      const int64_t rows = std::max<int64_t>(1, t.tile_sites / (g.nx * g.ncoset));
+      W.ext[0] = (int)g.nx;
+      W.ext[1] = (int)std::min<int64_t>(g.ny, rows);
+      W.ext[2] = rows >= g.ny ? (int)std::min<int64_t>(g.nz, std::max<int64_t>(1, rows / g.ny)) : 1;
+    }
+  } else {
+    W.halo = halo_of(d.dim, W.depth);
+    for (int a = 0; a < 3; ++a) W.ext[a] = a < d.dim ? std::min(t.box[d.dim - 1][a], W.n[a]) : 1;
+  }
+  W.ntiles = 1;
+  for (int a = 0; a < 3; ++a) {
+    W.nt[a] = (W.n[a] + W.ext[a] - 1) / W.ext[a];
+    W.ntiles *= W.nt[a];
+  }
+  W.vol = (int)g.vol;
+  W.t = d.t;
+  W.nstep = (d.t + W.depth - 1) / W.depth;
+  W.rounds = W.nstep + (W.nstep & 1);
+  W.buf[0] = static_cast<float2*>(d.psi_dev);
+  W.buf[1] = static_cast<float2*>(partner);
+  W.cf = make_coef32(d.dim, std::sqrt(1.0 - d.mass * d.mass), d.mass);
+  W.tile_base = 0;
+  return W;
+}
+
+// Build the walk table, groups and prefix arrays for the current tiling, and upload them.
 static qw_status build_schedule(qw_batch_s* b) {
   free_schedule(b);
   const int n = b->n;
@@ -288,7 +560,7 @@ static qw_status build_schedule(qw_batch_s* b) {
   int64_t acc = 0;
   for (int i : idx) {
     const int64_t fb = 2 * field_bytes(b->desc[i]);
-    if (grp.empty() || (acc + fb > b->l2_budget && !grp.back().empty())) {
+    if (grp.empty() || (acc + fb > b->tiling.l2_budget_bytes && !grp.back().empty())) {
       grp.emplace_back();
       acc = 0;
     }
@@ -299,11 +571,18 @@ static qw_status build_schedule(qw_batch_s* b) {
   std::vector<BatchGroup> groups;
   std::vector<int64_t> tiles, rounds;
   b->order.clear();
+  b->first_tile.assign(n, 0);
+  b->fused = false;
+  b->smem = 0;
   int64_t item0 = 0;
   int64_t ndone_acc = 0;
   for (auto& gw : grp) {
-    // inside a group: longest walks first, so the walks alive at round s are a prefix
-    std::stable_sort(gw.begin(), gw.end(), [&](int a, int c) { return b->desc[a].t > b->desc[c].t; });
+    std::vector<BatchWalk> gwalks;
+    for (int i : gw) gwalks.push_back(make_walk(b->desc[i], b->partners[i], b->tiling));
+    // inside a group: most rounds first, so the walks alive at round s are a prefix
+    std::vector<int> ord(gw.size());
+    for (size_t k = 0; k < gw.size(); ++k) ord[k] = (int)k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return gwalks[a].rounds > gwalks[c].rounds; });
     BatchGroup G;
     G.first = (int)walks.size();
     G.nw = (int)gw.size();
@@ -312,34 +591,27 @@ static qw_status build_schedule(qw_batch_s* b) {
     tiles.push_back(0);
     int64_t maxr = 0;
     std::vector<int64_t> wr;
-    for (int i : gw) {
-      const qw_walk& d = b->desc[i];
-      Geometry g;
-      make_geometry(d.dim, d.N, &g);
-      BatchWalk W;
-      W.dim = d.dim;
-      W.nx = g.nx;
-      W.ny = g.ny;
-      W.rows = g.dim == 1 ? 1 : (g.dim == 2 ? g.ny : 2 * g.ny * g.nz);
-      W.rows_per_tile = std::max<int64_t>(1, b->tile_sites / g.nx);
-      W.ntiles = (int)((W.rows + W.rows_per_tile - 1) / W.rows_per_tile);
-      // rows a site update reaches: 1 (2D), 2M + 3 (BCC rows interleave the cosets), 0 (1D: one row)
-      const int64_t reach_rows = g.dim == 1 ? 0 : (g.dim == 2 ? 1 : 2 * g.nx + 3);
-      // (+1 when the last tile is short: a cyclic neighbour window then needs one more tile)
-      W.reach = (int)((reach_rows + W.rows_per_tile - 1) / W.rows_per_tile) + (W.rows % W.rows_per_tile ? 1 : 0);
+    for (int k : ord) {
+      BatchWalk W = gwalks[k];
       W.tile_base = ndone_acc;
+      b->first_tile[gw[k]] = ndone_acc;
       ndone_acc += W.ntiles;
-      W.t = d.t;
-      W.rounds = d.t + (d.t & 1);
-      W.vol = g.vol;
-      W.buf[0] = static_cast<float2*>(d.psi_dev);
-      W.buf[1] = static_cast<float2*>(b->partners[i]);
-      W.cf = make_coef32(d.dim, std::sqrt(1.0 - d.mass * d.mass), d.mass);
+      if (W.depth > 1) {
+        // the box clipped to the walk: a box larger than a small walk costs nothing extra
+        const size_t need = fused_smem(W.dim, W.depth, W.ext);
+        if (need > kMaxBatchSmem) {
+          set_error("qw_batch tiling: a dim-%d walk's tile with depth %d needs %zu bytes of shared memory (max %zu)",
+                    W.dim, W.depth, need, kMaxBatchSmem);
+          return QW_EINVAL;
+        }
+        b->fused = true;
+        b->smem = std::max(b->smem, need);
+      }
       walks.push_back(W);
       tiles.push_back(tiles.back() + W.ntiles);
       wr.push_back(W.rounds);
       maxr = std::max(maxr, W.rounds);
-      b->order.push_back(i);
+      b->order.push_back(gw[k]);
     }
     // round prefix: items of round s = tiles of the walks with rounds > s (a prefix)
     rounds.push_back(0);
@@ -351,11 +623,10 @@ static qw_status build_schedule(qw_batch_s* b) {
     G.nrounds = maxr;
     G.item0 = item0;
     G.nitems = rounds.back() - rounds[G.round_off];
-    // make round prefix relative to the group's first item
     item0 += G.nitems;
     groups.push_back(G);
   }
-  // relative round prefixes: rounds[G.round_off + s] counts from the group's first item
+  // relative prefixes: rounds[G.round_off + s] and tiles[G.tile_off + w] count from the group's start
   for (auto& G : groups) {
     const int64_t base = rounds[G.round_off];
     for (int64_t s = 0; s <= G.nrounds; ++s) rounds[G.round_off + s] -= base;
@@ -366,6 +637,7 @@ static qw_status build_schedule(qw_batch_s* b) {
   }
   b->ngroups = (int)groups.size();
   b->total_items = item0;
+  b->dbg.stall_tile = b->stall_walk >= 0 ? b->first_tile[b->stall_walk] : -1;
   QW_CHECK_CUDA(cudaMalloc(&b->d_walks, walks.size() * sizeof(BatchWalk)));
   QW_CHECK_CUDA(cudaMalloc(&b->d_groups, groups.size() * sizeof(BatchGroup)));
   QW_CHECK_CUDA(cudaMalloc(&b->d_tiles, tiles.size() * sizeof(int64_t)));
@@ -381,7 +653,13 @@ static qw_status build_schedule(qw_batch_s* b) {
   QW_CHECK_CUDA(cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   QW_CHECK_CUDA(cudaMemcpy(b->d_rounds, rounds.data(), rounds.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   int per_sm = 0, nsm = 0;
-  QW_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, 256, 0));
+  if (b->fused) {
+    qw_status sa = smem_attr(batch_kernel<true>, (int)b->smem);
+    if (sa != QW_OK) return sa;
+    QW_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<true>, kBatchThreads, b->smem));
+  } else {
+    QW_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<false>, kBatchThreads, 0));
+  }
   QW_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
   b->grid = std::max(1, per_sm * nsm);
   return QW_OK;
@@ -390,9 +668,14 @@ static qw_status build_schedule(qw_batch_s* b) {
 static qw_status launch_batch(qw_batch_s* b, cudaStream_t s) {
   QW_CHECK_CUDA(cudaMemsetAsync(b->d_done, 0, std::max<int64_t>(1, b->ndone) * sizeof(unsigned int), s));
   QW_CHECK_CUDA(cudaMemsetAsync(b->d_ctl, 0, sizeof(BatchCtl), s));
-  batch_kernel<<<b->grid, 256, 0, s>>>(b->d_walks, b->d_groups, b->d_group_item0, b->ngroups, b->d_tiles,
-                                       b->d_rounds,
-                                       b->total_items, b->d_done, b->d_ctl);
+  if (b->fused)
+    batch_kernel<true><<<b->grid, kBatchThreads, b->smem, s>>>(b->d_walks, b->d_groups, b->d_group_item0,
+                                                               b->ngroups, b->d_tiles, b->d_rounds, b->total_items,
+                                                               b->d_done, b->d_ctl, b->dbg);
+  else
+    batch_kernel<false><<<b->grid, kBatchThreads, 0, s>>>(b->d_walks, b->d_groups, b->d_group_item0, b->ngroups,
+                                                          b->d_tiles, b->d_rounds, b->total_items, b->d_done,
+                                                          b->d_ctl, b->dbg);
   QW_CHECK_LAUNCH("batch kernel launch");
   return QW_OK;
 }
@@ -411,8 +694,8 @@ qw_status qw_batch_create(const qw_walk* walks, int n, qw_batch* out) {
     Geometry g;
     const qw_walk& w = walks[i];
     if (!make_geometry(w.dim, w.N, &g) || !(w.mass >= 0.0 && w.mass <= 1.0) || w.t < 0 || !w.psi_dev ||
-        w.t > 0x3fffffff) {
-      set_error("qw_batch_create: walk %d has a bad dim/N/mass/t or a null field", i);
+        w.t > 0x3fffffff || g.elems >= (int64_t(1) << 31)) {
+      set_error("qw_batch_create: walk %d has a bad dim/N/mass/t, more than 2^31 values or a null field", i);
       return QW_EINVAL;
     }
   }
@@ -424,6 +707,7 @@ qw_status qw_batch_create(const qw_walk* walks, int n, qw_batch* out) {
   b->n = n;
   b->desc.assign(walks, walks + n);
   b->partners.assign(n, nullptr);
+  b->tiling = default_tiling();
   qw_status st = QW_OK;
   cudaError_t e = cudaGetDevice(&b->device);
   for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaMalloc(&b->partners[i], field_bytes(walks[i]));
@@ -460,25 +744,35 @@ qw_status qw_batch_destroy(qw_batch b) {
   return QW_OK;
 }
 
-qw_status qw_batch_set_tiling(qw_batch b, int64_t tile_sites, int64_t l2_budget_bytes) {
-  if (!b || tile_sites < 32 || tile_sites > (1 << 22) || l2_budget_bytes < (1 << 20)) {
-    set_error("qw_batch_set_tiling: bad arguments (tile_sites in [32, 4M], budget >= 1 MiB)");
+qw_status qw_batch_set_tiling(qw_batch b, const qw_batch_tiling* tiling) {
+  if (!b || !tiling) {
+    set_error("qw_batch_set_tiling: null argument");
     return QW_EINVAL;
   }
-  b->tile_sites = tile_sites;
-  b->l2_budget = l2_budget_bytes;
+  qw_status st = check_tiling(*tiling);
+  if (st != QW_OK) return st;
+  b->tiling = *tiling;
   return build_schedule(b);
 }
 
-qw_status qw_batch_get_tiling(qw_batch b, int64_t* tile_sites, int64_t* l2_budget_bytes, int64_t* items) {
+qw_status qw_batch_get_tiling(qw_batch b, qw_batch_tiling* tiling, int64_t* items) {
   if (!b) {
     set_error("qw_batch_get_tiling: null batch");
     return QW_EINVAL;
   }
-  if (tile_sites) *tile_sites = b->tile_sites;
-  if (l2_budget_bytes) *l2_budget_bytes = b->l2_budget;
+  if (tiling) *tiling = b->tiling;
   if (items) *items = b->total_items;
   return QW_OK;
+}
+
+qw_status qw_batch_debug_stall(qw_batch b, int walk, int64_t spin_limit) {
+  if (!b || walk >= b->n || (walk >= 0 && spin_limit < 1)) {
+    set_error("qw_batch_debug_stall: null batch, walk index out of range or spin_limit < 1");
+    return QW_EINVAL;
+  }
+  b->stall_walk = walk < 0 ? -1 : walk;
+  b->dbg.spin_limit = walk < 0 ? kBatchSpin : spin_limit;
+  return build_schedule(b);  // drops the captured graph: its kernel arguments change
 }
 
 qw_status qw_batch_run(qw_batch b, void* stream) {
@@ -521,10 +815,14 @@ qw_status qw_batch_sync(qw_batch b, void* stream) {
   return QW_OK;
 }
 
-qw_status qw_batch_autotune(qw_batch b, int64_t rounds_cap, void* stream, int64_t* best_tile, int64_t* best_budget,
+qw_status qw_batch_autotune(qw_batch b, int64_t rounds_cap, void* stream, qw_batch_tiling* best_tiling,
                             double* best_rate) {
   if (!b || rounds_cap < 2) {
     set_error("qw_batch_autotune: null batch or rounds_cap < 2");
+    return QW_EINVAL;
+  }
+  if (b->stall_walk >= 0) {
+    set_error("qw_batch_autotune: a stall is injected (qw_batch_debug_stall); clear it first");
     return QW_EINVAL;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -549,52 +847,83 @@ qw_status qw_batch_autotune(qw_batch b, int64_t rounds_cap, void* stream, int64_
     make_geometry(w.dim, w.N, &g);
     site_steps += g.sites * w.t;
   }
-  const int64_t tiles[] = {1024, 2048, 4096, 8192, 16384};
-  const int64_t budgets[] = {int64_t(24) << 20, int64_t(48) << 20, int64_t(96) << 20, int64_t(192) << 20,
-                             int64_t(1) << 30, int64_t(16) << 30};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  double best = -1.0;
-  int64_t bt = b->tile_sites, bb = b->l2_budget;
+  const qw_batch_tiling saved = b->tiling;
+  qw_batch_tiling best = saved;
+  double best_r = -1.0;
   qw_status st = QW_OK;
-  for (int64_t ts : tiles) {
-    for (int64_t bu : budgets) {
-      b->tile_sites = ts;
-      b->l2_budget = bu;
-      st = build_schedule(b);
-      if (st != QW_OK) break;
-      st = launch_batch(b, s);  // warm-up
-      if (st != QW_OK) break;
-      cudaEventRecord(e0, s);
-      st = launch_batch(b, s);
-      cudaEventRecord(e1, s);
-      if (st != QW_OK) break;
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      const double rate = (double)site_steps / (ms * 1e-3);
-      if (rate > best) {
-        best = rate;
-        bt = ts;
-        bb = bu;
-      }
+  auto measure = [&](const qw_batch_tiling& t) -> qw_status {
+    if (check_tiling(t) != QW_OK) return QW_OK;  // not a candidate
+    b->tiling = t;
+    qw_status r = build_schedule(b);
+    if (r == QW_EINVAL) return QW_OK;  // a tile of this mix does not fit shared memory
+    if (r != QW_OK) return r;
+    if ((r = launch_batch(b, s)) != QW_OK) return r;  // warm-up
+    cudaEventRecord(e0, s);
+    if ((r = launch_batch(b, s)) != QW_OK) return r;
+    cudaEventRecord(e1, s);
+    QW_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double rate = (double)site_steps / (ms * 1e-3);
+    if (rate > best_r) {
+      best_r = rate;
+      best = t;
     }
+    return QW_OK;
+  };
+  // stage 1: one step per round, whole-row tiles of each size
+  const int64_t tiles[] = {1024, 2048, 4096, 8192};
+  qw_batch_tiling t = default_tiling();
+  t.depth[0] = t.depth[1] = t.depth[2] = 1;
+  for (int64_t ts : tiles) {
     if (st != QW_OK) break;
+    t.tile_sites = ts;
+    st = measure(t);
+  }
+  // stage 2: fused rounds, fusion depth and tile box per lattice (depth-1 walks keep the
+  // best row tile of stage 1)
+  const int depth2[] = {2, 4};
+  const int depth3[] = {1, 2};
+  const int box2[][3] = {{32, 16, 1}, {64, 8, 1}, {32, 32, 1}, {64, 16, 1}};
+  const int box3[][3] = {{8, 8, 4}, {8, 8, 6}, {16, 8, 4}, {8, 8, 8}};
+  const int64_t best_rows = best.tile_sites;
+  for (int d2 : depth2)
+    for (const auto& bx2 : box2)
+      for (int d3 : depth3)
+        for (int k3 = 0; k3 < (d3 == 1 ? 1 : 4) && st == QW_OK; ++k3) {
+          t = default_tiling();
+          t.tile_sites = best_rows;
+          t.depth[0] = t.depth[1] = d2;
+          t.depth[2] = d3;
+          for (int a = 0; a < 3; ++a) {
+            t.box[1][a] = bx2[a];
+            t.box[2][a] = box3[k3][a];
+          }
+          st = measure(t);
+        }
+  // stage 3: the group budget for the best tiling (small budgets keep a group in L2)
+  const int64_t budgets[] = {int64_t(48) << 20, int64_t(96) << 20, int64_t(192) << 20, int64_t(1) << 30};
+  const qw_batch_tiling stage2 = best;
+  for (int64_t bu : budgets) {
+    if (st != QW_OK) break;
+    t = stage2;
+    t.l2_budget_bytes = bu;
+    st = measure(t);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamSynchronize(s);
   cudaFree(pool);
   b->desc = real;
-  b->tile_sites = bt;
-  b->l2_budget = bb;
+  b->tiling = st == QW_OK ? best : saved;
   qw_status st2 = build_schedule(b);
   if (st != QW_OK) return st;
   if (st2 != QW_OK) return st2;
-  if (best_tile) *best_tile = bt;
-  if (best_budget) *best_budget = bb;
-  if (best_rate) *best_rate = best;
+  if (best_tiling) *best_tiling = best;
+  if (best_rate) *best_rate = best_r;
   return QW_OK;
 }
 

@@ -1,4 +1,4 @@
-// Probability projections (Sec. 5.3: the distribution of a localised state projected
+// Probability projections (Sec. 5.2: the distribution of a localised state projected
 // onto axes and planes): rho(x) = sum_s |psi_s(x)|^2 summed over the axes that are not
 // kept, on the physical grid (lattice coordinates (a, b) in 2D, physical BCC
 // coordinates 2 m + c (1, 1, 1) in 3D), in FP64.

@@ -15,9 +15,9 @@ namespace qw {
 void set_error(const char* fmt, ...);
 qw_status cuda_fail(cudaError_t e, const char* what);
 
-// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device, once
-// per (kernel, device, bytes).  Thread-safe: the server's scheduler thread and callers'
-// threads launch the same kernels, possibly on different devices.
+// Raise a kernel's dynamic shared-memory limit on the current device to at least `bytes`
+// (per kernel and device the limit only grows).  Thread-safe: the server's scheduler
+// thread and callers' threads launch the same kernels, possibly on different devices.
 qw_status smem_attr_once(const void* func, int bytes);
 template <typename K>
 inline qw_status smem_attr(K* kernel, int bytes) {
@@ -144,8 +144,8 @@ struct SpecAxes {  // digit split of each axis (storage order -> frequency) and 
   const float4* angdf;
 };
 SpecAxes spec_axes(const Geometry& g, const FftPlan& f);
-// FP64 omega per wave vector, or (split, complex64 plans) nu = omega / 2 pi as an FP32
-// (hi, lo) pair in the same 8 bytes
+// omega per wave vector: (split = false, complex128 plans) a double-double (hi, lo) in 16
+// bytes, or (split, complex64 plans) nu = omega / 2 pi as an FP32 (hi, lo) pair in 8 bytes
 qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,
                              cudaStream_t st, bool split);
 // psi_hat (forward DFT, storage order) <- D_k^t psi_hat / |V|, BCC cosets mixed per cell;
@@ -209,8 +209,8 @@ struct qw_plan_s {
   // spectral path (allocated by the first spectral call or qw_plan_prepare_spectral)
   bool spec_ready;
   qw::FftPlan fft;
-  double* omega;        // omega_k per stored wave vector (two per cell on the BCC lattice); complex64
-                        // plans hold nu = omega / 2 pi as FP32 (hi, lo) pairs instead
+  double* omega;        // omega_k per stored wave vector (two per cell on the BCC lattice): a double-
+                        // double (16 B) for complex128, nu = omega / 2 pi as an FP32 pair (8 B) for complex64
   double* spec_partials;  // 2 * kObsBlocks doubles for the particle-weight reduction
   double* xw_partials;    // 2 doubles per CTA of the x-pass weights (when the x pass is fused)
   double* red_partials; // 10 * kMom2MaxBlocks doubles (>= 4 * kObsBlocks)

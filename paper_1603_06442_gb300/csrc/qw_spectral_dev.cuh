@@ -196,6 +196,20 @@ __device__ __forceinline__ void phase(double omega, double tt, double& c, double
   r = fma(-kq, TWO_PI_LO, r) + e;
   sincos(r, &s, &c);
 }
+// (cos, sin) of omega t for omega = hi + lo (double-double): hi t is split exactly into
+// p + e (FMA), the low part adds lo t, and the reduction modulo 2 pi is that of phase();
+// the reduced phase then carries ~1e-16 of rounding whatever t (t < 2^53), instead of
+// t ulp(omega).
+__device__ __forceinline__ void phase_dd(double hi, double lo, double tt, double& c, double& s) {
+  const double TWO_PI_HI = 6.283185307179586232e+00;
+  const double TWO_PI_LO = 2.449293598294706e-16;
+  const double p = hi * tt;
+  const double e = fma(hi, tt, -p);
+  const double kq = rint(p * 0.15915494309189533577);
+  double r = fma(-kq, TWO_PI_HI, p);
+  r = fma(-kq, TWO_PI_LO, r) + (e + lo * tt);
+  sincos(r, &s, &c);
+}
 // complex64 path: same FP64 reduction without the product's low part (about
 // 1e-16 * omega t, far below the FP32 resolution of the reduced phase)
 __device__ __forceinline__ void phase32(double omega, double tt, float& c, float& s) {
@@ -438,7 +452,12 @@ __device__ __forceinline__ void cs_at(int dim, const AxesDev& a, const int64_t (
       cs_of<T, S>(omega_of(dim, a, f, q, ms), ta.tt, c, s);
     }
   } else if (sizeof(T) == 8) {
-    cs_of<T, S>(omega[slot], ta.tt, c, s);
+    // complex128 plans store omega_k as a double-double (hi, lo)
+    const double2 w = reinterpret_cast<const double2*>(omega)[slot];
+    double cd, sd;
+    phase_dd(w.x, w.y, ta.tt, cd, sd);
+    c = (T)cd;
+    s = (T)sd;
   } else {
     const float2 nu = reinterpret_cast<const float2*>(omega)[slot];
     if (ta.small) {

@@ -58,62 +58,70 @@ __device__ __forceinline__ I wrapm(I v, I M) { return v < 0 ? v + M : (v >= M ? 
 
 
 // ------------------------------------------------------------ per-site updates
+// Each update has a core that takes pointers to component 0 of the cells it reads and a
+// component stride, so that fields in global memory and tiles in shared memory (other
+// pitches) run the same arithmetic in the same order.
+
 // chain, s = 2: psi'_0(x) = n psi_0(x-1) + i m psi_1(x), psi'_1(x) = i m psi_0(x) + n psi_1(x+1)
+template <bool NC, typename C, typename CF, typename I>
+__device__ __forceinline__ void core_1d(const C* xm, const C* xp, const C* own, I cs, C* dst, I ds, const CF& cf) {
+  C a = ldg<NC>(xm);        // psi_0(x - 1)
+  C b = ldg<NC>(xp + cs);   // psi_1(x + 1)
+  C o0 = ldg<NC>(own), o1 = ldg<NC>(own + cs);
+  dst[0] = finish(cf, a, o1);
+  dst[ds] = finish(cf, b, o0);
+}
+
 // (I: index type; the batched kernel's walks fit 32-bit indices)
 template <typename R, bool NC = true, typename I = int64_t>
 __device__ __forceinline__ void site_update_1d(const typename CplxOf<R>::T* __restrict__ in,
                                                typename CplxOf<R>::T* __restrict__ out, I N, I x,
                                                const typename CoefOf<R>::T& cf) {
-  using C = typename CplxOf<R>::T;
-  const C* p0 = in;
-  const C* p1 = in + N;
-  C a = ldg<NC>(p0 + wrapm<I>(x - 1, N));   // psi_0(x - 1)
-  C b = ldg<NC>(p1 + wrapm<I>(x + 1, N));   // psi_1(x + 1)
-  C o0 = ldg<NC>(p0 + x), o1 = ldg<NC>(p1 + x);
-  out[x] = finish(cf, a, o1);
-  out[N + x] = finish(cf, b, o0);
+  core_1d<NC>(in + wrapm<I>(x - 1, N), in + wrapm<I>(x + 1, N), in + x, N, out + x, N, cf);
 }
 
-// square lattice, s = 4 (tables above), site (x, y) of the N x N box
-template <typename R, bool NC = true, typename I = int64_t>
-__device__ __forceinline__ void site_update_2d(const typename CplxOf<R>::T* __restrict__ in,
-                                               typename CplxOf<R>::T* __restrict__ out, I N, I x, I y,
-                                               const typename CoefOf<R>::T& cf) {
-  using C = typename CplxOf<R>::T;
-  const I vol = N * N;
-  const I xm = wrapm<I>(x - 1, N), xp = wrapm<I>(x + 1, N);
-  const I ym = wrapm<I>(y - 1, N), yp = wrapm<I>(y + 1, N);
+// square lattice, s = 4 (tables above): the cells x-1, x+1, y-1, y+1 and the own cell
+template <bool NC, typename C, typename CF, typename I>
+__device__ __forceinline__ void core_2d(const C* sxm, const C* sxp, const C* sym, const C* syp, const C* own, I cs,
+                                        C* dst, I ds, const CF& cf) {
   C S0 = {0, 0}, S1 = {0, 0}, S2 = {0, 0}, S3 = {0, 0};
   {  // h = +e1: source (x - 1, y)
-    const I i = y * N + xm;
-    C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
+    C a = ldg<NC>(sxm), b = ldg<NC>(sxm + cs), c = ldg<NC>(sxm + 2 * cs), d = ldg<NC>(sxm + 3 * cs);
     cmac<1, 1>(S0, a); cmac<1, -1>(S0, b); cmac<1, 1>(S1, a); cmac<1, -1>(S1, b);
     cmac<1, -1>(S2, c); cmac<-1, 1>(S2, d); cmac<-1, -1>(S3, c); cmac<1, 1>(S3, d);
   }
   {  // h = -e1: source (x + 1, y)
-    const I i = y * N + xp;
-    C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
+    C a = ldg<NC>(sxp), b = ldg<NC>(sxp + cs), c = ldg<NC>(sxp + 2 * cs), d = ldg<NC>(sxp + 3 * cs);
     cmac<1, 1>(S0, a); cmac<-1, 1>(S0, b); cmac<-1, -1>(S1, a); cmac<1, -1>(S1, b);
     cmac<1, -1>(S2, c); cmac<1, -1>(S2, d); cmac<1, 1>(S3, c); cmac<1, 1>(S3, d);
   }
   {  // h = +e2: source (x, y - 1)
-    const I i = ym * N + x;
-    C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
+    C a = ldg<NC>(sym), b = ldg<NC>(sym + cs), c = ldg<NC>(sym + 2 * cs), d = ldg<NC>(sym + 3 * cs);
     cmac<1, -1>(S0, a); cmac<1, 1>(S0, b); cmac<1, -1>(S1, a); cmac<1, 1>(S1, b);
     cmac<1, 1>(S2, c); cmac<-1, -1>(S2, d); cmac<-1, 1>(S3, c); cmac<1, -1>(S3, d);
   }
   {  // h = -e2: source (x, y + 1)
-    const I i = yp * N + x;
-    C a = ldg<NC>(in + i), b = ldg<NC>(in + vol + i), c = ldg<NC>(in + 2 * vol + i), d = ldg<NC>(in + 3 * vol + i);
+    C a = ldg<NC>(syp), b = ldg<NC>(syp + cs), c = ldg<NC>(syp + 2 * cs), d = ldg<NC>(syp + 3 * cs);
     cmac<1, -1>(S0, a); cmac<-1, -1>(S0, b); cmac<-1, 1>(S1, a); cmac<1, 1>(S1, b);
     cmac<1, 1>(S2, c); cmac<1, 1>(S2, d); cmac<1, -1>(S3, c); cmac<1, -1>(S3, d);
   }
+  C o0 = ldg<NC>(own), o1 = ldg<NC>(own + cs), o2 = ldg<NC>(own + 2 * cs), o3 = ldg<NC>(own + 3 * cs);
+  dst[0] = finish(cf, S0, o2);
+  dst[ds] = finish(cf, S1, o3);
+  dst[2 * ds] = finish(cf, S2, o0);
+  dst[3 * ds] = finish(cf, S3, o1);
+}
+
+// site (x, y) of the N x N box
+template <typename R, bool NC = true, typename I = int64_t>
+__device__ __forceinline__ void site_update_2d(const typename CplxOf<R>::T* __restrict__ in,
+                                               typename CplxOf<R>::T* __restrict__ out, I N, I x, I y,
+                                               const typename CoefOf<R>::T& cf) {
+  const I vol = N * N;
+  const I xm = wrapm<I>(x - 1, N), xp = wrapm<I>(x + 1, N);
+  const I ym = wrapm<I>(y - 1, N), yp = wrapm<I>(y + 1, N);
   const I i = y * N + x;
-  C o0 = ldg<NC>(in + i), o1 = ldg<NC>(in + vol + i), o2 = ldg<NC>(in + 2 * vol + i), o3 = ldg<NC>(in + 3 * vol + i);
-  out[i] = finish(cf, S0, o2);
-  out[vol + i] = finish(cf, S1, o3);
-  out[2 * vol + i] = finish(cf, S2, o0);
-  out[3 * vol + i] = finish(cf, S3, o1);
+  core_2d<NC>(in + y * N + xm, in + y * N + xp, in + ym * N + x, in + yp * N + x, in + i, vol, out + i, vol, cf);
 }
 
 // BCC, s = 4: output coset c at cell (x, y, z) reads coset 1-c at (per axis)
@@ -136,33 +144,38 @@ __device__ __forceinline__ void bcc_term(C& S0, C& S1, C& S2, C& S3, const C* __
   }
 }
 
+// src: component 0 of the other coset; (za, zb), (ya, yb), (xa, xb): its cells for h = +1 and
+// h = -1 per axis, with pitches sz (z) and sy (y); own / dst: component 0 of the own cell.
+template <bool NC, typename C, typename CF, typename I>
+__device__ __forceinline__ void core_3d(const C* src, I sz, I sy, I za, I zb, I ya, I yb, I xa, I xb, I cs,
+                                        const C* own, C* dst, I ds, const CF& cf) {
+  C S0 = {0, 0}, S1 = {0, 0}, S2 = {0, 0}, S3 = {0, 0};
+  bcc_term<+1, +1, +1, NC>(S0, S1, S2, S3, src + za * sz + ya * sy + xa, cs);
+  bcc_term<+1, -1, +1, NC>(S0, S1, S2, S3, src + za * sz + yb * sy + xa, cs);
+  bcc_term<-1, +1, +1, NC>(S0, S1, S2, S3, src + za * sz + ya * sy + xb, cs);
+  bcc_term<-1, -1, +1, NC>(S0, S1, S2, S3, src + za * sz + yb * sy + xb, cs);
+  bcc_term<+1, +1, -1, NC>(S0, S1, S2, S3, src + zb * sz + ya * sy + xa, cs);
+  bcc_term<+1, -1, -1, NC>(S0, S1, S2, S3, src + zb * sz + yb * sy + xa, cs);
+  bcc_term<-1, +1, -1, NC>(S0, S1, S2, S3, src + zb * sz + ya * sy + xb, cs);
+  bcc_term<-1, -1, -1, NC>(S0, S1, S2, S3, src + zb * sz + yb * sy + xb, cs);
+  C o0 = ldg<NC>(own), o1 = ldg<NC>(own + cs), o2 = ldg<NC>(own + 2 * cs), o3 = ldg<NC>(own + 3 * cs);
+  dst[0] = finish(cf, S0, o2);
+  dst[ds] = finish(cf, S1, o3);
+  dst[2 * ds] = finish(cf, S2, o0);
+  dst[3 * ds] = finish(cf, S3, o1);
+}
+
 template <typename R, bool NC = true, typename I = int64_t>
 __device__ __forceinline__ void site_update_3d(const typename CplxOf<R>::T* __restrict__ in,
                                                typename CplxOf<R>::T* __restrict__ out, I M, int c, I z, I y, I x,
                                                const typename CoefOf<R>::T& cf) {
-  using C = typename CplxOf<R>::T;
   const I plane = M * M, vol = plane * M;
   const I xa = wrapm<I>(x - 1 + c, M), xb = wrapm<I>(x + c, M);
   const I ya = wrapm<I>(y - 1 + c, M), yb = wrapm<I>(y + c, M);
   const I za = wrapm<I>(z - 1 + c, M), zb = wrapm<I>(z + c, M);
-  const C* src = in + (I)(1 - c) * 4 * vol;
-  C S0 = {0, 0}, S1 = {0, 0}, S2 = {0, 0}, S3 = {0, 0};
-  bcc_term<+1, +1, +1, NC>(S0, S1, S2, S3, src + za * plane + ya * M + xa, vol);
-  bcc_term<+1, -1, +1, NC>(S0, S1, S2, S3, src + za * plane + yb * M + xa, vol);
-  bcc_term<-1, +1, +1, NC>(S0, S1, S2, S3, src + za * plane + ya * M + xb, vol);
-  bcc_term<-1, -1, +1, NC>(S0, S1, S2, S3, src + za * plane + yb * M + xb, vol);
-  bcc_term<+1, +1, -1, NC>(S0, S1, S2, S3, src + zb * plane + ya * M + xa, vol);
-  bcc_term<+1, -1, -1, NC>(S0, S1, S2, S3, src + zb * plane + yb * M + xa, vol);
-  bcc_term<-1, +1, -1, NC>(S0, S1, S2, S3, src + zb * plane + ya * M + xb, vol);
-  bcc_term<-1, -1, -1, NC>(S0, S1, S2, S3, src + zb * plane + yb * M + xb, vol);
   const I i = z * plane + y * M + x;
-  const C* own = in + (I)c * 4 * vol + i;
-  C o0 = ldg<NC>(own), o1 = ldg<NC>(own + vol), o2 = ldg<NC>(own + 2 * vol), o3 = ldg<NC>(own + 3 * vol);
-  C* dst = out + (I)c * 4 * vol + i;
-  dst[0] = finish(cf, S0, o2);
-  dst[vol] = finish(cf, S1, o3);
-  dst[2 * vol] = finish(cf, S2, o0);
-  dst[3 * vol] = finish(cf, S3, o1);
+  core_3d<NC>(in + (I)(1 - c) * 4 * vol, plane, M, za, zb, ya, yb, xa, xb, vol, in + (I)c * 4 * vol + i,
+              out + (I)c * 4 * vol + i, vol, cf);
 }
 
 }  // namespace qw

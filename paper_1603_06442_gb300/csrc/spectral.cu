@@ -8,10 +8,11 @@
 //     D_k^t = cos(omega_k t) I - i sin(omega_k t) G^_k ,
 // the Chebyshev form (sin(omega t)/sin(omega) = U_{t-1}(cos omega)).
 // omega_k = atan2(sin omega_k, n u_k) (the paper's arccos(n u_k), Sec. 3.2) is
-// tabulated once per plan in FP64; each call reduces omega_k t modulo 2 pi in
-// FP64 (exact product low part included), so the phase stays accurate for
-// t up to ~1e6 and beyond.  Where sin(omega_k) = 0 (m = 0 and n~_k = 0)
-// D_k = +-I and G^_k is taken as 0.
+// tabulated once per plan: complex128 plans hold it as a double-double (~1e-31,
+// qw_dd.cuh), so the phase omega_k t reduced modulo 2 pi carries ~1e-16 of
+// rounding at any t instead of t ulp(omega_k); complex64 plans hold nu = omega/2pi
+// as an FP32 pair for an FP32 phase.  Where sin(omega_k) = 0 (m = 0 and
+// n~_k = 0) D_k = +-I and G^_k is taken as 0.
 //
 // BCC lattice (Eqs. bcc-dft, bcc-idft): the coset DFTs Psi^0, Psi^1 at the cell
 // wave vector kappa in [0, 2 pi)^3 hold the two BCC wave vectors
@@ -24,6 +25,7 @@
 
 #include <cmath>
 
+#include "qw_dd.cuh"
 #include "qw_spectral_dev.cuh"
 
 namespace qw {
@@ -49,11 +51,10 @@ SpecAxes spec_axes(const Geometry& g, const FftPlan& f) {
   return a;
 }
 
-// Per wave vector: omega (FP64) or, for complex64 plans (split = true), nu = omega / (2 pi)
-// as an unevaluated FP32 pair (hi, lo), hi = RN(nu), lo = RN(nu - hi): |nu - hi - lo| <=
-// 2^-48 nu, enough for the phase nu t of any t < 2^24 to ~1e-8 cycles with FP32 arithmetic.
-__global__ void omega_kernel(int dim, AxesDev a, int64_t count, double n, double m, double* __restrict__ omega,
-                             bool split) {
+// complex64 plans, per wave vector: nu = omega / (2 pi) (FP64) as an unevaluated FP32 pair
+// (hi, lo), hi = RN(nu), lo = RN(nu - hi): |nu - hi - lo| <= 2^-48 nu, enough for the phase
+// nu t of any t < 2^24 to ~1e-8 cycles with FP32 arithmetic.
+__global__ void omega_split_kernel(int dim, AxesDev a, double n, double m, float2* __restrict__ nu_out) {
   int64_t x, y, z;
   if (grid_pos(a, x, y, z)) {
     const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
@@ -64,15 +65,82 @@ __global__ void omega_kernel(int dim, AxesDev a, int64_t count, double n, double
       double u, nx, ny, nz;
       symbol_tab<double>(dim, a, f[0], f[1], f[2], q, u, nx, ny, nz);
       const double sw = sqrt(m * m + n * n * (nx * nx + ny * ny + nz * nz));
-      const double w = atan2(sw, n * u);
-      if (split) {
-        const double nu = w * 0.15915494309189533577;
-        const float hi = (float)nu;
-        reinterpret_cast<float2*>(omega)[idx * nq + q] = make_float2(hi, (float)(nu - (double)hi));
-      } else {
-        omega[idx * nq + q] = w;
-      }
+      const double nu = atan2(sw, n * u) * 0.15915494309189533577;
+      const float hi = (float)nu;
+      nu_out[idx * nq + q] = make_float2(hi, (float)(nu - (double)hi));
     }
+  }
+}
+
+// (cos, sin)(2 pi q / period) for q < len as double-double (cos hi, cos lo, sin hi, sin lo).
+__global__ void dd_table_kernel(double4* __restrict__ out, int64_t len, int64_t period) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= len) return;
+  dd c, s;
+  dd_cis_frac(q % period, period, c, s);
+  out[q] = make_double4(c.hi, c.lo, s.hi, s.lo);
+}
+
+// n = sqrt(1 - m^2) as double-double (m is exact in FP64)
+__global__ void dd_mass_kernel(double m, double2* out) {
+  const dd n = dd_sqrt(dd_sub(dd{1.0, 0.0}, dd_two_prod(m, m)));
+  *out = make_double2(n.hi, n.lo);
+}
+
+// complex128 plans: omega_k as a double-double (hi, lo) per stored wave vector, from the
+// symbol in double-double: per-axis tables of the same angles as the FP64 tables (2D:
+// pi q / N, q < 2N; BCC: the half angles pi f / M; the chain's 2 pi f / N is computed
+// directly) and the anchors of dd_omega.
+__global__ void omega_dd_kernel(int dim, AxesDev a, double m, const double2* __restrict__ nbox,
+                                const double4* __restrict__ tab0, const double4* __restrict__ tab1,
+                                const double4* __restrict__ tab2, const double4* __restrict__ anch,
+                                double2* __restrict__ omega) {
+  int64_t x, y, z;
+  if (!grid_pos(a, x, y, z)) return;
+  const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
+  int64_t f[3], fs;
+  wave_vectors(dim, x, y, z, a, f, fs);
+  const int nq = dim == 3 ? 2 : 1;
+  const dd n = dd{nbox->x, nbox->y};
+  const dd m2 = dd_two_prod(m, m), n2 = dd_mul(n, n);
+  for (int q = 0; q < nq; ++q) {
+    dd u, t1, t2, t3;  // u_k and n~_k (Eqs. weyl1d, weyl2d, weyl3d)
+    if (dim == 1) {
+      dd c, s;
+      dd_cis_frac(f[0], a.len[0], c, s);
+      u = c;
+      t1 = dd{0.0, 0.0};
+      t2 = t1;
+      t3 = s;
+    } else if (dim == 2) {
+      const int64_t N2 = 2 * a.len[0];
+      int64_t dm = f[0] - f[1];
+      if (dm < 0) dm += N2;
+      dd cx, sx, cy, sy;
+      dd_from4(tab0[f[0] + f[1]], cx, sx);
+      dd_from4(tab0[dm], cy, sy);
+      u = dd_mul(cx, cy);
+      t1 = dd_mul(sx, cy);
+      t2 = dd_mul(cx, sy);
+      t3 = dd_mul(sx, sy);
+    } else {
+      dd cx, sx, cy, sy, cz, sz;
+      dd_from4(tab0[f[0]], cx, sx);
+      dd_from4(tab1[f[1]], cy, sy);
+      dd_from4(tab2[f[2]], cz, sz);
+      if (q) {
+        cx = dd_neg(cx);
+        sx = dd_neg(sx);
+      }
+      u = dd_add(dd_mul(dd_mul(cx, cy), cz), dd_mul(dd_mul(sx, sy), sz));
+      t1 = dd_sub(dd_mul(dd_mul(sx, cy), cz), dd_mul(dd_mul(cx, sy), sz));
+      t2 = dd_add(dd_mul(dd_mul(cx, sy), cz), dd_mul(dd_mul(sx, cy), sz));
+      t3 = dd_sub(dd_mul(dd_mul(cx, cy), sz), dd_mul(dd_mul(sx, sy), cz));
+    }
+    const dd nt2 = dd_add(dd_add(dd_mul(t1, t1), dd_mul(t2, t2)), dd_mul(t3, t3));
+    const dd S = dd_sqrt(dd_add(m2, dd_mul(n2, nt2)));  // sin omega
+    const dd w = dd_omega(S, dd_mul(n, u), anch);
+    omega[idx * nq + q] = make_double2(w.hi, w.lo);
   }
 }
 
@@ -307,9 +375,49 @@ static dim3 grid3(const Geometry& g) {
   return dim3((unsigned)((g.nx + 255) / 256), (unsigned)g.ny, (unsigned)g.nz);
 }
 
+// complex128 plans: the double-double omega table (16 bytes per stored wave vector).  The
+// per-axis and anchor tables it needs live in one temporary buffer (synchronous).
+static qw_status launch_omega_table_dd(const Geometry& g, const SpecAxes& ax, double m, double* omega,
+                                       cudaStream_t st) {
+  const int64_t ext[3] = {g.nx, g.ny, g.nz};
+  int64_t len[3] = {0, 0, 0}, per[3] = {1, 1, 1};
+  if (g.dim == 2) {
+    len[0] = per[0] = 2 * g.nx;
+  } else if (g.dim == 3) {
+    for (int a = 0; a < 3; ++a) {
+      len[a] = ext[a];
+      per[a] = 2 * ext[a];
+    }
+  }
+  int64_t total = 1025 + 1;  // the anchors, then n
+  for (int a = 0; a < 3; ++a) total += len[a];
+  double4* buf = nullptr;
+  QW_CHECK_CUDA(cudaMalloc(&buf, total * sizeof(double4)));
+  double4* anch = buf;
+  double2* nbox = reinterpret_cast<double2*>(buf + 1025);
+  const double4* tabs[3] = {nullptr, nullptr, nullptr};
+  int64_t off = 1026;
+  for (int a = 0; a < 3; ++a) {
+    if (!len[a]) continue;
+    dd_table_kernel<<<(unsigned)((len[a] + 255) / 256), 256, 0, st>>>(buf + off, len[a], per[a]);
+    tabs[a] = buf + off;
+    off += len[a];
+  }
+  dd_table_kernel<<<5, 256, 0, st>>>(anch, 1025, 2048);
+  dd_mass_kernel<<<1, 1, 0, st>>>(m, nbox);
+  omega_dd_kernel<<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), m, nbox, tabs[0], tabs[1], tabs[2], anch,
+                                            reinterpret_cast<double2*>(omega));
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "double-double omega table");
+  return QW_OK;
+}
+
 qw_status launch_omega_table(const Geometry& g, const SpecAxes& ax, double n, double m, double* omega,
-                             cudaStream_t st, bool split) {
-  omega_kernel<<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), kcount(g), n, m, omega, split);
+                              cudaStream_t st, bool split) {
+  if (!split) return launch_omega_table_dd(g, ax, m, omega, st);
+  omega_split_kernel<<<grid3(g), 256, 0, st>>>(g.dim, to_dev(ax), n, m, reinterpret_cast<float2*>(omega));
   QW_CHECK_LAUNCH("omega table launch");
   return QW_OK;
 }

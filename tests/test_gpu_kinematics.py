@@ -128,3 +128,52 @@ def test_position_moments_rejects_null(qb):
     with pytest.raises(qb.QwError):
         qb.qw_position_moments(plan.handle, 0)
     plan.close()
+
+
+@pytest.mark.parametrize("dim,N,m,k0,sigma,times", [
+    (1, 4096, 0.1, [0.3], 40.0, [0, 200, 1000, 3000]),
+    (2, 128, 0.2, [0.4, 0.1], 10.0, [0, 50, 150, 300]),
+    (3, 64, 0.3, [0.2, 0.1, 0.3], 6.0, [0, 20, 60, 120]),
+])
+@pytest.mark.parametrize("path", ["spectral_c128", "spectral_c64", "stencil_c64"])
+def test_particle_state_overlap_above_fidelity_bound(qb, dim, N, m, k0, sigma, times, path):
+    """Sec. 5.1, Proposition "dispersive differential equation", Eq. overlap: a positive-
+    frequency particle state evolved on the GPU keeps an overlap with the second-order
+    (drift-diffusion) prediction of at least 1 - eps - gamma Sigma^3 t, and that overlap
+    equals the oracle's exact one (complex64: 1e-5 absolute; complex128: 1e-10)."""
+    method, dtype = path.split("_")
+    key = (1, 0) if dim == 1 else (1, 1)
+    psi0 = states.packet(dim, m, N, k0, sigma, [N / 2] * dim, {key: 1.0})
+    s = walk.n_components(dim)
+    k = spectral.k_grid(dim, N).reshape(-1, dim)
+    dk = states.wrapped_dk(dim, k, k0)
+    w = np.exp(-2 * sigma * sigma * np.sum(dk * dk, axis=-1))   # |g(k)|^2 of states.packet
+    om = walk.dispersion(dim, m, k)
+    om0 = float(walk.dispersion(dim, m, np.asarray(k0).reshape(1, dim))[0])
+    v, D = kinematics.drift(dim, m, k0), kinematics.diffusion(dim, m, k0)
+    ph2 = om0 + dk @ v + 0.5 * np.einsum("ki,ij,kj->k", dk, D, dk)
+    hat0 = spectral.dft(psi0, dim).reshape(s, -1)
+    plan = qb.Plan(dim, N, m, dtype)
+    x = to_dev(walk.to_device(dim, N, psi0), dtype)
+    done = 0
+    worst = 1.0
+    for t in times:
+        if method == "spectral":
+            x = to_dev(walk.to_device(dim, N, psi0), dtype)
+            plan.evolve_spectral(x, t)
+        else:
+            plan.step(x, t - done)
+            done = t
+        plan.sync()
+        got = walk.from_device(dim, N, x.cpu().numpy().astype(np.complex128).reshape(walk.to_device(dim, N, psi0).shape))
+        approx = spectral.idft((hat0 * np.exp(-1j * ph2 * t)).reshape(psi0.shape), dim)
+        ov = abs(np.vdot(approx, got)) / np.vdot(psi0, psi0).real
+        exact = kinematics.drift_diffusion_overlap(dim, m, k0, w, dk, om, t)
+        bound = kinematics.fidelity_bound(dim, m, k0, w, dk, [4.0 / (2.0 * sigma)] * dim, t)
+        tol = 1e-10 if dtype == "c128" else 1e-5
+        print("%s dim=%d t=%d: overlap GPU %.8f oracle %.8f bound %.5f" % (path, dim, t, ov, exact, bound))
+        assert abs(ov - exact) <= tol, (t, ov, exact)
+        assert ov >= bound - tol, (t, ov, bound)
+        worst = min(worst, ov - bound)
+    plan.close()
+    assert worst >= -1e-5

@@ -1,5 +1,5 @@
-"""GPU parity of qw_projection (probability projections onto axes and planes, Sec. 5.3) against
-the oracle, and the localised-state runs of Sec. 5.3 (light cone, projections along axes and
+"""GPU parity of qw_projection (probability projections onto axes and planes, Sec. 5.2) against
+the oracle, and the localised-state runs of Sec. 5.2 (light cone, projections along axes and
 onto the (x, y) plane).
 
 Tolerances, elementwise relative to the largest entry: complex128 1e-13, complex64 2e-6 (site
@@ -86,7 +86,7 @@ def localised_run(t):
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("t", [8, 16, 28])
 def test_localised_state_runs(qb, dtype, t):
-    """Sec. 5.3: a state on one site with spinor (1, 0, 0, 0), m = 0.03, evolved t steps; its
+    """Sec. 5.2: a state on one site with spinor (1, 0, 0, 0), m = 0.03, evolved t steps; its
     projections along y and x and onto the (x, y) plane against the oracle, and exact zeros
     beyond the light cone (t hops along every axis)."""
     dim, N, m = 3, 64, 0.03
@@ -158,7 +158,7 @@ def test_misaligned_complex64_projection_matches_aligned(qb):
     plan = qb.Plan(dim, N, 0.1, "c64")
     buf = torch.zeros(a.size + 1, dtype=torch.complex64, device="cuda")
     x_off = buf[1:]
-    x_off.copy_(torch.from_numpy(a))
+    x_off.copy_(torch.from_numpy(a.ravel()))
     assert x_off.data_ptr() % 16 == 8
     x = torch.from_numpy(a).cuda()
     psi = walk.from_device(dim, N, a.astype(np.complex128))

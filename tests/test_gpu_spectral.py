@@ -281,3 +281,31 @@ def test_weights_nan_without_fft_sizes(qb):
     with pytest.raises(qb.QwError):
         plan.evolve_spectral(to_dev(a, "c64"), 3)
     plan.close()
+
+
+def _golden_long_time():
+    import glob
+    import os
+    import re
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    out = []
+    for p in sorted(glob.glob(os.path.join(here, "long_time_spectral_*.txt"))):
+        d, N, m, s, t = re.search(r"_d(\d)_N(\d+)_m([\d.]+)_s(\d+)_t(\d+)\.txt$", p).groups()
+        out.append((int(d), int(N), float(m), int(s), int(t), p))
+    return out
+
+
+@pytest.mark.parametrize("case", _golden_long_time(), ids=lambda c: "d%d_N%d_t%d" % (c[0], c[1], c[4]))
+def test_fp64_long_time_vs_extended_precision(qb, case):
+    """FP64 spectral evolution at t ~ 1e5 .. 1e7 against the stored 50-digit evolution of the
+    same field (tests/golden, written by oracle.exact through make_long_time_spectral.py).
+    Both the GPU and the FP64 oracle (matrix power of D_k) are compared with it: the FP64
+    phase omega_k t carries ~t ulp(omega_k) in either, which the printed errors show."""
+    dim, N, m, seed, t, path = case
+    exact = np.loadtxt(path).view(complex).ravel()
+    a = inputs.random_field(dim, N, seed=seed)
+    got = run_spectral(qb, dim, N, m, "c128", a, t).ravel()
+    fp64 = walk.to_device(dim, N, spectral.evolve(dim, m, walk.from_device(dim, N, a), t)).ravel()
+    e_gpu, e_fp64 = rel_l2(got, exact), rel_l2(fp64, exact)
+    print("FP64 spectral t=%d dim=%d N=%d: GPU %.2e, FP64 oracle %.2e (vs 50-digit evolution)" % (t, dim, N, e_gpu, e_fp64))
+    assert e_gpu <= tol("c128", t)

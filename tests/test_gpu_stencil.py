@@ -221,7 +221,7 @@ def offset_view(a, dtype):
     npdt = np.complex64 if dtype == "c64" else np.complex128
     buf = torch.zeros(a.size + 1, dtype=torch.complex64 if dtype == "c64" else torch.complex128, device="cuda")
     v = buf[1:]
-    v.copy_(torch.from_numpy(np.ascontiguousarray(a.astype(npdt))))
+    v.copy_(torch.from_numpy(np.ascontiguousarray(a.astype(npdt)).ravel()))
     return v
 
 
@@ -237,7 +237,7 @@ def test_misaligned_complex64_view_takes_scalar_kernels(qb, variant):
     assert x.data_ptr() % 16 == 8
     plan.step(x, t)
     plan.sync()
-    got = x.cpu().numpy().astype(np.complex128)
+    got = x.cpu().numpy().astype(np.complex128).reshape(a.shape)
     plan.close()
     exp = walk.to_device(dim, N, walk.step(dim, m, walk.from_device(dim, N, a), t))
     assert rel_l2(got, exp) <= tol("c64", t)

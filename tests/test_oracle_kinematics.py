@@ -146,3 +146,98 @@ def test_positive_packet_spreads_by_the_velocity_spread_1d():
         assert abs((ct - c0) - t * t * var_v) <= 1e-6 * t * t * var_v
     D0 = kinematics.diffusion(dim, m, k0)[0, 0]
     assert abs(var_v / (D0 * D0 / (4 * sigma ** 2)) - 1) < 0.15
+
+
+# ---------------------------------------------------------------- fidelity bound (Eq. overlap)
+
+def test_third_derivatives_against_closed_form_1d():
+    """1D: omega = arccos(n cos k); its third derivative by symbolic differentiation."""
+    sp = pytest.importorskip("sympy")
+    ks, ns = sp.symbols("k n", real=True)
+    d3 = sp.lambdify((ks, ns), sp.diff(sp.acos(ns * sp.cos(ks)), ks, 3), "numpy")
+    for m in (0.05, 0.3, 0.8):
+        n = walk.mass_n(m)
+        for k in np.linspace(-2.9, 2.9, 13):
+            T = kinematics.third_derivatives(1, m, [k])
+            assert abs(T[0, 0, 0] - d3(k, n)) <= 1e-5 * max(1.0, abs(d3(k, n))), (m, k)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_third_derivatives_against_dispersion_differences(dim):
+    """2D/3D: against third-order central differences of the dispersion itself (the walk
+    module's arccos(n u_k), a separate code path), every index triple."""
+    rng = np.random.default_rng(40 + dim)
+    om = lambda k: float(walk.dispersion(dim, 0.3, np.asarray(k).reshape(1, dim))[0])
+    h = 2e-3
+    for _ in range(4):
+        k = rng.uniform(-2.5, 2.5, size=dim)
+        T = kinematics.third_derivatives(dim, 0.3, k)
+        for i, j, l in itertools.product(range(dim), repeat=3):
+            e = np.eye(dim) * h
+            f = lambda a, b, c: om(k + a * e[i] + b * e[j] + c * e[l])
+            num = sum(sa * sb * sc * f(sa, sb, sc) for sa in (1, -1) for sb in (1, -1) for sc in (1, -1)) / (8 * h ** 3)
+            assert abs(T[i, j, l] - num) <= 2e-3 * max(1.0, abs(num)), (dim, i, j, l)
+
+
+def _particle(dim, N, m, k0, sigma):
+    k = spectral.k_grid(dim, N).reshape(-1, dim)
+    dk = states.wrapped_dk(dim, k, k0)
+    w = np.exp(-2 * sigma * sigma * np.sum(dk * dk, axis=-1))    # |g(k)|^2 of states.packet
+    return k, dk, w
+
+
+@pytest.mark.parametrize("dim,N,m,k0,sigma", [(1, 512, 0.15, [0.3], 12.0), (2, 64, 0.2, [0.4, 0.1], 5.0),
+                                              (3, 32, 0.3, [0.2, 0.1, 0.3], 3.0)])
+def test_overlap_equals_position_space_overlap(dim, N, m, k0, sigma):
+    """The k-space overlap formula against the position-space route: the packet evolved by
+    the Fourier oracle (U^t), and the second-order state built as its own DFT with the
+    phases omega' + v.K + K.D.K/2, compared by an inner product over the sites."""
+    psi0 = states.packet(dim, m, N, k0, sigma, [N / 2] * dim, {(1, 1) if dim > 1 else (1, 0): 1.0})
+    k, dk, w = _particle(dim, N, m, k0, sigma)
+    om0 = float(walk.dispersion(dim, m, np.asarray(k0).reshape(1, dim))[0])
+    v, D = kinematics.drift(dim, m, k0), kinematics.diffusion(dim, m, k0)
+    ph2 = om0 + dk @ v + 0.5 * np.einsum("ki,ij,kj->k", dk, D, dk)
+    s = walk.n_components(dim)
+    for t in (7, 40):
+        exact = spectral.evolve(dim, m, psi0, t)
+        approx = spectral.idft((spectral.dft(psi0, dim).reshape(s, -1) * np.exp(-1j * ph2 * t)).reshape(psi0.shape),
+                               dim)
+        pos = abs(np.vdot(approx, exact)) / np.vdot(psi0, psi0).real
+        kov = kinematics.drift_diffusion_overlap(dim, m, k0, w, dk, walk.dispersion(dim, m, k), t)
+        assert abs(pos - kov) < 1e-10, (t, pos, kov)
+
+
+def test_overlap_small_t_expansion():
+    """1 - |E exp(-i R t)| = t^2 Var(R) / 2 + O(t^4): the overlap's leading decrease is the
+    variance of the Taylor remainder R_k of omega beyond second order."""
+    dim, N, m, k0, sigma = 1, 2048, 0.1, [0.5], 20.0
+    k, dk, w = _particle(dim, N, m, k0, sigma)
+    om = walk.dispersion(dim, m, k)
+    R = om - (float(walk.dispersion(dim, m, np.array([k0]))[0]) + dk @ kinematics.drift(dim, m, k0)
+              + 0.5 * np.einsum("ki,ij,kj->k", dk, kinematics.diffusion(dim, m, k0), dk))
+    p = w / w.sum()
+    var = float(np.sum(p * R * R) - np.sum(p * R) ** 2)
+    for t in (1.0, 3.0, 10.0):
+        loss = 1.0 - kinematics.drift_diffusion_overlap(dim, m, k0, w, dk, om, t)
+        assert abs(loss - 0.5 * var * t * t) <= 1e-3 * 0.5 * var * t * t, t
+
+
+@pytest.mark.parametrize("dim,N,m,k0,sigma", [(1, 4096, 0.1, [0.3], 40.0), (1, 4096, 0.6, [1.2], 25.0),
+                                              (2, 128, 0.2, [0.4, 0.1], 10.0), (3, 64, 0.3, [0.2, 0.1, 0.3], 6.0)])
+def test_overlap_stays_above_the_bound(dim, N, m, k0, sigma):
+    """The exact overlap of Eq. overlap is never below the Proposition's bound 1 - eps -
+    gamma Sigma^3 t (box half-width 4 standard deviations of |g|^2 per axis), over times
+    where the bound is informative; the bound is not vacuous early on."""
+    k, dk, w = _particle(dim, N, m, k0, sigma)
+    om = walk.dispersion(dim, m, k)
+    sb = [4.0 / (2.0 * sigma)] * dim
+    t1 = None
+    for t in np.linspace(0, 4000, 41):
+        b = kinematics.fidelity_bound(dim, m, k0, w, dk, sb, t)
+        if b <= 0:
+            t1 = t
+            break
+        o = kinematics.drift_diffusion_overlap(dim, m, k0, w, dk, om, t)
+        assert o >= b, (t, o, b)
+    assert kinematics.fidelity_bound(dim, m, k0, w, dk, sb, 0.0) > 0.999
+    assert t1 is None or t1 > 40

@@ -1,4 +1,4 @@
-"""Pins of the oracle's probability projections (Sec. 5.3: projections of a localised state's
+"""Pins of the oracle's probability projections (Sec. 5.2: projections of a localised state's
 distribution onto axes and planes) against brute force and the walk's light cone.
 
 * brute force: a pure-Python loop over the sites of tiny boxes (every lattice, every keep set);
