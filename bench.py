@@ -290,6 +290,20 @@ def run_ours(args, rank, world, local):
     plan.run_host([host] * e2e_steps, S, stream=stream)
     torch.cuda.synchronize(dev)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    # the same run again with per-field CUDA events on both streams (not the timed number):
+    # how long each copy took and how long each step waited for its field
+    plan.set_host_timing(True)
+    plan.run_host([host] * e2e_steps, S, stream=stream)
+    tl = plan.host_timing(e2e_steps)
+    plan.set_host_timing(False)
+    copy_ms = [c1 - c0 for c0, c1, _, _, _ in tl]
+    # field j's step could start when field j-1's observables ended; it waited for its copy
+    waits = [max(0.0, tl[j][2] - tl[j - 1][4]) for j in range(1, len(tl))]
+    overlap = {"copy_ms_median": float(np.median(copy_ms)), "copy_ms_max": float(max(copy_ms)),
+               "step_wait_for_copy_ms_mean": float(np.mean(waits)), "step_wait_for_copy_ms_max": float(max(waits)),
+               "copy_hidden_frac": float(1.0 - sum(waits) / max(1e-9, sum(copy_ms[1:]))),
+               "note": "second, event-instrumented run of the same fields: per field the copy's duration on the "
+                       "copy stream and how long its step started after the previous field's observables"}
     # the host-to-device copy alone (pinned field), for the e2e bound
     h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     h0.record(stream)
@@ -337,7 +351,7 @@ def run_ours(args, rank, world, local):
                      "site_steps_per_s_at_roofline": peak * 1e9 / (2 * field_bytes) * sites},
         "e2e": {"value": sites * S / (e2e_ms / 1e3), "unit": "site-steps/s",
                 "h2d_bytes_per_step": field_bytes, "d2h_bytes_per_step": 48, "ms_per_step": e2e_ms,
-                "h2d_GBps": h2d_GBps, "api": "qw_run_host",
+                "h2d_GBps": h2d_GBps, "api": "qw_run_host", "overlap": overlap,
                 "note": "pinned host field copied every step inside qw_run_host; the library copies the next "
                         "step's field on its copy stream while this one computes (two device buffers)"},
         "gpu_launches": args.steps * launches_per_step,
@@ -378,7 +392,7 @@ def extra_measurements(qb, dev, stream):
     psi = torch.zeros(plan.elems, dtype=torch.complex64, device=dev)
     psi[::7] = 1e-3
     variants = {}
-    for name in ("plain", "vec", "tma", "tma2"):
+    for name in ("plain", "vec", "tma", "tma2", "fused"):
         try:
             plan.set_stencil(name)
         except qb.QwError:
@@ -394,10 +408,51 @@ def extra_measurements(qb, dev, stream):
         variants[name] = {"ms_per_step": ms, "site_steps_per_s": plan.sites / (ms / 1e3),
                           "equiv_GBps_at_64B_per_site_step": 2 * plan.elems * 8 / (ms / 1e3) / 1e9}
     out["c64_stencil_variants"] = variants
+    plan.close()
+    out["lattices"] = lattice_stencil_measurement(qb, dev, stream)
     out["spectral"] = spectral_measurement(qb, dev, stream)
     out["projection"] = projection_measurement(qb, dev, stream)
     out["batched"] = batched_measurement(qb, dev, stream)
     out["served"] = served_measurement(qb, dev, stream)
+    return out
+
+
+def lattice_stencil_measurement(qb, dev, stream):
+    """complex64 stencil on the square lattice (N = 8192, 4-spinor, 2.1 GB) and the chain
+    (N = 2^28, 2-spinor, 2.1 GB), both larger than L2: every variant the plan supports, the
+    FUSED one at the depth and tile the autotuner picks; roofline fraction at the unfused
+    bytes per site-step (64 B square lattice, 32 B chain) against the measured copy rate."""
+    import torch
+    peak, kind = measured_peaks()
+    out = {}
+    for dim, N in ((2, 8192), (1, 1 << 28)):
+        plan = qb.Plan(dim, N, 0.1, "c64")
+        psi = torch.zeros(plan.elems, dtype=torch.complex64, device=dev)
+        psi[::7] = 1e-3
+        bps = 2 * plan.elems * 8 / plan.sites   # unfused algorithmic bytes per site-step
+        rate_tuned = plan.autotune(stream)
+        tuned = {"variant": [k for k, v in qb.STENCILS.items() if v == plan.stencil][0],
+                 "fusion": plan.fusion(), "autotune_rate": rate_tuned}
+        res = {}
+        for name in ("plain", "fused"):
+            plan.set_stencil(name)
+            if name == "fused" and tuned["variant"] != "fused":
+                continue
+            plan.step(psi, 4, stream)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n = 24
+            s0.record(stream)
+            plan.step(psi, n, stream)
+            s1.record(stream)
+            plan.sync(stream)
+            ms = s0.elapsed_time(s1) / n
+            r = plan.sites / (ms / 1e3)
+            res[name] = {"ms_per_step": ms, "site_steps_per_s": r, "frac_of_hbm_unfused": r * bps / 1e9 / peak}
+        out["%dd_N%d" % (dim, N)] = {"sites": plan.sites, "bytes_per_site_step_unfused": bps, "variants": res,
+                                     "autotuned": tuned, "peak_kind": kind}
+        plan.close()
+        del psi
+        torch.cuda.empty_cache()
     return out
 
 

@@ -61,14 +61,19 @@ typedef enum { QW_C64 = 0, QW_C128 = 1 } qw_dtype;
  * complex64, N/2 % 64 == 0; two cells per thread, 16-byte loads.  TMA: BCC,
  * complex64, N/2 % 64 == 0; z-marching CTAs with TMA-staged shared-memory tiles.
  * TMA2: as TMA with two steps fused per pass over HBM (temporal fusion; an odd
- * remaining step runs as TMA).  AUTO restores the default: the first supported
- * of TMA2 > TMA > VEC > PLAIN; qw_plan_autotune measures and keeps the fastest. */
+ * remaining step runs as TMA).  FUSED: any lattice and size, complex64; box
+ * tiles of the field with a halo loaded into shared memory, `depth` steps per
+ * launch (temporal fusion of depth 2..4, tile box and depth set by
+ * qw_plan_set_fusion or the autotuner).  AUTO restores the default: the first
+ * supported of TMA2 > TMA > VEC > PLAIN; qw_plan_autotune measures every
+ * variant (FUSED with several depths and boxes) and keeps the fastest. */
 typedef enum {
   QW_STENCIL_AUTO = 0,
   QW_STENCIL_PLAIN = 1,
   QW_STENCIL_VEC = 2,
   QW_STENCIL_TMA = 3,
-  QW_STENCIL_TMA2 = 4
+  QW_STENCIL_TMA2 = 4,
+  QW_STENCIL_FUSED = 5
 } qw_stencil_variant;
 
 typedef struct qw_plan_s* qw_plan;
@@ -118,8 +123,20 @@ qw_status qw_plan_set_stencil(qw_plan plan, int variant);
 /* The stencil variant qw_step currently uses (never QW_STENCIL_AUTO); -1 for null. */
 int qw_plan_get_stencil(qw_plan plan);
 
-/* Autotuner of the stencil: times every variant that supports the plan (fusion
- * depth 1 or 2, data movement PLAIN / VEC / TMA) for 8 steps on a temporary
+/* Temporal fusion of the FUSED variant: `depth` (2..4) steps per launch on tiles
+ * of box[0..dim) cells (x, y, z; on the BCC lattice both cosets of the cells),
+ * read with a halo of depth cells per side (depth/2 rounded up on the BCC
+ * lattice).  Defaults: depth 4 with 2048 cells (chain) or 64x16 (square
+ * lattice), depth 2 with 8x8x6 (BCC).
+ * Errors: QW_EINVAL (null argument, complex128 plan, depth outside 2..4, or a
+ * tile that with its halo needs more than 227 KB of shared memory). */
+qw_status qw_plan_set_fusion(qw_plan plan, int depth, const int* box);
+/* The FUSED variant's depth and box (either pointer may be NULL; box: 3 ints). */
+qw_status qw_plan_get_fusion(qw_plan plan, int* depth, int* box);
+
+/* Autotuner of the stencil: times every variant that supports the plan (data
+ * movement PLAIN / VEC / TMA, fusion depth 2 with TMA2, and FUSED with depth 2,
+ * 3, 4 on three tile boxes per lattice) for 8 steps on a temporary
  * field (allocated and freed here; the caller's fields are not touched) and keeps
  * the fastest; *best_rate (optional) receives its site-steps/s.  Synchronous.
  * Errors: QW_EINVAL, QW_ENOMEM, QW_ECUDA, QW_ETIMEOUT. */
@@ -229,6 +246,20 @@ int64_t qw_projection_elems(qw_plan plan, int keep);
  * null entry), QW_ENOMEM (device buffers), QW_ECUDA, QW_ETIMEOUT (as qw_sync). */
 qw_status qw_run_host(qw_plan plan, const void* const* psi_host, void* const* psi_out_host, int count,
                       int64_t nsteps, qw_obs* out, void* stream);
+
+/* Per-field timing of qw_run_host, to measure how well the host-to-device copies
+ * overlap the computation.  on != 0: later qw_run_host calls record CUDA events
+ * (timing enabled) at the start and end of each field's copy in (copy stream),
+ * the start and end of its steps and the end of its observables (compute
+ * stream); on = 0 stops recording.  Errors: QW_EINVAL (null plan). */
+qw_status qw_plan_set_host_timing(qw_plan plan, int on);
+
+/* For the first `count` fields of the last timed qw_run_host call, writes 5
+ * doubles per field (HOST array of 5 * count): copy start, copy end, step start,
+ * step end, observables end, in ms from the first field's copy start.
+ * Synchronises with those events.  Errors: QW_EINVAL (null argument, or count
+ * not in 1 .. the fields of the last timed run), QW_ECUDA. */
+qw_status qw_plan_host_timing(qw_plan plan, double* out, int count);
 
 /* ---------------------------------------------------------------- batches
  * Many independent walks of uneven size advanced together by one persistent

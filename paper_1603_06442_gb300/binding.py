@@ -14,8 +14,8 @@ LIB_PATH = os.path.join(PKG, "libqw.so")
 
 QW_OK, QW_EINVAL, QW_ENOMEM, QW_ECUDA, QW_ETIMEOUT, QW_EAGAIN, QW_EBUSY, QW_ENOTFOUND = range(8)
 QW_C64, QW_C128 = 0, 1
-QW_STENCIL_AUTO, QW_STENCIL_PLAIN, QW_STENCIL_VEC, QW_STENCIL_TMA, QW_STENCIL_TMA2 = 0, 1, 2, 3, 4
-STENCILS = {"auto": 0, "plain": 1, "vec": 2, "tma": 3, "tma2": 4}
+QW_STENCIL_AUTO, QW_STENCIL_PLAIN, QW_STENCIL_VEC, QW_STENCIL_TMA, QW_STENCIL_TMA2, QW_STENCIL_FUSED = 0, 1, 2, 3, 4, 5
+STENCILS = {"auto": 0, "plain": 1, "vec": 2, "tma": 3, "tma2": 4, "fused": 5}
 STATUS_NAMES = {0: "QW_OK", 1: "QW_EINVAL", 2: "QW_ENOMEM", 3: "QW_ECUDA", 4: "QW_ETIMEOUT",
                 5: "QW_EAGAIN", 6: "QW_EBUSY", 7: "QW_ENOTFOUND"}
 
@@ -108,6 +108,11 @@ _SIGS = {
     "qw_batch_debug_stall": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
     "qw_batch_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "qw_batch_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qw_obs), ctypes.c_void_p]),
+    "qw_plan_set_fusion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "qw_plan_get_fusion": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
+    "qw_plan_set_host_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "qw_plan_host_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "qw_step_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_void_p]),
     "qw_evolve_spectral": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
@@ -278,6 +283,28 @@ def qw_server_stats(server):
 
 def qw_server_destroy(server):
     _check(load().qw_server_destroy(server))
+
+
+def qw_plan_set_fusion(plan, depth, box):
+    b = (ctypes.c_int * 3)(*[int(v) for v in (list(box) + [1, 1, 1])[:3]])
+    _check(load().qw_plan_set_fusion(plan, int(depth), b))
+
+
+def qw_plan_get_fusion(plan):
+    d, b = ctypes.c_int(), (ctypes.c_int * 3)()
+    _check(load().qw_plan_get_fusion(plan, ctypes.byref(d), b))
+    return d.value, list(b)
+
+
+def qw_plan_set_host_timing(plan, on):
+    _check(load().qw_plan_set_host_timing(plan, 1 if on else 0))
+
+
+def qw_plan_host_timing(plan, count):
+    """[(copy_start, copy_end, step_start, step_end, obs_end) in ms] for the last timed run."""
+    out = (ctypes.c_double * (5 * count))()
+    _check(load().qw_plan_host_timing(plan, out, int(count)))
+    return [tuple(out[5 * j:5 * j + 5]) for j in range(count)]
 
 
 def qw_step_static(dim, N, mass, dtype, psi, nsteps, stream=None):
@@ -556,6 +583,18 @@ class Plan:
         for f in list(fields) + list(out_fields or []):
             self.check_host_field(f)
         return qw_run_host(self.handle, fields, nsteps, out_fields, stream)
+
+    def set_fusion(self, depth, box):
+        qw_plan_set_fusion(self.handle, depth, box)
+
+    def fusion(self):
+        return qw_plan_get_fusion(self.handle)
+
+    def set_host_timing(self, on=True):
+        qw_plan_set_host_timing(self.handle, on)
+
+    def host_timing(self, count):
+        return qw_plan_host_timing(self.handle, count)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1,6 +1,7 @@
 // C ABI entry points: errors, plans, the stepping driver and observables.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -10,6 +11,7 @@
 #include <new>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "qw_internal.cuh"
 
@@ -195,6 +197,11 @@ qw_status qw_plan_create(int dim, int64_t N, double mass, qw_dtype dtype, qw_pla
       return st;
     }
   }
+  // FUSED variant defaults: depth and tile box per lattice (qw_plan_autotune measures others)
+  p->fuse_depth = g.dim == 3 ? 2 : 4;
+  p->fuse_box[0] = g.dim == 1 ? 2048 : (g.dim == 2 ? 64 : 8);
+  p->fuse_box[1] = g.dim == 1 ? 1 : (g.dim == 2 ? 16 : 8);
+  p->fuse_box[2] = g.dim == 3 ? 6 : 1;
   p->stencil = default_stencil(p);
   *out = p;
   return QW_OK;
@@ -221,6 +228,7 @@ qw_status qw_plan_destroy(qw_plan p) {
     if (p->ev_stepped[b]) cudaEventDestroy(p->ev_stepped[b]);
   }
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
   if (p->proj_partials) cudaFree(p->proj_partials);
   if (p->hstage) cudaFreeHost(p->hstage);
   delete p;
@@ -242,7 +250,7 @@ qw_status qw_step(qw_plan p, void* psi, int64_t nsteps, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the VEC, TMA and TMA2 kernels move 16-byte vectors: a complex64 field that is only
   // 8-byte aligned (e.g. a view one element into an allocation) takes the PLAIN kernel
-  const int variant = aligned16(psi) ? p->stencil : QW_STENCIL_PLAIN;
+  const int variant = (aligned16(psi) || p->stencil == QW_STENCIL_FUSED) ? p->stencil : QW_STENCIL_PLAIN;
   void* cur = psi;
   void* nxt = p->scratch;
   for (int64_t i = 0; i < nsteps;) {
@@ -254,6 +262,9 @@ qw_status qw_step(qw_plan p, void* psi, int64_t nsteps, void* stream) {
     } else if (variant == QW_STENCIL_TMA || variant == QW_STENCIL_TMA2) {
       st = launch_step_tma(p->g, p->n, p->mass, cur, nxt, p->tma_items, p->tma_nitems, p->dev_flags,
                            p->dev_flags + 1, s);
+    } else if (variant == QW_STENCIL_FUSED) {
+      done = (int)std::min<int64_t>(p->fuse_depth, nsteps - i);
+      st = launch_step_fused(p->g, p->fuse_depth, p->fuse_box, done, p->n, p->mass, cur, nxt, s);
     } else {
       st = launch_step(p->g, p->dtype, variant, p->n, p->mass, cur, nxt, s);
     }
@@ -277,7 +288,8 @@ qw_status qw_plan_set_stencil(qw_plan p, int variant) {
     p->stencil = default_stencil(p);
     return QW_OK;
   }
-  if (!stencil_supported(p->g, p->dtype, variant)) {
+  if (variant == QW_STENCIL_FUSED ? !fused_step_supported(p->g, p->dtype, p->fuse_depth, p->fuse_box)
+                                  : !stencil_supported(p->g, p->dtype, variant)) {
     set_error("qw_plan_set_stencil: variant %d does not support dim=%d N=%lld dtype=%d", variant, p->g.dim,
               (long long)p->g.N, (int)p->dtype);
     return QW_EINVAL;
@@ -351,14 +363,34 @@ qw_status qw_plan_autotune(qw_plan p, void* stream, double* best_rate) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int saved = p->stencil;
-  int best = saved;
+  const int saved = p->stencil, saved_depth = p->fuse_depth;
+  const int saved_box[3] = {p->fuse_box[0], p->fuse_box[1], p->fuse_box[2]};
+  int best = saved, best_depth = saved_depth, best_box[3] = {saved_box[0], saved_box[1], saved_box[2]};
   double best_r = -1.0;
-  const int variants[] = {QW_STENCIL_PLAIN, QW_STENCIL_VEC, QW_STENCIL_TMA, QW_STENCIL_TMA2};
+  // candidates: the data-movement variants, then FUSED with depth 2..4 and a few tile boxes
+  struct Cand {
+    int v, depth, box[3];
+  };
+  std::vector<Cand> cands;
+  for (int v : {QW_STENCIL_PLAIN, QW_STENCIL_VEC, QW_STENCIL_TMA, QW_STENCIL_TMA2}) cands.push_back({v, 0, {0, 0, 0}});
+  const int boxes[3][3][3] = {{{1024, 1, 1}, {2048, 1, 1}, {4096, 1, 1}},
+                              {{32, 16, 1}, {64, 16, 1}, {64, 8, 1}},
+                              {{8, 8, 4}, {8, 8, 6}, {16, 8, 4}}};
+  for (int dpt = 2; dpt <= 4; ++dpt)
+    for (int k = 0; k < 3; ++k) {
+      const int* b = boxes[p->g.dim - 1][k];
+      cands.push_back({QW_STENCIL_FUSED, dpt, {b[0], b[1], b[2]}});
+    }
   const int64_t steps = 8;
-  for (int v : variants) {
-    if (!stencil_supported(p->g, p->dtype, v)) continue;
-    p->stencil = v;
+  for (const Cand& c : cands) {
+    if (c.v == QW_STENCIL_FUSED ? !fused_step_supported(p->g, p->dtype, c.depth, c.box)
+                                : !stencil_supported(p->g, p->dtype, c.v))
+      continue;
+    p->stencil = c.v;
+    if (c.v == QW_STENCIL_FUSED) {
+      p->fuse_depth = c.depth;
+      for (int a = 0; a < 3; ++a) p->fuse_box[a] = c.box[a];
+    }
     st = qw_step(p, tmp, 2, s);  // warm-up
     if (st != QW_OK) break;
     cudaEventRecord(e0, s);
@@ -371,9 +403,15 @@ qw_status qw_plan_autotune(qw_plan p, void* stream, double* best_rate) {
     const double r = (double)p->g.sites * steps / (ms * 1e-3);
     if (r > best_r) {
       best_r = r;
-      best = v;
+      best = c.v;
+      if (c.v == QW_STENCIL_FUSED) {
+        best_depth = c.depth;
+        for (int a = 0; a < 3; ++a) best_box[a] = c.box[a];
+      }
     }
   }
+  p->fuse_depth = st == QW_OK ? best_depth : saved_depth;
+  for (int a = 0; a < 3; ++a) p->fuse_box[a] = st == QW_OK ? best_box[a] : saved_box[a];
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamSynchronize(s);
@@ -580,7 +618,22 @@ qw_status qw_run_host(qw_plan p, const void* const* psi_host, void* const* psi_o
   // in(j + 2) waits for field j's observables (ev_freed) and follows out(j) in stream order.
   // Field j's sums go to the pinned stage j % 2; the host reads them only after field
   // j + 1's step is enqueued, so the device never waits for the host between fields.
+  const bool timing = p->host_timing;
+  if (timing) {
+    while ((int)p->tev.size() < 5 * count) {
+      cudaEvent_t e;
+      QW_CHECK_CUDA(cudaEventCreate(&e));
+      p->tev.push_back(e);
+    }
+    p->tev_fields = 0;
+  }
+  // timing event i of field j (no-op unless timing is on)
+  auto mark = [&](int j, int i, cudaStream_t on) -> cudaError_t {
+    return timing ? cudaEventRecord(p->tev[5 * j + i], on) : cudaSuccess;
+  };
+  QW_CHECK_CUDA(mark(0, 0, cs));
   QW_CHECK_CUDA(cudaMemcpyAsync(p->hbuf[0], psi_host[0], bytes, cudaMemcpyHostToDevice, cs));
+  QW_CHECK_CUDA(mark(0, 1, cs));
   QW_CHECK_CUDA(cudaEventRecord(p->ev_copied[0], cs));
   bool kspace = false;
   int done = 0;  // fields whose observables are on the host
@@ -589,12 +642,16 @@ qw_status qw_run_host(qw_plan p, const void* const* psi_host, void* const* psi_o
     if (j + 1 < count) {
       const int nb = b ^ 1;
       if (j >= 1) QW_CHECK_CUDA(cudaStreamWaitEvent(cs, p->ev_freed[nb], 0));
+      QW_CHECK_CUDA(mark(j + 1, 0, cs));
       QW_CHECK_CUDA(cudaMemcpyAsync(p->hbuf[nb], psi_host[j + 1], bytes, cudaMemcpyHostToDevice, cs));
+      QW_CHECK_CUDA(mark(j + 1, 1, cs));
       QW_CHECK_CUDA(cudaEventRecord(p->ev_copied[nb], cs));
     }
     QW_CHECK_CUDA(cudaStreamWaitEvent(s, p->ev_copied[b], 0));
+    QW_CHECK_CUDA(mark(j, 2, s));
     st = qw_step(p, p->hbuf[b], nsteps, stream);
     if (st != QW_OK) break;
+    QW_CHECK_CUDA(mark(j, 3, s));
     if (psi_out_host) {
       QW_CHECK_CUDA(cudaEventRecord(p->ev_stepped[b], s));
       QW_CHECK_CUDA(cudaStreamWaitEvent(cs, p->ev_stepped[b], 0));
@@ -603,6 +660,8 @@ qw_status qw_run_host(qw_plan p, const void* const* psi_host, void* const* psi_o
     st = obs_enqueue(p, p->hbuf[b], s, p->hstage + 8 * b, &kspace);
     if (st != QW_OK) break;
     QW_CHECK_CUDA(cudaEventRecord(p->ev_freed[b], s));
+    QW_CHECK_CUDA(mark(j, 4, s));
+    if (timing) p->tev_fields = j + 1;
     if (j >= 1) {  // the previous field's sums
       const cudaError_t e = cudaEventSynchronize(p->ev_freed[b ^ 1]);
       if (e != cudaSuccess) {
@@ -621,6 +680,56 @@ qw_status qw_run_host(qw_plan p, const void* const* psi_host, void* const* psi_o
   const cudaError_t e = cudaStreamSynchronize(cs);
   if (st == QW_OK && e != cudaSuccess) return cuda_fail(e, "qw_run_host: copy stream");
   return st;
+}
+
+qw_status qw_plan_set_host_timing(qw_plan p, int on) {
+  if (!p) {
+    set_error("qw_plan_set_host_timing: null plan");
+    return QW_EINVAL;
+  }
+  p->host_timing = on != 0;
+  return QW_OK;
+}
+
+qw_status qw_plan_host_timing(qw_plan p, double* out, int count) {
+  if (!p || !out || count < 1 || count > p->tev_fields) {
+    set_error("qw_plan_host_timing: null argument, or count outside 1..%d (fields of the last timed run)",
+              p ? p->tev_fields : 0);
+    return QW_EINVAL;
+  }
+  qw_status st = use_device(p);
+  if (st != QW_OK) return st;
+  QW_CHECK_CUDA(cudaEventSynchronize(p->tev[5 * (count - 1) + 4]));
+  for (int j = 0; j < count; ++j)
+    for (int i = 0; i < 5; ++i) {
+      float ms = 0.f;
+      QW_CHECK_CUDA(cudaEventElapsedTime(&ms, p->tev[0], p->tev[5 * j + i]));
+      out[5 * j + i] = ms;
+    }
+  return QW_OK;
+}
+
+qw_status qw_plan_set_fusion(qw_plan p, int depth, const int* box) {
+  if (!p || !box || !fused_step_supported(p->g, p->dtype, depth, box)) {
+    set_error("qw_plan_set_fusion: null argument, or depth %d / this box not supported for the plan "
+              "(complex64, depth 2..4, the tile and its halo in 227 KB of shared memory)",
+              depth);
+    return QW_EINVAL;
+  }
+  p->fuse_depth = depth;
+  for (int a = 0; a < 3; ++a) p->fuse_box[a] = a < p->g.dim ? box[a] : 1;
+  return QW_OK;
+}
+
+qw_status qw_plan_get_fusion(qw_plan p, int* depth, int* box) {
+  if (!p) {
+    set_error("qw_plan_get_fusion: null plan");
+    return QW_EINVAL;
+  }
+  if (depth) *depth = p->fuse_depth;
+  if (box)
+    for (int a = 0; a < 3; ++a) box[a] = p->fuse_box[a];
+  return QW_OK;
 }
 
 }  // extern "C"

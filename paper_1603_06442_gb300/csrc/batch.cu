@@ -136,6 +136,14 @@ __device__ __forceinline__ int wrap_into(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// v mod n for v usually within one period of [0, n) (a halo never reaches further unless
+// the walk is smaller than its halo): compares first, a division only otherwise.
+__device__ __forceinline__ int wrap_near(int v, int n) {
+  if (v < 0) v += n;
+  else if (v >= n) v -= n;
+  return (v < 0 || v >= n) ? wrap_into(v, n) : v;
+}
+
 // Region of coset c computed at step k of a fused round of `steps` steps, in the tile's
 // local frame [0, e + 2H) per axis (axes >= dim: [0, 1)).  The last step covers the tile
 // [H, H + e); going back one step, a BCC coset-0 cell needs coset 1 at m - 1 .. m and a
@@ -145,6 +153,7 @@ __device__ __forceinline__ int wrap_into(int v, int n) {
 __device__ __forceinline__ void step_region(const BatchWalk& W, const int (&e)[3], int steps, int k, int c,
                                             int (&lo)[3], int (&hi)[3]) {
   const int j = steps - k, H = W.halo;
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (a >= W.dim) {
       lo[a] = 0;
@@ -172,10 +181,11 @@ __device__ __forceinline__ void cp_async_all() {
 // One fused round of `steps` steps of tile (t0, t1, t2) of walk W: load the tile and its
 // halo from `in` into shared buffer A, step there (A -> B -> A ...), write the last step
 // to `out`.  Shared layout: [coset][component][z][y][x] with extents E = e + 2H per axis.
-__device__ void fused_round(const BatchWalk& W, const int (&t3)[3], int steps, const float2* in, float2* out,
+__device__ __forceinline__ void fused_round(const BatchWalk& W, const int (&t3)[3], int steps, const float2* in, float2* out,
                             float2* smA, float2* smB) {
   const int tid = threadIdx.x;
   int s0[3], e[3], E[3];
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     s0[a] = t3[a] * W.ext[a];
     e[a] = min(W.ext[a], W.n[a] - s0[a]);
@@ -184,26 +194,19 @@ __device__ void fused_round(const BatchWalk& W, const int (&t3)[3], int steps, c
   const int H = W.halo;
   const int sy = E[0], sz = E[0] * E[1], P = sz * E[2];  // pitches, component stride
   const int nx = W.n[0], ny = W.n[1], nz = W.n[2];
-  // ---- load: warp w copies rows w, w + 8, ... (a row: one (coset, component, z, y)), lanes
-  // walk x with the periodic wrap
+  // ---- load: this thread's cells of the halo box (x fastest, so consecutive threads copy
+  // consecutive x), each with every coset-component plane; periodic wrap per axis
   {
-    const int rows = W.ncos * W.ncomp * E[2] * E[1];
-    const int lane = tid & 31;
-    int gx0 = wrap_into(s0[0] - (W.dim >= 1 ? H : 0) + lane, nx);
-    for (int row = tid >> 5; row < rows; row += kBatchThreads / 32) {
-      const int y = row % E[1], r2 = row / E[1];
-      const int z = r2 % E[2], cq = r2 / E[2];
-      const int gy = W.dim >= 2 ? wrap_into(s0[1] - H + y, ny) : 0;
-      const int gz = W.dim >= 3 ? wrap_into(s0[2] - H + z, nz) : 0;
-      const float2* src = in + (int64_t)cq * W.vol + ((int64_t)gz * ny + gy) * nx;
-      float2* dst = smA + (int64_t)cq * P + z * sz + y * sy;
-      int gx = gx0;
-      for (int x = lane; x < E[0]; x += 32) {
-        cp_async8(dst + x, src + gx);
-        gx += 32;
-        while (gx >= nx) gx -= nx;
-      }
-    }
+    const int lo3[3] = {0, 0, 0};
+    const int planes = W.ncos * W.ncomp;
+    for_box<kBatchThreads>(lo3, E, tid, [&](int x, int y, int z) {
+      const int gx = wrap_near(s0[0] - H + x, nx);
+      const int gy = W.dim >= 2 ? wrap_near(s0[1] - H + y, ny) : 0;
+      const int gz = W.dim >= 3 ? wrap_near(s0[2] - H + z, nz) : 0;
+      const float2* src = in + ((int64_t)gz * ny + gy) * nx + gx;
+      float2* dst = smA + z * sz + y * sy + x;
+      for (int p = 0; p < planes; ++p) cp_async8(dst + p * P, src + (int64_t)p * W.vol);
+    });
     cp_async_all();
   }
   __syncthreads();
@@ -214,28 +217,33 @@ __device__ void fused_round(const BatchWalk& W, const int (&t3)[3], int steps, c
     for (int c = 0; c < W.ncos; ++c) {
       int lo[3], hi[3];
       step_region(W, e, steps, k, c, lo, hi);
-      const float2* own_base = cur + c * 4 * P;
       for_box<kBatchThreads>(lo, hi, tid, [&](int x, int y, int z) {
-        const int i = z * sz + y * sy + x;
-        float2* dst;
-        int ds;
+        const int i = z * sz + y * sy + x;  // 32-bit shared-memory offsets
+        float2 r[4];
+        if (W.dim == 1) {
+          float2 r2[2];
+          core_1d<false>(cur + i - 1, cur + i + 1, cur + i, P, r2, W.cf);
+          r[0] = r2[0];
+          r[1] = r2[1];
+        } else if (W.dim == 2) {
+          core_2d<false>(cur + i - 1, cur + i + 1, cur + i - sy, cur + i + sy, cur + i, P, r, W.cf);
+        } else {
+          core_3d<false>(cur + (1 - c) * 4 * P, sz, sy, z - 1 + c, z + c, y - 1 + c, y + c, x - 1 + c, x + c, P,
+                         cur + c * 4 * P + i, r, W.cf);
+        }
         if (last) {  // the tile's own cells: [H, H + e) maps to [s0, s0 + e), no wrap
           const int gx = s0[0] - H + x;
           const int gy = W.dim >= 2 ? s0[1] - H + y : 0;
           const int gz = W.dim >= 3 ? s0[2] - H + z : 0;
-          dst = out + (int64_t)c * W.ncomp * W.vol + ((int64_t)gz * ny + gy) * nx + gx;
-          ds = W.vol;
+          float2* dst = out + (int64_t)c * W.ncomp * W.vol + ((int64_t)gz * ny + gy) * nx + gx;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (q < W.ncomp) dst[(int64_t)q * W.vol] = r[q];
         } else {
-          dst = nxt + c * 4 * P + i;
-          ds = P;
-        }
-        if (W.dim == 1) {
-          core_1d<false>(cur + i - 1, cur + i + 1, cur + i, P, dst, ds, W.cf);
-        } else if (W.dim == 2) {
-          core_2d<false>(cur + i - 1, cur + i + 1, cur + i - sy, cur + i + sy, cur + i, P, dst, ds, W.cf);
-        } else {
-          core_3d<false>(cur + (1 - c) * 4 * P, sz, sy, z - 1 + c, z + c, y - 1 + c, y + c, x - 1 + c, x + c, P,
-                         own_base + i, dst, ds, W.cf);
+          float2* dst = nxt + c * 4 * P + i;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (q < W.ncomp) dst[q * P] = r[q];
         }
       });
     }
@@ -250,8 +258,9 @@ __device__ void fused_round(const BatchWalk& W, const int (&t3)[3], int steps, c
 
 // The plain round of tile (t0, t1, t2): every cell of the tile (both cosets) updated once
 // from global memory, or (copy round) copied from buf[1] to buf[0].
-__device__ void plain_round(const BatchWalk& W, const int (&t3)[3], bool copy, const float2* in, float2* out) {
+__device__ __forceinline__ void plain_round(const BatchWalk& W, const int (&t3)[3], bool copy, const float2* in, float2* out) {
   int lo[3], hi[3];
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     lo[a] = t3[a] * W.ext[a];
     hi[a] = min(W.n[a], lo[a] + W.ext[a]);
@@ -276,7 +285,7 @@ __device__ void plain_round(const BatchWalk& W, const int (&t3)[3], bool copy, c
 // FUSED = false: every walk has depth 1 (no shared memory, high occupancy);
 // FUSED = true: walks of depth >= 2 run fused rounds in dynamic shared memory.
 template <bool FUSED>
-__global__ void __launch_bounds__(kBatchThreads, FUSED ? 2 : 6)
+__global__ void __launch_bounds__(kBatchThreads, FUSED ? 3 : 6)
     batch_kernel(const BatchWalk* __restrict__ walks, const BatchGroup* __restrict__ groups,
                  const int64_t* __restrict__ group_item0, int ngroups, const int64_t* __restrict__ tile_prefix,
                  const int64_t* __restrict__ round_prefix, int64_t total_items, unsigned int* __restrict__ done,
@@ -363,7 +372,9 @@ __global__ void __launch_bounds__(kBatchThreads, FUSED ? 2 : 6)
     if (s_abort) break;
     const int64_t s = s_round;
     const int tile = s_tile;
-    const BatchWalk& W = walks[s_walk];
+    // the walk's descriptor in registers: read through a reference, every field access in the
+    // per-cell loops would be a global load that the field stores may alias
+    const BatchWalk W = walks[s_walk];
     // claim the next item now (every thread read s_next before the barrier above): the
     // atomic's round trip overlaps this item's work, and the claimed item is started by
     // this CTA right after this one, so every claimed item still gets done
@@ -392,6 +403,21 @@ __global__ void __launch_bounds__(kBatchThreads, FUSED ? 2 : 6)
       cuda::atomic_ref<unsigned int, cuda::thread_scope_device>(done[W.tile_base + tile])
           .store((unsigned int)(s + 1), cuda::memory_order_release);
     }
+  }
+}
+
+// qw_step's FUSED variant: `steps` updates of a whole field in one launch, one CTA per
+// box tile (grid-stride), each a fused round from `in` to `out` (every tile reads only `in`,
+// so the launch needs no dependency waits; successive launches ping-pong).
+__global__ void __launch_bounds__(kBatchThreads, 3)
+    fused_step_kernel(BatchWalk W, int steps, const float2* __restrict__ in, float2* __restrict__ out) {
+  extern __shared__ float2 smem_dyn[];
+  const int P = (W.ncos * W.ncomp) * (W.ext[0] + 2 * W.halo) * (W.dim >= 2 ? W.ext[1] + 2 * W.halo : 1) *
+                (W.dim >= 3 ? W.ext[2] + 2 * W.halo : 1);
+  for (int tile = blockIdx.x; tile < W.ntiles; tile += gridDim.x) {
+    const int t3[3] = {tile % W.nt[0], (tile / W.nt[0]) % W.nt[1], tile / (W.nt[0] * W.nt[1])};
+    fused_round(W, t3, steps, in, out, smem_dyn, smem_dyn + P);
+    __syncthreads();
   }
 }
 
@@ -545,6 +571,47 @@ static BatchWalk make_walk(const qw_walk& d, void* partner, const qw_batch_tilin
   W.cf = make_coef32(d.dim, std::sqrt(1.0 - d.mass * d.mass), d.mass);
   W.tile_base = 0;
   return W;
+}
+
+bool fused_step_supported(const Geometry& g, qw_dtype dt, int depth, const int* box) {
+  if (dt != QW_C64 || depth < 2 || depth > 4 || g.elems >= (int64_t(1) << 31)) return false;
+  int ext[3];
+  for (int a = 0; a < 3; ++a) {
+    if (a < g.dim && box[a] < 1) return false;
+    ext[a] = a < g.dim ? (int)std::min<int64_t>(box[a], a == 0 ? g.nx : (a == 1 ? g.ny : g.nz)) : 1;
+  }
+  return fused_smem(g.dim, depth, ext) <= kMaxBatchSmem;
+}
+
+qw_status launch_step_fused(const Geometry& g, int depth, const int* box, int steps, double n, double m,
+                            const void* in, void* out, cudaStream_t st) {
+  if (!fused_step_supported(g, QW_C64, depth, box) || steps < 1 || steps > depth) {
+    set_error("fused stencil: unsupported geometry, depth %d, box or step count %d", depth, steps);
+    return QW_EINVAL;
+  }
+  qw_walk d;
+  d.dim = g.dim;
+  d.N = g.N;
+  d.mass = m;
+  d.t = steps;
+  d.psi_dev = const_cast<void*>(in);
+  qw_batch_tiling t = default_tiling();
+  t.depth[g.dim - 1] = depth;
+  for (int a = 0; a < 3; ++a) t.box[g.dim - 1][a] = box[a];
+  BatchWalk W = make_walk(d, out, t);
+  W.cf = make_coef32(g.dim, n, m);
+  const size_t smem = fused_smem(W.dim, W.depth, W.ext);
+  qw_status sa = smem_attr(fused_step_kernel, (int)smem);
+  if (sa != QW_OK) return sa;
+  int dev = 0, nsm = 0, per_sm = 0;
+  QW_CHECK_CUDA(cudaGetDevice(&dev));
+  QW_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  QW_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_step_kernel, kBatchThreads, smem));
+  const int grid = (int)std::min<int64_t>(W.ntiles, (int64_t)std::max(1, per_sm) * nsm);
+  fused_step_kernel<<<grid, kBatchThreads, smem, st>>>(W, steps, static_cast<const float2*>(in),
+                                                       static_cast<float2*>(out));
+  QW_CHECK_LAUNCH("fused stencil launch");
+  return QW_OK;
 }
 
 // Build the walk table, groups and prefix arrays for the current tiling, and upload them.

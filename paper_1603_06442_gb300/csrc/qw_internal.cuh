@@ -91,6 +91,11 @@ qw_status launch_step_tma2(const Geometry& g, double n, double m, const void* in
                            int nitems, int* err, int* next_item, cudaStream_t st);
 qw_status launch_step_tma(const Geometry& g, double n, double m, const void* in, void* out, const int4* items,
                           int nitems, int* err, int* next_item, cudaStream_t st);
+// FUSED: `steps` <= depth updates in one launch, box tiles of the field and a halo in shared
+// memory (complex64, any geometry whose tile fits shared memory; batch.cu).
+bool fused_step_supported(const Geometry& g, qw_dtype dt, int depth, const int* box);
+qw_status launch_step_fused(const Geometry& g, int depth, const int* box, int steps, double n, double m,
+                            const void* in, void* out, cudaStream_t st);
 
 // ---- device reduction helpers ------------------------------------------------
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -200,6 +205,8 @@ struct qw_plan_s {
   int device;
   size_t elem_bytes;
   int stencil;          // qw_stencil_variant in use (never AUTO after creation)
+  int fuse_depth;       // FUSED variant: steps per launch and tile box (x, y, z cells)
+  int fuse_box[3];
   void* scratch;        // one field: ping-pong partner of the caller's buffer
   int* dev_flags;       // [0] error word of bounded device waits, [1] work counter
   int4* tma_items;      // work-item table of the TMA stencil (device), or null
@@ -222,6 +229,12 @@ struct qw_plan_s {
   cudaStream_t copy_stream;
   cudaEvent_t ev_copied[2], ev_freed[2], ev_stepped[2];
   double* hstage;  // 2 x 8 doubles (pinned): observables of the two fields in flight
+  // optional per-field timing of qw_run_host: for field j, events (timing enabled) at its copy's
+  // start and end (copy stream) and at its step's start and end and its observables' end
+  // (compute stream); tev_fields = fields recorded by the last run
+  bool host_timing;
+  std::vector<cudaEvent_t> tev;
+  int tev_fields;
   // probability projections: chunk partials, grown on demand
   double* proj_partials;
   int64_t proj_cap;

@@ -64,12 +64,12 @@ __device__ __forceinline__ I wrapm(I v, I M) { return v < 0 ? v + M : (v >= M ? 
 
 // chain, s = 2: psi'_0(x) = n psi_0(x-1) + i m psi_1(x), psi'_1(x) = i m psi_0(x) + n psi_1(x+1)
 template <bool NC, typename C, typename CF, typename I>
-__device__ __forceinline__ void core_1d(const C* xm, const C* xp, const C* own, I cs, C* dst, I ds, const CF& cf) {
+__device__ __forceinline__ void core_1d(const C* xm, const C* xp, const C* own, I cs, C (&r)[2], const CF& cf) {
   C a = ldg<NC>(xm);        // psi_0(x - 1)
   C b = ldg<NC>(xp + cs);   // psi_1(x + 1)
   C o0 = ldg<NC>(own), o1 = ldg<NC>(own + cs);
-  dst[0] = finish(cf, a, o1);
-  dst[ds] = finish(cf, b, o0);
+  r[0] = finish(cf, a, o1);
+  r[1] = finish(cf, b, o0);
 }
 
 // (I: index type; the batched kernel's walks fit 32-bit indices)
@@ -77,39 +77,47 @@ template <typename R, bool NC = true, typename I = int64_t>
 __device__ __forceinline__ void site_update_1d(const typename CplxOf<R>::T* __restrict__ in,
                                                typename CplxOf<R>::T* __restrict__ out, I N, I x,
                                                const typename CoefOf<R>::T& cf) {
-  core_1d<NC>(in + wrapm<I>(x - 1, N), in + wrapm<I>(x + 1, N), in + x, N, out + x, N, cf);
+  typename CplxOf<R>::T r[2];
+  core_1d<NC>(in + wrapm<I>(x - 1, N), in + wrapm<I>(x + 1, N), in + x, N, r, cf);
+  out[x] = r[0];
+  out[N + x] = r[1];
 }
 
-// square lattice, s = 4 (tables above): the cells x-1, x+1, y-1, y+1 and the own cell
+// Complex helpers of the factored updates: rho = 1 + i, rhob = 1 - i.
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C rho(C z) { return C{z.x - z.y, z.x + z.y}; }
+template <typename C> __device__ __forceinline__ C rhob(C z) { return C{z.x + z.y, z.y - z.x}; }
+template <typename C> __device__ __forceinline__ C addi(C a, C b) { return C{a.x - b.y, a.y + b.x}; }  // a + i b
+
+// square lattice, s = 4: the four outputs from the cells A = x-1, B = x+1, C = y-1, D = y+1
+// (sources of h = +e1, -e1, +e2, -e2) and the own cell.  From the tables above, rho = 1 + i:
+//   S0 = (P + Q) + (U - V),  S1 = (P + Q) - (U - V),
+//     P = rho A0 + rhob A1, Q = rhob C0 + rho C1, U = rho (B0 + i B1), V = rho (D1 + i D0);
+//   S2 = rhob (a + b) + rho (c + d),  S3 = rho (b - a) + rhob (d - c),
+//     a = A2 - A3, b = B2 + B3, c = C2 - C3, d = D2 + D3
+// (56 real additions instead of 128 term by term), then the mass step (finish).
 template <bool NC, typename C, typename CF, typename I>
 __device__ __forceinline__ void core_2d(const C* sxm, const C* sxp, const C* sym, const C* syp, const C* own, I cs,
-                                        C* dst, I ds, const CF& cf) {
-  C S0 = {0, 0}, S1 = {0, 0}, S2 = {0, 0}, S3 = {0, 0};
-  {  // h = +e1: source (x - 1, y)
-    C a = ldg<NC>(sxm), b = ldg<NC>(sxm + cs), c = ldg<NC>(sxm + 2 * cs), d = ldg<NC>(sxm + 3 * cs);
-    cmac<1, 1>(S0, a); cmac<1, -1>(S0, b); cmac<1, 1>(S1, a); cmac<1, -1>(S1, b);
-    cmac<1, -1>(S2, c); cmac<-1, 1>(S2, d); cmac<-1, -1>(S3, c); cmac<1, 1>(S3, d);
-  }
-  {  // h = -e1: source (x + 1, y)
-    C a = ldg<NC>(sxp), b = ldg<NC>(sxp + cs), c = ldg<NC>(sxp + 2 * cs), d = ldg<NC>(sxp + 3 * cs);
-    cmac<1, 1>(S0, a); cmac<-1, 1>(S0, b); cmac<-1, -1>(S1, a); cmac<1, -1>(S1, b);
-    cmac<1, -1>(S2, c); cmac<1, -1>(S2, d); cmac<1, 1>(S3, c); cmac<1, 1>(S3, d);
-  }
-  {  // h = +e2: source (x, y - 1)
-    C a = ldg<NC>(sym), b = ldg<NC>(sym + cs), c = ldg<NC>(sym + 2 * cs), d = ldg<NC>(sym + 3 * cs);
-    cmac<1, -1>(S0, a); cmac<1, 1>(S0, b); cmac<1, -1>(S1, a); cmac<1, 1>(S1, b);
-    cmac<1, 1>(S2, c); cmac<-1, -1>(S2, d); cmac<-1, 1>(S3, c); cmac<1, -1>(S3, d);
-  }
-  {  // h = -e2: source (x, y + 1)
-    C a = ldg<NC>(syp), b = ldg<NC>(syp + cs), c = ldg<NC>(syp + 2 * cs), d = ldg<NC>(syp + 3 * cs);
-    cmac<1, -1>(S0, a); cmac<-1, -1>(S0, b); cmac<-1, 1>(S1, a); cmac<1, 1>(S1, b);
-    cmac<1, 1>(S2, c); cmac<1, 1>(S2, d); cmac<1, -1>(S3, c); cmac<1, -1>(S3, d);
-  }
-  C o0 = ldg<NC>(own), o1 = ldg<NC>(own + cs), o2 = ldg<NC>(own + 2 * cs), o3 = ldg<NC>(own + 3 * cs);
-  dst[0] = finish(cf, S0, o2);
-  dst[ds] = finish(cf, S1, o3);
-  dst[2 * ds] = finish(cf, S2, o0);
-  dst[3 * ds] = finish(cf, S3, o1);
+                                        C (&r)[4], const CF& cf) {
+  const C A0 = ldg<NC>(sxm), A1 = ldg<NC>(sxm + cs), A2 = ldg<NC>(sxm + 2 * cs), A3 = ldg<NC>(sxm + 3 * cs);
+  const C B0 = ldg<NC>(sxp), B1 = ldg<NC>(sxp + cs), B2 = ldg<NC>(sxp + 2 * cs), B3 = ldg<NC>(sxp + 3 * cs);
+  const C C0 = ldg<NC>(sym), C1 = ldg<NC>(sym + cs), C2 = ldg<NC>(sym + 2 * cs), C3 = ldg<NC>(sym + 3 * cs);
+  const C D0 = ldg<NC>(syp), D1 = ldg<NC>(syp + cs), D2 = ldg<NC>(syp + 2 * cs), D3 = ldg<NC>(syp + 3 * cs);
+  const C P = addi(cadd(A0, A1), csub(A0, A1));  // rho A0 + rhob A1
+  const C Q = addi(cadd(C0, C1), csub(C1, C0));  // rhob C0 + rho C1
+  const C U = rho(addi(B0, B1));
+  const C V = rho(addi(D1, D0));
+  const C PQ = cadd(P, Q), UV = csub(U, V);
+  const C S0 = cadd(PQ, UV), S1 = csub(PQ, UV);
+  const C a = csub(A2, A3), b = cadd(B2, B3), c = csub(C2, C3), d = cadd(D2, D3);
+  const C S2 = cadd(rhob(cadd(a, b)), rho(cadd(c, d)));
+  const C S3 = cadd(rho(csub(b, a)), rhob(csub(d, c)));
+  const C o0 = ldg<NC>(own), o1 = ldg<NC>(own + cs), o2 = ldg<NC>(own + 2 * cs), o3 = ldg<NC>(own + 3 * cs);
+  r[0] = finish(cf, S0, o2);
+  r[1] = finish(cf, S1, o3);
+  r[2] = finish(cf, S2, o0);
+  r[3] = finish(cf, S3, o1);
 }
 
 // site (x, y) of the N x N box
@@ -121,48 +129,58 @@ __device__ __forceinline__ void site_update_2d(const typename CplxOf<R>::T* __re
   const I xm = wrapm<I>(x - 1, N), xp = wrapm<I>(x + 1, N);
   const I ym = wrapm<I>(y - 1, N), yp = wrapm<I>(y + 1, N);
   const I i = y * N + x;
-  core_2d<NC>(in + y * N + xm, in + y * N + xp, in + ym * N + x, in + yp * N + x, in + i, vol, out + i, vol, cf);
+  typename CplxOf<R>::T r[4];
+  core_2d<NC>(in + y * N + xm, in + y * N + xp, in + ym * N + x, in + yp * N + x, in + i, vol, r, cf);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) out[i + q * vol] = r[q];
 }
 
-// BCC, s = 4: output coset c at cell (x, y, z) reads coset 1-c at (per axis)
-// m - 1 + c for h = +1 and m + c for h = -1 (the site x - h of the other sublattice).
-template <int HX, int HY, int HZ, bool NC = true, typename C, typename I>
-__device__ __forceinline__ void bcc_term(C& S0, C& S1, C& S2, C& S3, const C* __restrict__ src, I vol) {
-  constexpr int P = HX * HY * HZ;
-  if constexpr (HZ == 1) {
-    C a = ldg<NC>(src), b = ldg<NC>(src + vol), d = ldg<NC>(src + 3 * vol);
-    cmac<1, -P>(S0, a);
-    cmac<HX, -HY>(S0, b);
-    cmac<-HX, HY>(S2, d);
-    cmac<1, -P>(S3, d);
-  } else {
-    C a = ldg<NC>(src), b = ldg<NC>(src + vol), c = ldg<NC>(src + 2 * vol);
-    cmac<HX, HY>(S1, a);
-    cmac<1, -P>(S1, b);
-    cmac<1, -P>(S2, c);
-    cmac<-HX, -HY>(S3, c);
-  }
-}
-
+// BCC, s = 4: output coset c at cell (x, y, z) reads coset 1-c at (per axis) m - 1 + c for
+// h = +1 and m + c for h = -1 (the site x - h of the other sublattice).  From the tables above,
+// with the sources s_{hx hy} of the plane of h_z = +1 and t_{hx hy} of the plane of h_z = -1,
+// components a, b, c, d, and rho = 1 + i:
+//   S0 = rhob [(a_{++} + b_{++}) + (a_{--} - b_{--})] + rho [(a_{+-} + b_{+-}) + (a_{-+} - b_{-+})]   (s)
+//   S1 = rho [(a_{++} + b_{++}) + (b_{--} - a_{--})] + rhob [(a_{+-} + b_{+-}) + (b_{-+} - a_{-+})]   (t)
+//   S2 = rhob (d_{--} - d_{++}) + rho (d_{-+} - d_{+-})  (s)  +  rho (c_{++} + c_{--}) + rhob (c_{+-} + c_{-+})  (t)
+//   S3 = rhob (d_{++} + d_{--}) + rho (d_{+-} + d_{-+})  (s)  +  rho (c_{--} - c_{++}) + rhob (c_{-+} - c_{+-})  (t)
+// (88 real additions instead of 128 term by term), then the mass step (finish).
 // src: component 0 of the other coset; (za, zb), (ya, yb), (xa, xb): its cells for h = +1 and
-// h = -1 per axis, with pitches sz (z) and sy (y); own / dst: component 0 of the own cell.
+// h = -1 per axis, with pitches sz (z) and sy (y); own: component 0 of the own cell.
 template <bool NC, typename C, typename CF, typename I>
 __device__ __forceinline__ void core_3d(const C* src, I sz, I sy, I za, I zb, I ya, I yb, I xa, I xb, I cs,
-                                        const C* own, C* dst, I ds, const CF& cf) {
-  C S0 = {0, 0}, S1 = {0, 0}, S2 = {0, 0}, S3 = {0, 0};
-  bcc_term<+1, +1, +1, NC>(S0, S1, S2, S3, src + za * sz + ya * sy + xa, cs);
-  bcc_term<+1, -1, +1, NC>(S0, S1, S2, S3, src + za * sz + yb * sy + xa, cs);
-  bcc_term<-1, +1, +1, NC>(S0, S1, S2, S3, src + za * sz + ya * sy + xb, cs);
-  bcc_term<-1, -1, +1, NC>(S0, S1, S2, S3, src + za * sz + yb * sy + xb, cs);
-  bcc_term<+1, +1, -1, NC>(S0, S1, S2, S3, src + zb * sz + ya * sy + xa, cs);
-  bcc_term<+1, -1, -1, NC>(S0, S1, S2, S3, src + zb * sz + yb * sy + xa, cs);
-  bcc_term<-1, +1, -1, NC>(S0, S1, S2, S3, src + zb * sz + ya * sy + xb, cs);
-  bcc_term<-1, -1, -1, NC>(S0, S1, S2, S3, src + zb * sz + yb * sy + xb, cs);
-  C o0 = ldg<NC>(own), o1 = ldg<NC>(own + cs), o2 = ldg<NC>(own + 2 * cs), o3 = ldg<NC>(own + 3 * cs);
-  dst[0] = finish(cf, S0, o2);
-  dst[ds] = finish(cf, S1, o3);
-  dst[2 * ds] = finish(cf, S2, o0);
-  dst[3 * ds] = finish(cf, S3, o1);
+                                        const C* own, C (&r)[4], const CF& cf) {
+  C S0, S1, S2, S3;
+  {  // h_z = +1: plane za, components a, b, d
+    const C* pp = src + za * sz + ya * sy + xa;  // (h_x, h_y) = (+, +)
+    const C* pm = src + za * sz + yb * sy + xa;  // (+, -)
+    const C* mp = src + za * sz + ya * sy + xb;  // (-, +)
+    const C* mm = src + za * sz + yb * sy + xb;  // (-, -)
+    const C app = ldg<NC>(pp), bpp = ldg<NC>(pp + cs), dpp = ldg<NC>(pp + 3 * cs);
+    const C apm = ldg<NC>(pm), bpm = ldg<NC>(pm + cs), dpm = ldg<NC>(pm + 3 * cs);
+    const C amp = ldg<NC>(mp), bmp = ldg<NC>(mp + cs), dmp = ldg<NC>(mp + 3 * cs);
+    const C amm = ldg<NC>(mm), bmm = ldg<NC>(mm + cs), dmm = ldg<NC>(mm + 3 * cs);
+    S0 = cadd(rhob(cadd(cadd(app, bpp), csub(amm, bmm))), rho(cadd(cadd(apm, bpm), csub(amp, bmp))));
+    S2 = cadd(rhob(csub(dmm, dpp)), rho(csub(dmp, dpm)));
+    S3 = cadd(rhob(cadd(dpp, dmm)), rho(cadd(dpm, dmp)));
+  }
+  {  // h_z = -1: plane zb, components a, b, c
+    const C* pp = src + zb * sz + ya * sy + xa;
+    const C* pm = src + zb * sz + yb * sy + xa;
+    const C* mp = src + zb * sz + ya * sy + xb;
+    const C* mm = src + zb * sz + yb * sy + xb;
+    const C app = ldg<NC>(pp), bpp = ldg<NC>(pp + cs), cpp = ldg<NC>(pp + 2 * cs);
+    const C apm = ldg<NC>(pm), bpm = ldg<NC>(pm + cs), cpm = ldg<NC>(pm + 2 * cs);
+    const C amp = ldg<NC>(mp), bmp = ldg<NC>(mp + cs), cmp = ldg<NC>(mp + 2 * cs);
+    const C amm = ldg<NC>(mm), bmm = ldg<NC>(mm + cs), cmm = ldg<NC>(mm + 2 * cs);
+    S1 = cadd(rho(cadd(cadd(app, bpp), csub(bmm, amm))), rhob(cadd(cadd(apm, bpm), csub(bmp, amp))));
+    S2 = cadd(S2, cadd(rho(cadd(cpp, cmm)), rhob(cadd(cpm, cmp))));
+    S3 = cadd(S3, cadd(rho(csub(cmm, cpp)), rhob(csub(cmp, cpm))));
+  }
+  const C o0 = ldg<NC>(own), o1 = ldg<NC>(own + cs), o2 = ldg<NC>(own + 2 * cs), o3 = ldg<NC>(own + 3 * cs);
+  r[0] = finish(cf, S0, o2);
+  r[1] = finish(cf, S1, o3);
+  r[2] = finish(cf, S2, o0);
+  r[3] = finish(cf, S3, o1);
 }
 
 template <typename R, bool NC = true, typename I = int64_t>
@@ -174,8 +192,11 @@ __device__ __forceinline__ void site_update_3d(const typename CplxOf<R>::T* __re
   const I ya = wrapm<I>(y - 1 + c, M), yb = wrapm<I>(y + c, M);
   const I za = wrapm<I>(z - 1 + c, M), zb = wrapm<I>(z + c, M);
   const I i = z * plane + y * M + x;
-  core_3d<NC>(in + (I)(1 - c) * 4 * vol, plane, M, za, zb, ya, yb, xa, xb, vol, in + (I)c * 4 * vol + i,
-              out + (I)c * 4 * vol + i, vol, cf);
+  typename CplxOf<R>::T r[4];
+  core_3d<NC>(in + (I)(1 - c) * 4 * vol, plane, M, za, zb, ya, yb, xa, xb, vol, in + (I)c * 4 * vol + i, r, cf);
+  typename CplxOf<R>::T* dst = out + (I)c * 4 * vol + i;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dst[q * vol] = r[q];
 }
 
 }  // namespace qw

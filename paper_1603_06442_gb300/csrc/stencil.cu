@@ -232,6 +232,10 @@ bool stencil_supported(const Geometry& g, qw_dtype dt, int variant) {
     case QW_STENCIL_VEC: return g.dim == 3 && dt == QW_C64 && g.nx % 64 == 0;
     case QW_STENCIL_TMA: return dt == QW_C64 && tma_step_supported(g);  // item table built at plan creation
     case QW_STENCIL_TMA2: return dt == QW_C64 && tma2_step_supported(g);
+    case QW_STENCIL_FUSED: {
+      const int box[3] = {g.dim == 1 ? 2048 : 64, g.dim == 2 ? 16 : 8, 8};
+      return fused_step_supported(g, dt, 2, box);
+    }
     default: return false;
   }
 }

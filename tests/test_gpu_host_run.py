@@ -98,3 +98,24 @@ def test_run_host_rejects_bad_arguments(qb):
     with pytest.raises(ValueError):
         plan.run_host([torch.zeros(plan.elems, dtype=torch.complex64, device="cuda")], 1)
     plan.close()
+
+
+def test_host_run_timing_timeline(qb):
+    """qw_plan_set_host_timing / qw_plan_host_timing: per field, the copy precedes the step
+    (the step waits for its field), the observables follow the step, and the copy of field
+    j + 1 starts no later than field j's step ends (it overlaps)."""
+    dim, N, m = 3, 64, 0.2
+    plan = qb.Plan(dim, N, m, "c64")
+    a = inputs.random_field(dim, N, seed=4).astype(np.complex64)
+    host = [torch.from_numpy(a).pin_memory() for _ in range(4)]
+    plan.set_host_timing(True)
+    plan.run_host(host, 6)
+    tl = plan.host_timing(4)
+    plan.set_host_timing(False)
+    with pytest.raises(qb.QwError):
+        plan.host_timing(5)
+    plan.close()
+    for j, (c0, c1, s0, s1, o1) in enumerate(tl):
+        assert 0.0 <= c0 <= c1 <= s0 <= s1 <= o1, (j, tl[j])
+        if j + 1 < len(tl):
+            assert tl[j + 1][0] <= s1, (j, tl)

@@ -19,9 +19,12 @@ TOL = {"c128": 1e-11, "c64": 1e-5}
 
 
 def tol(dtype, t):
-    """1e-11 (FP64) and 1e-5 (FP32) as stated; for FP64 beyond t ~ 1e4 the phase
-    omega_k t itself carries ~t ulp(omega) of rounding in any FP64 method (the
-    oracle's matrix power accumulates the same), so the bound grows as 1e-15 t."""
+    """1e-11 (FP64) and 1e-5 (FP32) as stated, for comparisons with the FP64 oracle.  Beyond
+    t ~ 1e4 the oracle's own matrix power carries ~t ulp(omega_k) in the phase (measured
+    against the 50-digit evolution: 3e-11 at t = 123457, 2.4e-9 at t = 1e7), so against it
+    the FP64 bound grows as 1e-15 t.  The GPU's complex128 path (double-double omega_k) is
+    held to a flat 1e-13 against the 50-digit evolution itself
+    (test_fp64_long_time_vs_extended_precision)."""
     return max(TOL[dtype], 1e-15 * t) if dtype == "c128" else TOL[dtype]
 
 
@@ -299,8 +302,8 @@ def _golden_long_time():
 def test_fp64_long_time_vs_extended_precision(qb, case):
     """FP64 spectral evolution at t ~ 1e5 .. 1e7 against the stored 50-digit evolution of the
     same field (tests/golden, written by oracle.exact through make_long_time_spectral.py).
-    Both the GPU and the FP64 oracle (matrix power of D_k) are compared with it: the FP64
-    phase omega_k t carries ~t ulp(omega_k) in either, which the printed errors show."""
+    The FP64 oracle (matrix power of D_k) drifts as t ulp(omega_k), as its printed error
+    shows; the GPU's phase comes from a double-double omega_k and stays at ~4e-16."""
     dim, N, m, seed, t, path = case
     exact = np.loadtxt(path).view(complex).ravel()
     a = inputs.random_field(dim, N, seed=seed)
@@ -308,4 +311,4 @@ def test_fp64_long_time_vs_extended_precision(qb, case):
     fp64 = walk.to_device(dim, N, spectral.evolve(dim, m, walk.from_device(dim, N, a), t)).ravel()
     e_gpu, e_fp64 = rel_l2(got, exact), rel_l2(fp64, exact)
     print("FP64 spectral t=%d dim=%d N=%d: GPU %.2e, FP64 oracle %.2e (vs 50-digit evolution)" % (t, dim, N, e_gpu, e_fp64))
-    assert e_gpu <= tol("c128", t)
+    assert e_gpu <= 1e-13     # flat in t: the phase comes from a double-double omega_k

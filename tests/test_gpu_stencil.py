@@ -69,7 +69,7 @@ def test_stencil_parity(qb, dim, N, dtype, t):
     assert rel_l2(got, exp) <= tol(dtype, t)
 
 
-@pytest.mark.parametrize("variant", ["plain", "vec", "tma", "tma2"])
+@pytest.mark.parametrize("variant", ["plain", "vec", "tma", "tma2", "fused"])
 @pytest.mark.parametrize("N,t", [(128, 1), (128, 6), (128, 7), (256, 3), (256, 10)])
 def test_bcc_c64_variants(qb, variant, N, t):
     """Every complex64 BCC kernel variant against the oracle (N/2 % 64 == 0 boxes)."""
@@ -241,3 +241,45 @@ def test_misaligned_complex64_view_takes_scalar_kernels(qb, variant):
     plan.close()
     exp = walk.to_device(dim, N, walk.step(dim, m, walk.from_device(dim, N, a), t))
     assert rel_l2(got, exp) <= tol("c64", t)
+
+
+FUSED_CASES = [(1, 1000, 4, (256, 1, 1)), (1, 37, 3, (2048, 1, 1)), (2, 67, 4, (32, 16, 1)), (2, 40, 2, (7, 5, 1)),
+               (2, 9, 4, (64, 64, 1)), (3, 20, 2, (8, 8, 6)), (3, 34, 3, (5, 3, 4)), (3, 128, 2, (16, 8, 4)),
+               (3, 12, 4, (16, 16, 16))]
+
+
+@pytest.mark.parametrize("dim,N,depth,box", FUSED_CASES)
+@pytest.mark.parametrize("t", [1, 5, 12])
+def test_fused_stencil_parity(qb, dim, N, depth, box, t):
+    """FUSED (box tiles + halo in shared memory, `depth` steps per launch; ragged tiles and
+    boxes larger than the walk included) against the oracle, and bit for bit against PLAIN."""
+    m = 0.29
+    a = inputs.random_field(dim, N, seed=N + depth)
+    plan = qb.Plan(dim, N, m, "c64")
+    plan.set_fusion(depth, box)
+    plan.set_stencil("fused")
+    assert plan.stencil == qb.STENCILS["fused"] and plan.fusion() == (depth, [box[k] if k < dim else 1 for k in range(3)])
+    x = to_dev(a, "c64")
+    plan.step(x, t)
+    plan.sync()
+    got = x.cpu().numpy()
+    plan.set_stencil("plain")
+    y = to_dev(a, "c64")
+    plan.step(y, t)
+    plan.close()
+    assert np.array_equal(got, y.cpu().numpy())
+    exp = walk.to_device(dim, N, walk.step(dim, m, walk.from_device(dim, N, a), t))
+    assert rel_l2(got.astype(np.complex128), exp) <= tol("c64", t)
+
+
+def test_fused_rejects_oversize_tiles_and_complex128(qb):
+    plan = qb.Plan(2, 256, 0.1, "c64")
+    with pytest.raises(qb.QwError):
+        plan.set_fusion(4, (128, 64, 1))      # (128 + 8) x (64 + 8) x 4 x 8 B x 2 > 227 KB
+    with pytest.raises(qb.QwError):
+        plan.set_fusion(5, (32, 16, 1))
+    plan.close()
+    plan = qb.Plan(2, 64, 0.1, "c128")
+    with pytest.raises(qb.QwError):
+        plan.set_stencil("fused")
+    plan.close()
