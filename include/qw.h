@@ -123,6 +123,15 @@ qw_status qw_plan_set_stencil(qw_plan plan, int variant);
 /* The stencil variant qw_step currently uses (never QW_STENCIL_AUTO); -1 for null. */
 int qw_plan_get_stencil(qw_plan plan);
 
+/* Autotune cache, process-wide: while `path` is set, qw_plan_autotune and
+ * qw_batch_autotune first look in that text file for a choice measured on the
+ * same GPU model for the same problem (plan: dim, N, dtype; batch: the walks'
+ * (dim, N, t) and rounds_cap) and apply it without measuring; otherwise they
+ * measure and append a line "<kind> <GPU model> <problem> | <values>".  The last
+ * matching line wins; delete the file to re-measure.  NULL or "" turns the
+ * cache off (the default).  Never fails (QW_OK). */
+qw_status qw_set_autotune_cache(const char* path);
+
 /* Temporal fusion of the FUSED variant: `depth` (2..4) steps per launch on tiles
  * of box[0..dim) cells (x, y, z; on the BCC lattice both cosets of the cells),
  * read with a halo of depth cells per side (depth/2 rounded up on the BCC

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -46,6 +47,59 @@ qw_status smem_attr_once(const void* func, int bytes) {
   QW_CHECK_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   limit[key] = bytes;
   return QW_OK;
+}
+
+static std::mutex g_cache_mu;
+static std::string g_cache_path;  // empty: no autotune cache
+
+// "<kind> <GPU model> <problem>" (spaces in the model name become '_')
+static std::string cache_key(const char* kind, const char* problem) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  std::string name = "unknown-gpu";
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+  for (char& c : name)
+    if (c == ' ') c = '_';
+  return std::string(kind) + " " + name + " " + problem;
+}
+
+bool autotune_cache_get(const char* kind, const char* problem, std::vector<double>* values) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  if (g_cache_path.empty()) return false;
+  FILE* f = std::fopen(g_cache_path.c_str(), "r");
+  if (!f) return false;
+  const std::string key = cache_key(kind, problem) + " |";
+  char line[1024];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), f)) {
+    if (std::strncmp(line, key.c_str(), key.size()) != 0) continue;
+    std::vector<double> v;
+    const char* p = line + key.size();
+    char* end = nullptr;
+    for (double x = std::strtod(p, &end); end != p; x = std::strtod(p, &end)) {
+      v.push_back(x);
+      p = end;
+    }
+    *values = v;  // the last matching line wins
+    found = true;
+  }
+  std::fclose(f);
+  return found;
+}
+
+void autotune_cache_put(const char* kind, const char* problem, const std::vector<double>& values) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  if (g_cache_path.empty()) return;
+  FILE* f = std::fopen(g_cache_path.c_str(), "a");
+  if (!f) return;
+  std::string line = cache_key(kind, problem) + " |";
+  char buf[64];
+  for (double x : values) {
+    std::snprintf(buf, sizeof(buf), " %.17g", x);
+    line += buf;
+  }
+  std::fprintf(f, "%s\n", line.c_str());
+  std::fclose(f);
 }
 
 bool make_geometry(int dim, int64_t N, Geometry* g) {
@@ -240,6 +294,7 @@ int64_t qw_plan_field_elems(qw_plan p) { return p ? p->g.elems : -1; }
 int64_t qw_plan_sites(qw_plan p) { return p ? p->g.sites : -1; }
 
 qw_status qw_step(qw_plan p, void* psi, int64_t nsteps, void* stream) {
+  NvtxRange nvtx_range("qw_step");
   if (!p || !psi || nsteps < 0) {
     set_error("qw_step: null plan/field or nsteps < 0");
     return QW_EINVAL;
@@ -301,6 +356,7 @@ qw_status qw_plan_set_stencil(qw_plan p, int variant) {
 int qw_plan_get_stencil(qw_plan p) { return p ? p->stencil : -1; }
 
 qw_status qw_plan_prepare_spectral(qw_plan p) {
+  NvtxRange nvtx_range("qw_plan_prepare_spectral");
   if (!p) {
     set_error("qw_plan_prepare_spectral: null plan");
     return QW_EINVAL;
@@ -311,6 +367,7 @@ qw_status qw_plan_prepare_spectral(qw_plan p) {
 }
 
 qw_status qw_evolve_spectral(qw_plan p, void* psi, int64_t t, void* stream) {
+  NvtxRange nvtx_range("qw_evolve_spectral");
   if (!p || !psi || t < 0) {
     set_error("qw_evolve_spectral: null plan/field or t < 0");
     return QW_EINVAL;
@@ -339,6 +396,7 @@ qw_status qw_evolve_spectral(qw_plan p, void* psi, int64_t t, void* stream) {
 
 qw_status qw_prepare_packet(qw_plan p, void* psi, const double* x0, double sigma, const double* k0,
                             const double* chi, void* stream) {
+  NvtxRange nvtx_range("qw_prepare_packet");
   if (!p || !psi || !x0 || !k0 || !chi) {
     set_error("qw_prepare_packet: null argument");
     return QW_EINVAL;
@@ -349,12 +407,33 @@ qw_status qw_prepare_packet(qw_plan p, void* psi, const double* x0, double sigma
 }
 
 qw_status qw_plan_autotune(qw_plan p, void* stream, double* best_rate) {
+  NvtxRange nvtx_range("qw_plan_autotune");
   if (!p) {
     set_error("qw_plan_autotune: null plan");
     return QW_EINVAL;
   }
   qw_status st = use_device(p);
   if (st != QW_OK) return st;
+  char problem[96];
+  std::snprintf(problem, sizeof(problem), "dim=%d N=%lld dtype=%s", p->g.dim, (long long)p->g.N,
+                p->dtype == QW_C64 ? "c64" : "c128");
+  std::vector<double> cached;
+  if (autotune_cache_get("plan", problem, &cached) && cached.size() == 6) {
+    const int v = (int)cached[0], dpt = (int)cached[1];
+    const int box[3] = {(int)cached[2], (int)cached[3], (int)cached[4]};
+    const bool ok = v == QW_STENCIL_FUSED ? fused_step_supported(p->g, p->dtype, dpt, box)
+                                          : (v >= QW_STENCIL_PLAIN && v <= QW_STENCIL_TMA2 &&
+                                             stencil_supported(p->g, p->dtype, v));
+    if (ok) {  // the measured choice of an earlier run on this GPU model
+      p->stencil = v;
+      if (v == QW_STENCIL_FUSED) {
+        p->fuse_depth = dpt;
+        for (int a = 0; a < 3; ++a) p->fuse_box[a] = box[a];
+      }
+      if (best_rate) *best_rate = cached[5];
+      return QW_OK;
+    }
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* tmp = nullptr;
   const size_t bytes = (size_t)p->g.elems * p->elem_bytes;
@@ -419,7 +498,11 @@ qw_status qw_plan_autotune(qw_plan p, void* stream, double* best_rate) {
   p->stencil = (st == QW_OK) ? best : saved;
   if (best_rate) *best_rate = best_r;
   if (st != QW_OK) return st;
-  return check_flags(p, s);
+  st = check_flags(p, s);
+  if (st == QW_OK)
+    autotune_cache_put("plan", problem, {(double)best, (double)best_depth, (double)best_box[0], (double)best_box[1],
+                                         (double)best_box[2], best_r});
+  return st;
 }
 
 qw_status qw_sync(qw_plan p, void* stream) {
@@ -481,6 +564,7 @@ static void obs_fill(const qw_plan_s* p, const double* r, bool kspace, qw_obs* o
 }
 
 qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) {
+  NvtxRange nvtx_range("qw_observables");
   if (!p || !psi || !out) {
     set_error("qw_observables: null argument");
     return QW_EINVAL;
@@ -498,6 +582,7 @@ qw_status qw_observables(qw_plan p, const void* psi, qw_obs* out, void* stream) 
 }
 
 qw_status qw_fw_transform(qw_plan p, const void* psi, void* out, void* stream) {
+  NvtxRange nvtx_range("qw_fw_transform");
   if (!p || !psi || !out) {
     set_error("qw_fw_transform: null argument");
     return QW_EINVAL;
@@ -515,6 +600,7 @@ qw_status qw_fw_transform(qw_plan p, const void* psi, void* out, void* stream) {
 }
 
 qw_status qw_position_moments(qw_plan p, const void* psi, double* out, void* stream) {
+  NvtxRange nvtx_range("qw_position_moments");
   if (!p || !psi || !out) {
     set_error("qw_position_moments: null argument");
     return QW_EINVAL;
@@ -541,6 +627,7 @@ qw_status qw_position_moments(qw_plan p, const void* psi, double* out, void* str
 }
 
 qw_status qw_projection(qw_plan p, const void* psi, int keep, double* out, void* stream) {
+  NvtxRange nvtx_range("qw_projection");
   if (!p || !psi || !out) {
     set_error("qw_projection: null argument");
     return QW_EINVAL;
@@ -598,6 +685,7 @@ static qw_status host_run_setup(qw_plan_s* p) {
 
 qw_status qw_run_host(qw_plan p, const void* const* psi_host, void* const* psi_out_host, int count, int64_t nsteps,
                       qw_obs* out, void* stream) {
+  NvtxRange nvtx_range("qw_run_host");
   if (!p || count < 0 || nsteps < 0 || (count > 0 && (!psi_host || !out))) {
     set_error("qw_run_host: null plan/array, count < 0 or nsteps < 0");
     return QW_EINVAL;
@@ -729,6 +817,12 @@ qw_status qw_plan_get_fusion(qw_plan p, int* depth, int* box) {
   if (depth) *depth = p->fuse_depth;
   if (box)
     for (int a = 0; a < 3; ++a) box[a] = p->fuse_box[a];
+  return QW_OK;
+}
+
+qw_status qw_set_autotune_cache(const char* path) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  g_cache_path = path ? path : "";
   return QW_OK;
 }
 

@@ -35,6 +35,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <new>
 #include <vector>
 
@@ -85,7 +86,8 @@ struct BatchDebug {
 };
 
 constexpr long long kBatchSpin = 1ll << 24;
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 256;   // plain (depth-1) launches
+constexpr int kFusedThreads = 256;   // launches with fused rounds (512 measured slower: 172 vs 232 G on the chain)
 
 // Largest i in [0, n) with a[i] <= v (a ascending, a[0] <= v), searched by the 32 lanes
 // of a warp together: each round cuts the range into 32 slices and keeps the last
@@ -181,6 +183,7 @@ __device__ __forceinline__ void cp_async_all() {
 // One fused round of `steps` steps of tile (t0, t1, t2) of walk W: load the tile and its
 // halo from `in` into shared buffer A, step there (A -> B -> A ...), write the last step
 // to `out`.  Shared layout: [coset][component][z][y][x] with extents E = e + 2H per axis.
+template <int NT>
 __device__ __forceinline__ void fused_round(const BatchWalk& W, const int (&t3)[3], int steps, const float2* in, float2* out,
                             float2* smA, float2* smB) {
   const int tid = threadIdx.x;
@@ -199,7 +202,7 @@ __device__ __forceinline__ void fused_round(const BatchWalk& W, const int (&t3)[
   {
     const int lo3[3] = {0, 0, 0};
     const int planes = W.ncos * W.ncomp;
-    for_box<kBatchThreads>(lo3, E, tid, [&](int x, int y, int z) {
+    for_box<NT>(lo3, E, tid, [&](int x, int y, int z) {
       const int gx = wrap_near(s0[0] - H + x, nx);
       const int gy = W.dim >= 2 ? wrap_near(s0[1] - H + y, ny) : 0;
       const int gz = W.dim >= 3 ? wrap_near(s0[2] - H + z, nz) : 0;
@@ -217,7 +220,7 @@ __device__ __forceinline__ void fused_round(const BatchWalk& W, const int (&t3)[
     for (int c = 0; c < W.ncos; ++c) {
       int lo[3], hi[3];
       step_region(W, e, steps, k, c, lo, hi);
-      for_box<kBatchThreads>(lo, hi, tid, [&](int x, int y, int z) {
+      for_box<NT>(lo, hi, tid, [&](int x, int y, int z) {
         const int i = z * sz + y * sy + x;  // 32-bit shared-memory offsets
         float2 r[4];
         if (W.dim == 1) {
@@ -258,6 +261,7 @@ __device__ __forceinline__ void fused_round(const BatchWalk& W, const int (&t3)[
 
 // The plain round of tile (t0, t1, t2): every cell of the tile (both cosets) updated once
 // from global memory, or (copy round) copied from buf[1] to buf[0].
+template <int NT>
 __device__ __forceinline__ void plain_round(const BatchWalk& W, const int (&t3)[3], bool copy, const float2* in, float2* out) {
   int lo[3], hi[3];
 #pragma unroll
@@ -267,7 +271,7 @@ __device__ __forceinline__ void plain_round(const BatchWalk& W, const int (&t3)[
   }
   const int nx = W.n[0], ny = W.n[1];
   for (int c = 0; c < W.ncos; ++c) {
-    for_box<kBatchThreads>(lo, hi, threadIdx.x, [&](int x, int y, int z) {
+    for_box<NT>(lo, hi, threadIdx.x, [&](int x, int y, int z) {
       if (copy) {
         const int64_t base = (int64_t)c * W.ncomp * W.vol + ((int64_t)z * ny + y) * nx + x;
         for (int q = 0; q < W.ncomp; ++q) out[base + (int64_t)q * W.vol] = in[base + (int64_t)q * W.vol];
@@ -285,7 +289,7 @@ __device__ __forceinline__ void plain_round(const BatchWalk& W, const int (&t3)[
 // FUSED = false: every walk has depth 1 (no shared memory, high occupancy);
 // FUSED = true: walks of depth >= 2 run fused rounds in dynamic shared memory.
 template <bool FUSED>
-__global__ void __launch_bounds__(kBatchThreads, FUSED ? 3 : 6)
+__global__ void __launch_bounds__(FUSED ? kFusedThreads : kBatchThreads, FUSED ? 3 : 6)
     batch_kernel(const BatchWalk* __restrict__ walks, const BatchGroup* __restrict__ groups,
                  const int64_t* __restrict__ group_item0, int ngroups, const int64_t* __restrict__ tile_prefix,
                  const int64_t* __restrict__ round_prefix, int64_t total_items, unsigned int* __restrict__ done,
@@ -390,12 +394,12 @@ __global__ void __launch_bounds__(kBatchThreads, FUSED ? 3 : 6)
       if (FUSED && W.depth > 1) {
         const int P = (W.ncos * W.ncomp) * (W.ext[0] + 2 * W.halo) * (W.dim >= 2 ? W.ext[1] + 2 * W.halo : 1) *
                       (W.dim >= 3 ? W.ext[2] + 2 * W.halo : 1);
-        fused_round(W, t3, steps, in, out, smem_dyn, smem_dyn + P);
+        fused_round<FUSED ? kFusedThreads : kBatchThreads>(W, t3, steps, in, out, smem_dyn, smem_dyn + P);
       } else {
-        plain_round(W, t3, false, in, out);
+        plain_round<FUSED ? kFusedThreads : kBatchThreads>(W, t3, false, in, out);
       }
     } else {
-      plain_round(W, t3, true, b1, b0);  // copy round: the result sits in buf[1]
+      plain_round<FUSED ? kFusedThreads : kBatchThreads>(W, t3, true, b1, b0);  // copy round: the result sits in buf[1]
     }
     __syncthreads();
     if (tid == 0 && W.tile_base + tile != dbg.stall_tile) {
@@ -409,14 +413,14 @@ __global__ void __launch_bounds__(kBatchThreads, FUSED ? 3 : 6)
 // qw_step's FUSED variant: `steps` updates of a whole field in one launch, one CTA per
 // box tile (grid-stride), each a fused round from `in` to `out` (every tile reads only `in`,
 // so the launch needs no dependency waits; successive launches ping-pong).
-__global__ void __launch_bounds__(kBatchThreads, 3)
+__global__ void __launch_bounds__(kFusedThreads, 3)
     fused_step_kernel(BatchWalk W, int steps, const float2* __restrict__ in, float2* __restrict__ out) {
   extern __shared__ float2 smem_dyn[];
   const int P = (W.ncos * W.ncomp) * (W.ext[0] + 2 * W.halo) * (W.dim >= 2 ? W.ext[1] + 2 * W.halo : 1) *
                 (W.dim >= 3 ? W.ext[2] + 2 * W.halo : 1);
   for (int tile = blockIdx.x; tile < W.ntiles; tile += gridDim.x) {
     const int t3[3] = {tile % W.nt[0], (tile / W.nt[0]) % W.nt[1], tile / (W.nt[0] * W.nt[1])};
-    fused_round(W, t3, steps, in, out, smem_dyn, smem_dyn + P);
+    fused_round<kFusedThreads>(W, t3, steps, in, out, smem_dyn, smem_dyn + P);
     __syncthreads();
   }
 }
@@ -606,9 +610,9 @@ qw_status launch_step_fused(const Geometry& g, int depth, const int* box, int st
   int dev = 0, nsm = 0, per_sm = 0;
   QW_CHECK_CUDA(cudaGetDevice(&dev));
   QW_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  QW_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_step_kernel, kBatchThreads, smem));
+  QW_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_step_kernel, kFusedThreads, smem));
   const int grid = (int)std::min<int64_t>(W.ntiles, (int64_t)std::max(1, per_sm) * nsm);
-  fused_step_kernel<<<grid, kBatchThreads, smem, st>>>(W, steps, static_cast<const float2*>(in),
+  fused_step_kernel<<<grid, kFusedThreads, smem, st>>>(W, steps, static_cast<const float2*>(in),
                                                        static_cast<float2*>(out));
   QW_CHECK_LAUNCH("fused stencil launch");
   return QW_OK;
@@ -723,7 +727,7 @@ static qw_status build_schedule(qw_batch_s* b) {
   if (b->fused) {
     qw_status sa = smem_attr(batch_kernel<true>, (int)b->smem);
     if (sa != QW_OK) return sa;
-    QW_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<true>, kBatchThreads, b->smem));
+    QW_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<true>, kFusedThreads, b->smem));
   } else {
     QW_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<false>, kBatchThreads, 0));
   }
@@ -736,7 +740,7 @@ static qw_status launch_batch(qw_batch_s* b, cudaStream_t s) {
   QW_CHECK_CUDA(cudaMemsetAsync(b->d_done, 0, std::max<int64_t>(1, b->ndone) * sizeof(unsigned int), s));
   QW_CHECK_CUDA(cudaMemsetAsync(b->d_ctl, 0, sizeof(BatchCtl), s));
   if (b->fused)
-    batch_kernel<true><<<b->grid, kBatchThreads, b->smem, s>>>(b->d_walks, b->d_groups, b->d_group_item0,
+    batch_kernel<true><<<b->grid, kFusedThreads, b->smem, s>>>(b->d_walks, b->d_groups, b->d_group_item0,
                                                                b->ngroups, b->d_tiles, b->d_rounds, b->total_items,
                                                                b->d_done, b->d_ctl, b->dbg);
   else
@@ -843,6 +847,7 @@ qw_status qw_batch_debug_stall(qw_batch b, int walk, int64_t spin_limit) {
 }
 
 qw_status qw_batch_run(qw_batch b, void* stream) {
+  NvtxRange nvtx_range("qw_batch_run");
   if (!b) {
     set_error("qw_batch_run: null batch");
     return QW_EINVAL;
@@ -884,6 +889,7 @@ qw_status qw_batch_sync(qw_batch b, void* stream) {
 
 qw_status qw_batch_autotune(qw_batch b, int64_t rounds_cap, void* stream, qw_batch_tiling* best_tiling,
                             double* best_rate) {
+  NvtxRange nvtx_range("qw_batch_autotune");
   if (!b || rounds_cap < 2) {
     set_error("qw_batch_autotune: null batch or rounds_cap < 2");
     return QW_EINVAL;
@@ -891,6 +897,40 @@ qw_status qw_batch_autotune(qw_batch b, int64_t rounds_cap, void* stream, qw_bat
   if (b->stall_walk >= 0) {
     set_error("qw_batch_autotune: a stall is injected (qw_batch_debug_stall); clear it first");
     return QW_EINVAL;
+  }
+  // the cache key: the walks' (dim, N, t) in the caller's order (FNV-1a) and the tuning length
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](uint64_t v) {
+    for (int k = 0; k < 8; ++k) {
+      h ^= (v >> (8 * k)) & 0xff;
+      h *= 1099511628211ull;
+    }
+  };
+  for (const qw_walk& w : b->desc) {
+    mix((uint64_t)w.dim);
+    mix((uint64_t)w.N);
+    mix((uint64_t)w.t);
+  }
+  char problem[96];
+  std::snprintf(problem, sizeof(problem), "walks=%d mix=%016llx cap=%lld", b->n, (unsigned long long)h,
+                (long long)rounds_cap);
+  std::vector<double> cached;
+  if (autotune_cache_get("batch", problem, &cached) && cached.size() == 15) {
+    qw_batch_tiling t;
+    t.tile_sites = (int64_t)cached[0];
+    t.l2_budget_bytes = (int64_t)cached[1];
+    for (int d = 0; d < 3; ++d) {
+      t.depth[d] = (int)cached[2 + d];
+      for (int a = 0; a < 3; ++a) t.box[d][a] = (int)cached[5 + 3 * d + a];
+    }
+    if (check_tiling(t) == QW_OK) {  // the measured choice of an earlier run on this GPU model
+      b->tiling = t;
+      qw_status st = build_schedule(b);
+      if (st != QW_OK) return st;
+      if (best_tiling) *best_tiling = t;
+      if (best_rate) *best_rate = cached[14];
+      return QW_OK;
+    }
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // stand-in fields of the same sizes (the walks' own fields are left untouched)
@@ -989,12 +1029,19 @@ qw_status qw_batch_autotune(qw_batch b, int64_t rounds_cap, void* stream, qw_bat
   qw_status st2 = build_schedule(b);
   if (st != QW_OK) return st;
   if (st2 != QW_OK) return st2;
+  std::vector<double> v = {(double)best.tile_sites, (double)best.l2_budget_bytes};
+  for (int d = 0; d < 3; ++d) v.push_back(best.depth[d]);
+  for (int d = 0; d < 3; ++d)
+    for (int a = 0; a < 3; ++a) v.push_back(best.box[d][a]);
+  v.push_back(best_r);
+  autotune_cache_put("batch", problem, v);
   if (best_tiling) *best_tiling = best;
   if (best_rate) *best_rate = best_r;
   return QW_OK;
 }
 
 qw_status qw_batch_observables(qw_batch b, qw_obs* out, void* stream) {
+  NvtxRange nvtx_range("qw_batch_observables");
   if (!b || !out) {
     set_error("qw_batch_observables: null argument");
     return QW_EINVAL;

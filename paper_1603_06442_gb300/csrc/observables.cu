@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(kObsThreads) fold_partials_kernel(const double
 // Z^2 d, Y Z d over groups of four rows in the field's precision, then in FP64, and adds
 // the X-weighted terms once per column.  One partial per block, folded in a fixed order.
 constexpr int kMom2 = 10;
-template <typename R>
+// S: spinor components (compile time, so that a group's loads are all issued before the sums)
+template <typename R, int S>
 __global__ void __launch_bounds__(kObsThreads) moments2_kernel(const typename Cplx<R>::T* __restrict__ psi,
                                                                Geometry g, int chunks, double* __restrict__ partials) {
   using C = typename Cplx<R>::T;
@@ -105,18 +106,37 @@ __global__ void __launch_bounds__(kObsThreads) moments2_kernel(const typename Cp
     const C* col = psi + (int64_t)c * g.s * g.vol + x;
     int z = (int)(r0 / ny), y = (int)(r0 - (int64_t)z * ny);
     double n = 0.0, sy = 0.0, sz = 0.0, syy = 0.0, szz = 0.0, syz = 0.0;
-    for (int64_t r = r0; r < r1;) {
-      R gn = 0, gy = 0, gz = 0, gyy = 0, gzz = 0, gyz = 0;
-      const int64_t rend = r + 4 < r1 ? r + 4 : r1;
-      for (; r < rend; ++r) {
-        const C* q = col + ((int64_t)z * ny + y) * g.nx;
-        R d = 0;
-        for (int s = 0; s < g.s; ++s) {
-          const C v = q[(int64_t)s * g.vol];
-          d = fma(v.x, v.x, d);
-          d = fma(v.y, v.y, d);
+    for (int64_t r = r0; r < r1; r += 4) {
+      // the group's (up to) four rows: every load first, then the sums
+      C v[4][S];
+      R Yk[4], Zk[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Yk[k] = g.dim >= 2 ? sc * (R)y + off : (R)0;
+        Zk[k] = g.dim >= 3 ? sc * (R)z + off : (R)0;
+        if (r + k < r1) {
+          const C* q = col + ((int64_t)z * ny + y) * g.nx;
+#pragma unroll
+          for (int s = 0; s < S; ++s) v[k][s] = q[(int64_t)s * g.vol];
+        } else {
+#pragma unroll
+          for (int s = 0; s < S; ++s) v[k][s] = C{0, 0};
         }
-        const R Y = g.dim >= 2 ? sc * (R)y + off : (R)0, Z = g.dim >= 3 ? sc * (R)z + off : (R)0;
+        if (++y == ny) {
+          y = 0;
+          ++z;
+        }
+      }
+      R gn = 0, gy = 0, gz = 0, gyy = 0, gzz = 0, gyz = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        R d = 0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          d = fma(v[k][s].x, v[k][s].x, d);
+          d = fma(v[k][s].y, v[k][s].y, d);
+        }
+        const R Y = Yk[k], Z = Zk[k];
         const R yd = Y * d, zd = Z * d;
         gn += d;
         gy += yd;
@@ -124,10 +144,6 @@ __global__ void __launch_bounds__(kObsThreads) moments2_kernel(const typename Cp
         gyy = fma(Y, yd, gyy);
         gzz = fma(Z, zd, gzz);
         gyz = fma(Y, zd, gyz);
-        if (++y == ny) {
-          y = 0;
-          ++z;
-        }
       }
       n += (double)gn;
       sy += (double)gy;
@@ -183,8 +199,12 @@ static int launch_moments2_t(const Geometry& g, const void* psi, double* partial
   if (chunks > rows) chunks = rows;
   if (chunks * bx > kMom2MaxBlocks) chunks = kMom2MaxBlocks / bx;
   if (chunks < 1) chunks = 1;
-  moments2_kernel<R><<<dim3((unsigned)bx, (unsigned)chunks), kObsThreads, 0, st>>>(static_cast<const C*>(psi), g,
-                                                                                   (int)chunks, partials);
+  if (g.s == 2)
+    moments2_kernel<R, 2><<<dim3((unsigned)bx, (unsigned)chunks), kObsThreads, 0, st>>>(static_cast<const C*>(psi), g,
+                                                                                        (int)chunks, partials);
+  else
+    moments2_kernel<R, 4><<<dim3((unsigned)bx, (unsigned)chunks), kObsThreads, 0, st>>>(static_cast<const C*>(psi), g,
+                                                                                        (int)chunks, partials);
   return (int)(bx * chunks);
 }
 

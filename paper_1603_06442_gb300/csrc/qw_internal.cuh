@@ -4,12 +4,23 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <vector>
 
 #include "qw.h"
 #include "qw_fft.cuh"
 
 namespace qw {
+
+// ---- tracing: an NVTX range around each ABI call (header-only NVTX 3: free unless a
+// profiler such as Nsight Systems attaches and records the ranges) ---------------------
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---- errors ---------------------------------------------------------------
 void set_error(const char* fmt, ...);
@@ -39,6 +50,12 @@ inline qw_status smem_attr(K* kernel, int bytes) {
 template <typename T> struct CplxOf2;
 template <> struct CplxOf2<float> { using t = float2; };
 template <> struct CplxOf2<double> { using t = double2; };
+
+// ---- autotune cache (api.cu) ------------------------------------------------
+// A text file of "key | value" lines; the key starts with the GPU model.  Lookups take the
+// last line with the key; stores append.  Both are no-ops while no cache file is set.
+bool autotune_cache_get(const char* kind, const char* problem, std::vector<double>* values);
+void autotune_cache_put(const char* kind, const char* problem, const std::vector<double>& values);
 
 // ---- geometry -------------------------------------------------------------
 // One field in the device layout: ncoset x s planes of `vol` complex values,

@@ -63,6 +63,7 @@ struct TimeArg {
   double tt;
   float tf;
   int small;  // t < 2^24: the split-nu phase applies
+  int odd;    // t odd: (-1)^t = -1
 };
 inline float2 split_df(double v) {
   const float hi = (float)v;
@@ -71,7 +72,9 @@ inline float2 split_df(double v) {
 inline Mass make_mass(double n, double m) {
   return Mass{n, m, (float)n, (float)m, split_df(n), split_df(n * n), split_df(m * m)};
 }
-inline TimeArg make_time(int64_t t) { return TimeArg{(double)t, (float)t, t < (int64_t(1) << 24) ? 1 : 0}; }
+inline TimeArg make_time(int64_t t) {
+  return TimeArg{(double)t, (float)t, t < (int64_t(1) << 24) ? 1 : 0, (int)(t & 1)};
+}
 
 // Frequency index of storage position p on an axis split into digits
 // (A), (A, B) or (A, B1, B2): the passes leave frequency k1 + A k2 at B k1 + k2
@@ -151,7 +154,19 @@ __device__ __forceinline__ void wave_vectors(int dim, int64_t x, int64_t y, int6
   fsum = f[0] + f[1] + f[2];
 }
 
-// a = exp(i (k1 + k2 + k3)/2) = exp(i pi fsum / M) on the cubic coset grid.
+// a = exp(i (k1 + k2 + k3)/2) = exp(i pi fx / M) exp(i pi fy / M) exp(i pi fz / M): the
+// product of the three per-axis table entries (the half angles of the BCC symbol tables).
+template <typename T>
+__device__ __forceinline__ void coset_phase_tab(const AxesDev& a, const int64_t (&f)[3], T& ar, T& ai) {
+  T c0, s0, c1, s1, c2, s2;
+  tab<T>(a, 0, f[0], c0, s0);
+  tab<T>(a, 1, f[1], c1, s1);
+  tab<T>(a, 2, f[2], c2, s2);
+  const T pr = c0 * c1 - s0 * s1, pi = c0 * s1 + s0 * c1;
+  ar = pr * c2 - pi * s2;
+  ai = pr * s2 + pi * c2;
+}
+
 template <typename T>
 __device__ __forceinline__ void coset_phase(int64_t fsum, int64_t M, T& ar, T& ai) {
   const int64_t q = fsum % (2 * M);
@@ -499,7 +514,7 @@ __device__ __forceinline__ void evolve_point(int dim, const AxesDev& a, int64_t 
     for (int q = 0; q < 4; ++q) v[q] = make_vec(w[q], scale);
   } else {
     T ar, ai;
-    coset_phase<T>(fs, a.len[0], ar, ai);  // a = exp(i (k1 + k2 + k3)/2)
+    coset_phase_tab<T>(a, f, ar, ai);  // a = exp(i (k1 + k2 + k3)/2)
     V c0[4], c1[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -513,16 +528,21 @@ __device__ __forceinline__ void evolve_point(int dim, const AxesDev& a, int64_t 
       c1[q].y = (T)0.5 * (v[q].y - b.y);
     }
     {
+      // q1 = q0 + (pi, 0, 0) flips the signs of u and n~ (the x half angle moves by pi), so
+      // omega_q1 = pi - omega_q0 and D_q1 = -Gamma D_q0 Gamma with Gamma = diag(I, -I):
+      // D_q1^t = (-1)^t Gamma D_q0^t Gamma.  One phase and one G^ serve both half spectra.
       T c, s, gx, gy, gz, gm;
       cs_at<T, 4>(3, a, f, 0, 2 * idx, ms, omega, ta, c, s);
       ghat<T>(3, a, f, 0, ms, gx, gy, gz, gm);
       apply_dt<T, 4>(c0, c, s, (T)0, gx, gy, gz, gm);
-    }
-    {
-      T c, s, gx, gy, gz, gm;
-      cs_at<T, 4>(3, a, f, 1, 2 * idx + 1, ms, omega, ta, c, s);
-      ghat<T>(3, a, f, 1, ms, gx, gy, gz, gm);
+      c1[2] = make_vec(c1[2], (T)-1);
+      c1[3] = make_vec(c1[3], (T)-1);
       apply_dt<T, 4>(c1, c, s, (T)0, gx, gy, gz, gm);
+      const T sg = ta.odd ? (T)-1 : (T)1;
+      c1[0] = make_vec(c1[0], sg);
+      c1[1] = make_vec(c1[1], sg);
+      c1[2] = make_vec(c1[2], -sg);
+      c1[3] = make_vec(c1[3], -sg);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -556,7 +576,7 @@ __device__ __forceinline__ void weights_point(int dim, const AxesDev& a, int64_t
   V vq[2][4];
   if (dim == 3) {
     T ar, ai;
-    coset_phase<T>(fs, a.len[0], ar, ai);
+    coset_phase_tab<T>(a, f, ar, ai);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const V p0 = vin[q], p1 = vin[4 + q];
@@ -572,9 +592,15 @@ __device__ __forceinline__ void weights_point(int dim, const AxesDev& a, int64_t
 #pragma unroll
     for (int q = 0; q < 4; ++q) vq[0][q] = vin[q];
   }
+  // G^ of the BCC half spectrum q1 is -Gamma G^_q0 Gamma (Gamma = diag(I, -I); see
+  // evolve_point): v^dag G^_q1 v = -(Gamma v)^dag G^_q0 (Gamma v)
+  T gx, gy, gz, gm;
+  ghat<T>(dim, a, f, 0, ms, gx, gy, gz, gm);
+  if (dim == 3) {
+    vq[1][2] = make_vec(vq[1][2], (T)-1);
+    vq[1][3] = make_vec(vq[1][3], (T)-1);
+  }
   for (int j = 0; j < nq; ++j) {
-    T gx, gy, gz, gm;
-    ghat<T>(dim, a, f, dim == 3 ? j : 0, ms, gx, gy, gz, gm);
     // cos = 1, sin = 1 turns apply_dt into v - i G^ v; recover G^ v from it
     T nrm = 0, gdot = 0;
     if (S == 2) {
@@ -596,7 +622,7 @@ __device__ __forceinline__ void weights_point(int dim, const AxesDev& a, int64_t
       }
     }
     acc[0] += (A)nrm;
-    acc[1] += (A)gdot;
+    acc[1] += j ? -(A)gdot : (A)gdot;
   }
 }
 

@@ -226,6 +226,7 @@ static bool admit_memory(qw_server_s* S, Request& R, Slot& sl, qw_status* st) {
 
 // Enqueue the whole request on the slot's stream.
 static qw_status launch_request(qw_server_s* S, Slot& sl) {
+  NvtxRange nvtx_range("qw_server request launch");
   Request& R = *sl.r;
   const Geometry& g = R.g;
   cudaStream_t s = sl.stream;

@@ -49,6 +49,7 @@ using namespace qw;
 
 extern "C" qw_status qw_step_static(int dim, int64_t N, double mass, qw_dtype dtype, void* psi, int64_t nsteps,
                                     void* stream) {
+  NvtxRange nvtx_range("qw_step_static");
   Geometry g;
   if (!make_geometry(dim, N, &g)) {
     set_error("qw_step_static: bad dim=%d / N=%lld", dim, (long long)N);
