@@ -52,8 +52,12 @@ def parse():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--N", type=int, default=None, help="override the box side (profiling runs)")
     ap.add_argument("--stencil", default=None, help="force a stencil variant (plain, vec, tma)")
-    ap.add_argument("--only", default=None, choices=["spectral", "batched", "served", "projection"],
+    ap.add_argument("--only", default=None, choices=["spectral", "batched", "served", "projection", "lattices"],
                     help="run one secondary workload alone and print its JSON (profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched / lattices: keep the default tiling or variant instead of autotuning (profiling runs)")
+    ap.add_argument("--lattice-scale", type=int, default=1,
+                    help="lattices: divide the chain's N by this and the square lattice's N by its square root")
     ap.add_argument("--requests", type=int, default=2000, help="served workload: number of requests")
     ap.add_argument("--walks", type=int, default=256, help="batched workload: number of walks")
     ap.add_argument("--substeps", type=int, default=None, help="override stencil steps per bench step")
@@ -364,8 +368,16 @@ def run_ours(args, rank, world, local):
         "final_obs": obs,
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = oracle_cpu_baseline()
-        line["cpu_baseline"]["all_cores"] = oracle_cpu_baseline_all_cores()
+        # the oracle on every host core (one process per core, the same bounded sample each);
+        # the single-core figure rides along
+        single = oracle_cpu_baseline()
+        allc = oracle_cpu_baseline_all_cores()
+        if allc.get("value"):
+            line["cpu_baseline"] = {"value": allc["value"], "unit": "site-steps/s", "cores": allc["cores"],
+                                    "kind": "oracle", "sample": "BCC N=64 box, FP64 numpy update steps: " + allc["sample"],
+                                    "single_core": single}
+        else:
+            line["cpu_baseline"] = single
     if extra:
         line["extra"] = extra
     plan.close()
@@ -414,6 +426,7 @@ def extra_measurements(qb, dev, stream):
                           "equiv_GBps_at_64B_per_site_step": 2 * plan.elems * 8 / (ms / 1e3) / 1e9}
     out["c64_stencil_variants"] = variants
     plan.close()
+    out["fp32_error_vs_fp64"] = fp32_error_measurement(qb, dev, stream)
     out["lattices"] = lattice_stencil_measurement(qb, dev, stream)
     out["spectral"] = spectral_measurement(qb, dev, stream)
     out["projection"] = projection_measurement(qb, dev, stream)
@@ -422,7 +435,41 @@ def extra_measurements(qb, dev, stream):
     return out
 
 
-def lattice_stencil_measurement(qb, dev, stream):
+def fp32_error_measurement(qb, dev, stream):
+    """The bench workload's complex64 result against the complex128 path on the same initial
+    field (the complex128 path is the one held to 1e-11 of the FP64 oracle): relative L2 and
+    norm drift after the bench step's 100 stencil steps, and after a spectral evolution to
+    t = 10^4 (the spectral complex64 error does not grow with t)."""
+    import torch
+    from paper_1603_06442_gb300 import inputs
+    W = WORKLOAD
+    dim, N = W["dim"], W["N"]
+    a = inputs.gaussian_packet(dim, N, (N / 2,) * 3, W["sigma"], W["k0"], [0.5, 0.5j, 0.5, -0.5j])
+    out = {}
+    for mode, t in (("stencil", W["substeps"]), ("spectral", 10000)):
+        res = {}
+        for dt in ("c64", "c128"):
+            plan = qb.Plan(dim, N, W["mass"], dt)
+            x = torch.from_numpy(a.astype(np.complex64 if dt == "c64" else np.complex128)).to(dev)
+            if mode == "stencil":
+                plan.step(x, t, stream)
+            else:
+                plan.evolve_spectral(x, t, stream)
+            plan.sync(stream)
+            res[dt] = x.to(torch.complex128)
+            plan.close()
+            del x
+        diff = torch.linalg.vector_norm(res["c64"] - res["c128"]).item()
+        ref = torch.linalg.vector_norm(res["c128"]).item()
+        n64 = torch.linalg.vector_norm(res["c64"]).item() ** 2
+        n0 = float(np.sum(np.abs(a.astype(np.complex64).astype(np.complex128)) ** 2))
+        out[mode] = {"t": t, "rel_l2_c64_vs_c128": diff / ref, "norm_drift_c64": abs(n64 - n0) / n0}
+        del res
+        torch.cuda.empty_cache()
+    return out
+
+
+def lattice_stencil_measurement(qb, dev, stream, autotune=True, scale=1):
     """complex64 stencil on the square lattice (N = 8192, 4-spinor, 2.1 GB) and the chain
     (N = 2^28, 2-spinor, 2.1 GB), both larger than L2: every variant the plan supports, the
     FUSED one at the depth and tile the autotuner picks; roofline fraction at the unfused
@@ -430,19 +477,23 @@ def lattice_stencil_measurement(qb, dev, stream):
     import torch
     peak, kind = measured_peaks()
     out = {}
-    for dim, N in ((2, 8192), (1, 1 << 28)):
+    for dim, N in ((2, 8192 // int(round(scale ** 0.5))), (1, (1 << 28) // scale)):
         plan = qb.Plan(dim, N, 0.1, "c64")
         psi = torch.zeros(plan.elems, dtype=torch.complex64, device=dev)
         psi[::7] = 1e-3
         bps = 2 * plan.elems * 8 / plan.sites   # unfused algorithmic bytes per site-step
-        rate_tuned = plan.autotune(stream)
+        if autotune:
+            rate_tuned = plan.autotune(stream)
+        else:   # the default FUSED depth and tile for this lattice
+            plan.set_stencil("fused")
+            rate_tuned = None
         tuned = {"variant": [k for k, v in qb.STENCILS.items() if v == plan.stencil][0],
                  "fusion": plan.fusion(), "autotune_rate": rate_tuned}
         res = {}
         for name in ("plain", "fused"):
-            plan.set_stencil(name)
             if name == "fused" and tuned["variant"] != "fused":
                 continue
+            plan.set_stencil(name)
             plan.step(psi, 4, stream)
             s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             n = 24
@@ -678,7 +729,7 @@ def _drain(qb, srv, tickets):
         _t.sleep(0.0005)
 
 
-def batched_measurement(qb, dev, stream, runs=3, n_walks=256):
+def batched_measurement(qb, dev, stream, runs=3, n_walks=256, autotune=True):
     """256 uneven walks (2D N log-U[64,1024], BCC N log-U[32,128], m U[0,0.5], t U{100..5000},
     packets of width N/16) in one persistent launch replayed from a CUDA graph; tiling autotuned."""
     import torch
@@ -691,7 +742,10 @@ def batched_measurement(qb, dev, stream, runs=3, n_walks=256):
                                    [0.5, 0.5, 0.5j, -0.5j])
         fields.append(torch.from_numpy(a.astype(np.complex64)).to(dev))
     b = qb.Batch([(w["dim"], w["N"], w["mass"], w["t"], x) for w, x in zip(mix, fields)])
-    best, tuned_rate = b.autotune(rounds_cap=256, stream=stream)
+    if autotune:
+        best, tuned_rate = b.autotune(rounds_cap=256, stream=stream)
+    else:
+        best, tuned_rate = b.tiling()[0], None
     site_steps = 0
     for w in mix:
         sites = w["N"] ** 2 if w["dim"] == 2 else w["N"] ** 3 // 4
@@ -733,7 +787,9 @@ def run_only(args, local):
     if args.only == "served":
         out = served_measurement(qb, dev, stream, n_req=args.requests)
     elif args.only == "batched":
-        out = batched_measurement(qb, dev, stream, n_walks=args.walks)
+        out = batched_measurement(qb, dev, stream, n_walks=args.walks, autotune=not args.no_autotune)
+    elif args.only == "lattices":
+        out = lattice_stencil_measurement(qb, dev, stream, autotune=not args.no_autotune, scale=args.lattice_scale)
     elif args.only == "projection":
         out = projection_measurement(qb, dev, stream)
     else:

@@ -64,9 +64,10 @@ typedef enum { QW_C64 = 0, QW_C128 = 1 } qw_dtype;
  * remaining step runs as TMA).  FUSED: any lattice and size, complex64; box
  * tiles of the field with a halo loaded into shared memory, `depth` steps per
  * launch (temporal fusion of depth 2..4, tile box and depth set by
- * qw_plan_set_fusion or the autotuner).  AUTO restores the default: the first
- * supported of TMA2 > TMA > VEC > PLAIN; qw_plan_autotune measures every
- * variant (FUSED with several depths and boxes) and keeps the fastest. */
+ * qw_plan_set_fusion or the autotuner).  AUTO restores the default, the
+ * fastest measured on GB300: TMA2 where supported, FUSED for complex64 chains,
+ * else TMA > VEC > PLAIN; qw_plan_autotune measures every variant (FUSED with
+ * several depths and boxes) and keeps the fastest. */
 typedef enum {
   QW_STENCIL_AUTO = 0,
   QW_STENCIL_PLAIN = 1,
@@ -122,6 +123,14 @@ qw_status qw_plan_set_stencil(qw_plan plan, int variant);
 
 /* The stencil variant qw_step currently uses (never QW_STENCIL_AUTO); -1 for null. */
 int qw_plan_get_stencil(qw_plan plan);
+
+/* Debug poison, process-wide: while on != 0, the scratch and partner buffers of
+ * plans (qw_step, qw_observables), batches (each launch; a batch's CUDA graph
+ * holds the fills if it is captured while this is on) and qw_step_static are
+ * filled with NaN before every call that must write them before reading them,
+ * so that a read of memory a kernel did not write shows as NaN in the results.
+ * Costs one device fill per call; off by default.  Never fails (QW_OK). */
+qw_status qw_set_debug_poison(int on);
 
 /* Autotune cache, process-wide: while `path` is set, qw_plan_autotune and
  * qw_batch_autotune first look in that text file for a choice measured on the
@@ -288,8 +297,10 @@ typedef struct qw_batch_s* qw_batch;
 
 /* Create a batch over n walks (descriptors copied).  Allocates a partner
  * field per walk, the schedule tables and counters on the current device.
- * Default tiling: depth 2 on every lattice, boxes 1024, 32x16 and 8x8x4 cells,
- * one group (16 GiB); qw_batch_autotune measures better ones.
+ * Default tiling: depth 1 on every lattice with 2048-site tiles, one group
+ * (16 GiB), the autotuner's choice for a mix of 256 square-lattice and BCC walks
+ * on GB300; boxes for fused rounds 1024, 32x16 and 8x8x4 cells.  qw_batch_autotune
+ * measures the mix at hand.
  * Errors: QW_EINVAL (bad descriptor, a walk of 2^31 complex values or more),
  * QW_ENOMEM, QW_ECUDA. */
 qw_status qw_batch_create(const qw_walk* walks, int n, qw_batch* out);

@@ -109,6 +109,7 @@ _SIGS = {
     "qw_batch_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "qw_batch_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(qw_obs), ctypes.c_void_p]),
     "qw_set_autotune_cache": (ctypes.c_int, [ctypes.c_char_p]),
+    "qw_set_debug_poison": (ctypes.c_int, [ctypes.c_int]),
     "qw_plan_set_fusion": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "qw_plan_get_fusion": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]),
@@ -284,6 +285,10 @@ def qw_server_stats(server):
 
 def qw_server_destroy(server):
     _check(load().qw_server_destroy(server))
+
+
+def qw_set_debug_poison(on):
+    _check(load().qw_set_debug_poison(1 if on else 0))
 
 
 def qw_set_autotune_cache(path):

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -48,6 +49,9 @@ qw_status smem_attr_once(const void* func, int bytes) {
   limit[key] = bytes;
   return QW_OK;
 }
+
+static std::atomic<bool> g_poison{false};
+bool debug_poison() { return g_poison.load(std::memory_order_relaxed); }
 
 static std::mutex g_cache_mu;
 static std::string g_cache_path;  // empty: no autotune cache
@@ -127,10 +131,12 @@ bool make_geometry(int dim, int64_t N, Geometry* g) {
 }
 
 static int default_stencil(const qw_plan_s* p) {
-  // measured on GB300 (BCC N = 512): the fused two-step kernel (one HBM pass per
-  // two steps, shared-memory bound) ahead of the one-step TMA kernel (HBM bound);
-  // qw_plan_autotune re-measures on the device.
+  // measured on GB300: BCC N = 512, the fused two-step kernel (one HBM pass per two steps,
+  // shared-memory bound) ahead of the one-step TMA kernel (HBM bound); the chain (N = 2^28),
+  // FUSED with four steps per launch ahead of PLAIN (232 against 209 G site-steps/s); the
+  // square lattice, PLAIN.  qw_plan_autotune re-measures on the device.
   if (stencil_supported(p->g, p->dtype, QW_STENCIL_TMA2)) return QW_STENCIL_TMA2;
+  if (p->g.dim == 1 && fused_step_supported(p->g, p->dtype, p->fuse_depth, p->fuse_box)) return QW_STENCIL_FUSED;
   if (stencil_supported(p->g, p->dtype, QW_STENCIL_TMA)) return QW_STENCIL_TMA;
   if (stencil_supported(p->g, p->dtype, QW_STENCIL_VEC)) return QW_STENCIL_VEC;
   return QW_STENCIL_PLAIN;
@@ -306,6 +312,8 @@ qw_status qw_step(qw_plan p, void* psi, int64_t nsteps, void* stream) {
   // the VEC, TMA and TMA2 kernels move 16-byte vectors: a complex64 field that is only
   // 8-byte aligned (e.g. a view one element into an allocation) takes the PLAIN kernel
   const int variant = (aligned16(psi) || p->stencil == QW_STENCIL_FUSED) ? p->stencil : QW_STENCIL_PLAIN;
+  if (debug_poison())
+    QW_CHECK_CUDA(cudaMemsetAsync(p->scratch, kPoisonByte, (size_t)p->g.elems * p->elem_bytes, s));
   void* cur = psi;
   void* nxt = p->scratch;
   for (int64_t i = 0; i < nsteps;) {
@@ -518,6 +526,8 @@ qw_status qw_sync(qw_plan p, void* stream) {
 // Observables of psi: the reductions are enqueued on s, then obs_finish waits for them
 // and fills *out.  kspace: whether the particle weights are computed (axis lengths 2^a 3^b).
 static qw_status obs_enqueue(qw_plan_s* p, const void* psi, cudaStream_t s, double* host_dst, bool* kspace_out) {
+  if (debug_poison())
+    QW_CHECK_CUDA(cudaMemsetAsync(p->scratch, kPoisonByte, (size_t)p->g.elems * p->elem_bytes, s));
   qw_status st = launch_position_moments(p->g, p->dtype, psi, p->red_partials, p->red_result, s);
   if (st != QW_OK) return st;
   // particle weights need the spectrum (computed into the scratch field)
@@ -823,6 +833,11 @@ qw_status qw_plan_get_fusion(qw_plan p, int* depth, int* box) {
 qw_status qw_set_autotune_cache(const char* path) {
   std::lock_guard<std::mutex> lock(g_cache_mu);
   g_cache_path = path ? path : "";
+  return QW_OK;
+}
+
+qw_status qw_set_debug_poison(int on) {
+  g_poison.store(on != 0, std::memory_order_relaxed);
   return QW_OK;
 }
 

@@ -462,13 +462,15 @@ struct qw_batch_s {
 
 namespace qw {
 
+// Defaults: what the autotuner picks for the 256-walk mix on GB300 (depth 1 on every lattice,
+// 2048-site rows, one group); the boxes are those of fused rounds when a depth is raised.
 static qw_batch_tiling default_tiling() {
   qw_batch_tiling t;
-  t.tile_sites = 4096;
+  t.tile_sites = 2048;
   t.l2_budget_bytes = int64_t(16) << 30;
-  t.depth[0] = 2;
-  t.depth[1] = 2;
-  t.depth[2] = 2;
+  t.depth[0] = 1;
+  t.depth[1] = 1;
+  t.depth[2] = 1;
   const int box[3][3] = {{1024, 1, 1}, {32, 16, 1}, {8, 8, 4}};
   for (int d = 0; d < 3; ++d)
     for (int a = 0; a < 3; ++a) t.box[d][a] = box[d][a];
@@ -737,6 +739,9 @@ static qw_status build_schedule(qw_batch_s* b) {
 }
 
 static qw_status launch_batch(qw_batch_s* b, cudaStream_t s) {
+  if (debug_poison())  // every round writes its tile of the partner before any round reads it
+    for (int i = 0; i < b->n; ++i)
+      QW_CHECK_CUDA(cudaMemsetAsync(b->partners[i], kPoisonByte, field_bytes(b->desc[i]), s));
   QW_CHECK_CUDA(cudaMemsetAsync(b->d_done, 0, std::max<int64_t>(1, b->ndone) * sizeof(unsigned int), s));
   QW_CHECK_CUDA(cudaMemsetAsync(b->d_ctl, 0, sizeof(BatchCtl), s));
   if (b->fused)

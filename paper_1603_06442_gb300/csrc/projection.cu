@@ -90,9 +90,12 @@ struct RowWalk {
   }
 };
 
-template <typename R>
+// S: spinor components (compile time): a group's loads (four rows, every component) are all
+// issued before its sums.
+template <typename R, int S>
 __global__ void __launch_bounds__(256) proj_x_kernel(const typename Cx<R>::T* __restrict__ psi, ProjGeo p,
                                                      double* __restrict__ out, double* __restrict__ partials) {
+  using C = typename Cx<R>::T;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= p.nout) return;
   const int x = (int)(gid % p.nx);
@@ -103,20 +106,27 @@ __global__ void __launch_bounds__(256) proj_x_kernel(const typename Cx<R>::T* __
   const int64_t r0 = j * p.rrows / p.chunks, r1 = (j + 1) * p.rrows / p.chunks;
   double acc = 0.0;
   RowWalk w(p, zk, yk, r0);
-  int64_t r = r0;
   // groups of four rows summed in the field's precision, then in FP64
-  for (; r + 4 <= r1; r += 4) {
-    R g = 0;
+  for (int64_t r = r0; r < r1; r += 4) {
+    C v[4][S];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      g += density<R>(psi + w.offset(p, c) + x, p.s, p.vol);
-      w.next(p);
+      if (r + u < r1) {
+        const C* q = psi + w.offset(p, c) + x;
+#pragma unroll
+        for (int k = 0; k < S; ++k) v[u][k] = q[(int64_t)k * p.vol];
+        w.next(p);
+      } else {
+#pragma unroll
+        for (int k = 0; k < S; ++k) v[u][k] = C{0, 0};
+      }
     }
+    R g = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < S; ++k) g = fma(v[u][k].x, v[u][k].x, fma(v[u][k].y, v[u][k].y, g));
     acc += (double)g;
-  }
-  for (; r < r1; ++r) {
-    acc += (double)density<R>(psi + w.offset(p, c) + x, p.s, p.vol);
-    w.next(p);
   }
   if (p.chunks == 1)
     out[phys_index(p, c, zk, yk, x)] = acc;
@@ -126,6 +136,7 @@ __global__ void __launch_bounds__(256) proj_x_kernel(const typename Cx<R>::T* __
 
 // proj_x_kernel for complex64 with two adjacent x per thread (x even): one 16-byte load per
 // component and row instead of two 8-byte ones.
+template <int S>
 __global__ void __launch_bounds__(256) proj_x2_kernel(const float2* __restrict__ psi, ProjGeo p,
                                                       double* __restrict__ out, double* __restrict__ partials) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,21 +150,28 @@ __global__ void __launch_bounds__(256) proj_x2_kernel(const float2* __restrict__
   const int64_t r0 = j * p.rrows / p.chunks, r1 = (j + 1) * p.rrows / p.chunks;
   double a0 = 0.0, a1 = 0.0;
   RowWalk w(p, zk, yk, r0);
-  for (int64_t r = r0; r < r1;) {
-    float g0 = 0.f, g1 = 0.f;
-    const int64_t rend = r + 4 < r1 ? r + 4 : r1;
-    for (; r < rend; ++r) {
-      const float2* q = psi + w.offset(p, c) + x;
-      float d0 = 0.f, d1 = 0.f;
-      for (int s = 0; s < p.s; ++s) {
-        const float4 v = *reinterpret_cast<const float4*>(q + (int64_t)s * p.vol);
-        d0 = fmaf(v.x, v.x, fmaf(v.y, v.y, d0));
-        d1 = fmaf(v.z, v.z, fmaf(v.w, v.w, d1));
+  for (int64_t r = r0; r < r1; r += 4) {
+    float4 v[4][S];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (r + u < r1) {
+        const float2* q = psi + w.offset(p, c) + x;
+#pragma unroll
+        for (int k = 0; k < S; ++k) v[u][k] = *reinterpret_cast<const float4*>(q + (int64_t)k * p.vol);
+        w.next(p);
+      } else {
+#pragma unroll
+        for (int k = 0; k < S; ++k) v[u][k] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      g0 += d0;
-      g1 += d1;
-      w.next(p);
     }
+    float g0 = 0.f, g1 = 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < S; ++k) {
+        g0 = fmaf(v[u][k].x, v[u][k].x, fmaf(v[u][k].y, v[u][k].y, g0));
+        g1 = fmaf(v[u][k].z, v[u][k].z, fmaf(v[u][k].w, v[u][k].w, g1));
+      }
     a0 += (double)g0;
     a1 += (double)g1;
   }
@@ -267,12 +285,19 @@ qw_status launch_projection(const Geometry& g, qw_dtype dt, const void* psi, int
   const int64_t threads = p.kx ? (p.pair ? p.nout / 2 : p.nout) : p.n_orows * 32;
   const dim3 grid((unsigned)((threads + 255) / 256), (unsigned)p.chunks);
   if (p.pair) {
-    proj_x2_kernel<<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
-  } else if (p.kx) {
-    if (dt == QW_C64)
-      proj_x_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
+    if (g.s == 2)
+      proj_x2_kernel<2><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
     else
-      proj_x_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double2*>(psi), p, out, partials);
+      proj_x2_kernel<4><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
+  } else if (p.kx) {
+    if (dt == QW_C64 && g.s == 2)
+      proj_x_kernel<float, 2><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
+    else if (dt == QW_C64)
+      proj_x_kernel<float, 4><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
+    else if (g.s == 2)
+      proj_x_kernel<double, 2><<<grid, 256, 0, st>>>(static_cast<const double2*>(psi), p, out, partials);
+    else
+      proj_x_kernel<double, 4><<<grid, 256, 0, st>>>(static_cast<const double2*>(psi), p, out, partials);
   } else {
     if (dt == QW_C64)
       proj_w_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);

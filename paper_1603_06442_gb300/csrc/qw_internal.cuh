@@ -51,6 +51,11 @@ template <typename T> struct CplxOf2;
 template <> struct CplxOf2<float> { using t = float2; };
 template <> struct CplxOf2<double> { using t = double2; };
 
+// ---- debug poison (api.cu): while on, scratch and partner buffers are filled with NaN
+// (all bytes 0xFF) before each call that must write them before reading them
+bool debug_poison();
+constexpr int kPoisonByte = 0xFF;  // 0xFFFFFFFF / 0xFFFF...FF are NaN in FP32 and FP64
+
 // ---- autotune cache (api.cu) ------------------------------------------------
 // A text file of "key | value" lines; the key starts with the GPU model.  Lookups take the
 // last line with the key; stores append.  Both are no-ops while no cache file is set.

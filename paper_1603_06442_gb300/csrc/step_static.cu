@@ -86,6 +86,7 @@ extern "C" qw_status qw_step_static(int dim, int64_t N, double mass, qw_dtype dt
   const int variant =
       (stencil_supported(g, dtype, QW_STENCIL_VEC) && aligned16(psi)) ? QW_STENCIL_VEC : QW_STENCIL_PLAIN;
   const double n = std::sqrt(1.0 - mass * mass);
+  if (debug_poison()) QW_CHECK_CUDA(cudaMemsetAsync(scratch, kPoisonByte, bytes, s));
   void* cur = psi;
   void* nxt = scratch;
   for (int64_t i = 0; i < nsteps; ++i) {
