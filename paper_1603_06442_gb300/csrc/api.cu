@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <string>
@@ -48,6 +49,23 @@ qw_status smem_attr_once(const void* func, int bytes) {
   QW_CHECK_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   limit[key] = bytes;
   return QW_OK;
+}
+
+int resident_blocks_once(const void* func, int threads, int smem) {
+  // blocks of func resident on the whole device (per-SM occupancy x SMs), per device
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, int, int>, int> known;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const auto key = std::make_tuple(func, dev, threads, smem);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = known.find(key);
+  if (it != known.end()) return it->second;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return known[key] = per_sm * sms;
 }
 
 static std::atomic<bool> g_poison{false};
@@ -143,7 +161,9 @@ static int default_stencil(const qw_plan_s* p) {
 }
 
 static qw_status check_flags(qw_plan_s* p, cudaStream_t s) {
-  int flags[2] = {0, 0};
+  // the error word lands in the last slot of the pinned result buffer (an asynchronous copy;
+  // a pageable destination would be staged)
+  int* flags = reinterpret_cast<int*>(p->red_host + 15);
   QW_CHECK_CUDA(cudaMemcpyAsync(flags, p->dev_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
   QW_CHECK_CUDA(cudaStreamSynchronize(s));
   if (flags[0] != 0) {

@@ -10,7 +10,8 @@
 //   x summed  a warp owns an output row and a chunk of its reduced rows, lanes striding
 //             along x, then a warp sum.
 // With one chunk a kernel writes the physical output directly; otherwise it writes
-// partials [chunk][output] and proj_fold_kernel adds the chunks in order.  Site densities
+// partials [chunk][output] and a fold adds the chunks in a fixed order (a thread per output,
+// or with 64 chunks or more a warp per output).  Site densities
 // are taken in the field's precision and summed in FP64 in a fixed order: deterministic.
 #include <cuda_runtime.h>
 
@@ -90,9 +91,9 @@ struct RowWalk {
   }
 };
 
-// S: spinor components (compile time): a group's loads (four rows, every component) are all
-// issued before its sums.
-template <typename R, int S>
+// S: spinor components, G: rows per group (4, or 1 when a chunk has fewer than four rows),
+// compile time: a group's loads (G rows, every component) are all issued before its sums.
+template <typename R, int S, int G>
 __global__ void __launch_bounds__(256) proj_x_kernel(const typename Cx<R>::T* __restrict__ psi, ProjGeo p,
                                                      double* __restrict__ out, double* __restrict__ partials) {
   using C = typename Cx<R>::T;
@@ -106,11 +107,11 @@ __global__ void __launch_bounds__(256) proj_x_kernel(const typename Cx<R>::T* __
   const int64_t r0 = j * p.rrows / p.chunks, r1 = (j + 1) * p.rrows / p.chunks;
   double acc = 0.0;
   RowWalk w(p, zk, yk, r0);
-  // groups of four rows summed in the field's precision, then in FP64
-  for (int64_t r = r0; r < r1; r += 4) {
-    C v[4][S];
+  // groups of G rows summed in the field's precision, then in FP64
+  for (int64_t r = r0; r < r1; r += G) {
+    C v[G][S];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < G; ++u) {
       if (r + u < r1) {
         const C* q = psi + w.offset(p, c) + x;
 #pragma unroll
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256) proj_x_kernel(const typename Cx<R>::T* __
     }
     R g = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < G; ++u)
 #pragma unroll
       for (int k = 0; k < S; ++k) g = fma(v[u][k].x, v[u][k].x, fma(v[u][k].y, v[u][k].y, g));
     acc += (double)g;
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(256) proj_x_kernel(const typename Cx<R>::T* __
 
 // proj_x_kernel for complex64 with two adjacent x per thread (x even): one 16-byte load per
 // component and row instead of two 8-byte ones.
-template <int S>
+template <int S, int G>
 __global__ void __launch_bounds__(256) proj_x2_kernel(const float2* __restrict__ psi, ProjGeo p,
                                                       double* __restrict__ out, double* __restrict__ partials) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,10 +151,10 @@ __global__ void __launch_bounds__(256) proj_x2_kernel(const float2* __restrict__
   const int64_t r0 = j * p.rrows / p.chunks, r1 = (j + 1) * p.rrows / p.chunks;
   double a0 = 0.0, a1 = 0.0;
   RowWalk w(p, zk, yk, r0);
-  for (int64_t r = r0; r < r1; r += 4) {
-    float4 v[4][S];
+  for (int64_t r = r0; r < r1; r += G) {
+    float4 v[G][S];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < G; ++u) {
       if (r + u < r1) {
         const float2* q = psi + w.offset(p, c) + x;
 #pragma unroll
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(256) proj_x2_kernel(const float2* __restrict__
     }
     float g0 = 0.f, g1 = 0.f;
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < G; ++u)
 #pragma unroll
       for (int k = 0; k < S; ++k) {
         g0 = fmaf(v[u][k].x, v[u][k].x, fmaf(v[u][k].y, v[u][k].y, g0));
@@ -181,6 +182,63 @@ __global__ void __launch_bounds__(256) proj_x2_kernel(const float2* __restrict__
   } else {
     partials[(int64_t)j * p.nout + o] = a0;
     partials[(int64_t)j * p.nout + o + 1] = a1;
+  }
+}
+
+// BCC, every axis kept (the site density on the physical N^3 grid): a thread owns W cells
+// of one storage x line and the 2 W physical points (2 x, 2 x + 1, ...) of one physical row
+// (Z, Y), which it writes whole: the density at the even points of a row with Z and Y even
+// (coset 0), at the odd points of a row with Z and Y odd (coset 1), zero elsewhere (rows of
+// mixed parity are written without a read).  V2: out is 16-byte aligned.
+template <typename R, int W, bool V2>
+__global__ void __launch_bounds__(256) density_bcc_kernel(const typename Cx<R>::T* __restrict__ psi, ProjGeo p,
+                                                          double* __restrict__ out) {
+  using C = typename Cx<R>::T;
+  const int64_t per_row = p.nx / W;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)p.N * p.N * per_row) return;
+  const int64_t prow = gid / per_row;  // Z * N + Y
+  const int xi = (int)(gid - prow * per_row) * W;
+  const int Z = (int)(prow / p.N), Y = (int)(prow - (int64_t)Z * p.N);
+  double d[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) d[w] = 0.0;
+  const int c = Z & 1;
+  const bool site = (Z & 1) == (Y & 1);
+  if (site) {
+    const C* q = psi + (int64_t)c * p.s * p.vol + ((int64_t)(Z >> 1) * p.ny + (Y >> 1)) * p.nx + xi;
+    if constexpr (W == 2) {
+      float4 v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = *reinterpret_cast<const float4*>(q + (int64_t)k * p.vol);
+      float g0 = 0.f, g1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        g0 = fmaf(v[k].x, v[k].x, fmaf(v[k].y, v[k].y, g0));
+        g1 = fmaf(v[k].z, v[k].z, fmaf(v[k].w, v[k].w, g1));
+      }
+      d[0] = g0;
+      d[W - 1] = g1;
+    } else {
+      C v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = q[(int64_t)k * p.vol];
+      R g = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) g = fma(v[k].x, v[k].x, fma(v[k].y, v[k].y, g));
+      d[0] = (double)g;
+    }
+  }
+  double* o = out + prow * p.N + 2 * xi;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const double e = c ? 0.0 : d[w], f = c ? d[w] : 0.0;  // points 2 (xi + w) and 2 (xi + w) + 1
+    if constexpr (V2) {
+      *reinterpret_cast<double2*>(o + 2 * w) = make_double2(e, f);
+    } else {
+      o[2 * w] = e;
+      o[2 * w + 1] = f;
+    }
   }
 }
 
@@ -224,6 +282,26 @@ __global__ void __launch_bounds__(256) proj_fold_kernel(const double* __restrict
   int c, zk, yk;
   decode_orow(p, orow, c, zk, yk);
   out[phys_index(p, c, zk, yk, xk)] = acc;
+}
+
+// proj_fold_kernel for many chunks (few outputs, each with a long column of partials): a warp
+// per output, lane l adding the chunks l, l + 32, ..., then a warp sum (a fixed order).
+__global__ void __launch_bounds__(256) proj_fold_warp_kernel(const double* __restrict__ partials, ProjGeo p,
+                                                             double* __restrict__ out) {
+  const int64_t nout = p.kx ? p.nout : p.n_orows;
+  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gid >= nout) return;  // whole warps leave together
+  double acc = 0.0;
+  for (int j = lane; j < p.chunks; j += 32) acc += partials[(int64_t)j * nout + gid];
+  acc = warp_sum_d(acc);
+  if (lane == 0) {
+    const int xk = p.kx ? (int)(gid % p.nx) : 0;
+    const int64_t orow = p.kx ? gid / p.nx : gid;
+    int c, zk, yk;
+    decode_orow(p, orow, c, zk, yk);
+    out[phys_index(p, c, zk, yk, xk)] = acc;
+  }
 }
 
 // Threads (x kept) and warps (x summed) a launch aims for: ~1700 threads per SM.
@@ -279,25 +357,53 @@ qw_status launch_projection(const Geometry& g, qw_dtype dt, const void* psi, int
                             double* partials, cudaStream_t st) {
   const ProjGeo p = make_proj(g, keep, dt, aligned16(psi));
   const int kept = p.kx + p.ky + p.kz;
+  if (g.dim == 3 && kept == 3) {  // every point of the output written once, zeros included
+    const int w = p.pair ? 2 : 1;
+    const int64_t threads = (int64_t)p.N * p.N * (p.nx / w);
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    const bool v2 = aligned16(out);
+    if (dt == QW_C64 && p.pair)
+      v2 ? density_bcc_kernel<float, 2, true><<<blocks, 256, 0, st>>>(static_cast<const float2*>(psi), p, out)
+         : density_bcc_kernel<float, 2, false><<<blocks, 256, 0, st>>>(static_cast<const float2*>(psi), p, out);
+    else if (dt == QW_C64)
+      v2 ? density_bcc_kernel<float, 1, true><<<blocks, 256, 0, st>>>(static_cast<const float2*>(psi), p, out)
+         : density_bcc_kernel<float, 1, false><<<blocks, 256, 0, st>>>(static_cast<const float2*>(psi), p, out);
+    else
+      v2 ? density_bcc_kernel<double, 1, true><<<blocks, 256, 0, st>>>(static_cast<const double2*>(psi), p, out)
+         : density_bcc_kernel<double, 1, false><<<blocks, 256, 0, st>>>(static_cast<const double2*>(psi), p, out);
+    QW_CHECK_LAUNCH("density launch");
+    return QW_OK;
+  }
   // BCC: physical points of mixed coordinate parity are not sites (two or more kept axes)
   if (g.dim == 3 && kept >= 2)
     QW_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * projection_outputs(g, keep), st));
   const int64_t threads = p.kx ? (p.pair ? p.nout / 2 : p.nout) : p.n_orows * 32;
   const dim3 grid((unsigned)((threads + 255) / 256), (unsigned)p.chunks);
+  const bool few = p.rrows < 4 * (int64_t)p.chunks;  // chunks of fewer than four rows: one row per group
   if (p.pair) {
+    const float2* q = static_cast<const float2*>(psi);
     if (g.s == 2)
-      proj_x2_kernel<2><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
+      few ? proj_x2_kernel<2, 1><<<grid, 256, 0, st>>>(q, p, out, partials)
+          : proj_x2_kernel<2, 4><<<grid, 256, 0, st>>>(q, p, out, partials);
     else
-      proj_x2_kernel<4><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
+      few ? proj_x2_kernel<4, 1><<<grid, 256, 0, st>>>(q, p, out, partials)
+          : proj_x2_kernel<4, 4><<<grid, 256, 0, st>>>(q, p, out, partials);
+  } else if (p.kx && dt == QW_C64) {
+    const float2* q = static_cast<const float2*>(psi);
+    if (g.s == 2)
+      few ? proj_x_kernel<float, 2, 1><<<grid, 256, 0, st>>>(q, p, out, partials)
+          : proj_x_kernel<float, 2, 4><<<grid, 256, 0, st>>>(q, p, out, partials);
+    else
+      few ? proj_x_kernel<float, 4, 1><<<grid, 256, 0, st>>>(q, p, out, partials)
+          : proj_x_kernel<float, 4, 4><<<grid, 256, 0, st>>>(q, p, out, partials);
   } else if (p.kx) {
-    if (dt == QW_C64 && g.s == 2)
-      proj_x_kernel<float, 2><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
-    else if (dt == QW_C64)
-      proj_x_kernel<float, 4><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
-    else if (g.s == 2)
-      proj_x_kernel<double, 2><<<grid, 256, 0, st>>>(static_cast<const double2*>(psi), p, out, partials);
+    const double2* q = static_cast<const double2*>(psi);
+    if (g.s == 2)
+      few ? proj_x_kernel<double, 2, 1><<<grid, 256, 0, st>>>(q, p, out, partials)
+          : proj_x_kernel<double, 2, 4><<<grid, 256, 0, st>>>(q, p, out, partials);
     else
-      proj_x_kernel<double, 4><<<grid, 256, 0, st>>>(static_cast<const double2*>(psi), p, out, partials);
+      few ? proj_x_kernel<double, 4, 1><<<grid, 256, 0, st>>>(q, p, out, partials)
+          : proj_x_kernel<double, 4, 4><<<grid, 256, 0, st>>>(q, p, out, partials);
   } else {
     if (dt == QW_C64)
       proj_w_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float2*>(psi), p, out, partials);
@@ -307,7 +413,10 @@ qw_status launch_projection(const Geometry& g, qw_dtype dt, const void* psi, int
   QW_CHECK_LAUNCH("projection launch");
   if (p.chunks > 1) {
     const int64_t n = p.kx ? p.nout : p.n_orows;
-    proj_fold_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partials, p, out);
+    if (p.chunks >= 64)
+      proj_fold_warp_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(partials, p, out);
+    else
+      proj_fold_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partials, p, out);
     QW_CHECK_LAUNCH("projection fold launch");
   }
   return QW_OK;

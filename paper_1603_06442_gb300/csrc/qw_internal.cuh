@@ -34,6 +34,12 @@ template <typename K>
 inline qw_status smem_attr(K* kernel, int bytes) {
   return smem_attr_once(reinterpret_cast<const void*>(kernel), bytes);
 }
+// Blocks of a kernel resident on the current device at once (0 if the query fails).
+int resident_blocks_once(const void* func, int threads, int smem);
+template <typename K>
+inline int resident_blocks(K* kernel, int threads, int smem = 0) {
+  return resident_blocks_once(reinterpret_cast<const void*>(kernel), threads, smem);
+}
 
 #define QW_CHECK_CUDA(call)                                        \
   do {                                                             \
@@ -244,7 +250,7 @@ struct qw_plan_s {
   double* xw_partials;    // 2 doubles per CTA of the x-pass weights (when the x pass is fused)
   double* red_partials; // 10 * kMom2MaxBlocks doubles (>= 4 * kObsBlocks)
   double* red_result;   // 16 doubles (device)
-  double* red_host;     // 16 doubles (pinned host)
+  double* red_host;     // 16 doubles (pinned host); the last holds the copied error word
   // host-field runs (qw_run_host): two device fields, a copy stream and its events,
   // allocated by the first call
   void* hbuf[2];

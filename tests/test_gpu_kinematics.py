@@ -32,19 +32,71 @@ def to_dev(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a.astype(npdt))).cuda()
 
 
+def moments_field(dim, N):
+    a = inputs.gaussian_packet(dim, N, [N / 3] * dim, N / 9, [0.2] * dim,
+                               [1, 0] if dim == 1 else [0.6, 0.8j, 0, 0])
+    return a + 0.2 * inputs.random_field(dim, N, 6)
+
+
 @pytest.mark.parametrize("dim,N", [(1, 64), (1, 1000), (2, 24), (2, 33), (3, 16), (3, 42), (3, 128)])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_position_moments_match_oracle(qb, dim, N, dtype):
-    a = inputs.gaussian_packet(dim, N, [N / 3] * dim, N / 9, [0.2] * dim,
+    a = moments_field(dim, N)
+    plan = qb.Plan(dim, N, 0.1, dtype)
+    check_moments(plan, dim, N, dtype, a, to_dev(a, dtype))
+    plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_position_moments_long_chain(qb, dtype):
+    """2^20 sites on one row: far more units than threads, every thread strides over many."""
+    dim, N = 1, 1 << 20
+    a = moments_field(dim, N)
+    plan = qb.Plan(dim, N, 0.1, dtype)
+    check_moments(plan, dim, N, dtype, a, to_dev(a, dtype))
+    plan.close()
+
+
+@pytest.mark.parametrize("dim,N", [(1, 1000), (2, 64), (3, 64)])
+def test_position_moments_misaligned_complex64(qb, dim, N):
+    """Paired (16-byte) loads only on 16-byte aligned complex64 fields: an 8-byte aligned view
+    takes the scalar kernel and gives the same moments."""
+    a = moments_field(dim, N).astype(np.complex64)
+    plan = qb.Plan(dim, N, 0.1, "c64")
+    buf = torch.zeros(a.size + 1, dtype=torch.complex64, device="cuda")
+    x_off = buf[1:]
+    x_off.copy_(torch.from_numpy(a.ravel()))
+    assert x_off.data_ptr() % 16 == 8
+    check_moments(plan, dim, N, "c64", a, x_off)
+    plan.close()
+
+
+@pytest.mark.parametrize("dim,N", [(1, 4096), (2, 1024), (3, 128)])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_position_covariance_narrow_far_packet(qb, dim, N, dtype):
+    """A packet a few sites wide at 0.8 N: its covariance is a small difference of raw moments
+    of size (0.8 N)^2, so a coordinate product rounded in the field's precision would show at
+    ~1e-7 (0.8 N)^2.  Bound: 2e-5 of the covariance scale in complex64 (FP32 site densities
+    alone give ~1e-7), 1e-10 in complex128."""
+    a = inputs.gaussian_packet(dim, N, [0.8 * N] * dim, 2.5, [0.3] * dim,
                                [1, 0] if dim == 1 else [0.6, 0.8j, 0, 0])
-    a = a + 0.2 * inputs.random_field(dim, N, 6)
     npdt = np.complex64 if dtype == "c64" else np.complex128
     psi = walk.from_device(dim, N, a.astype(npdt))
     plan = qb.Plan(dim, N, 0.1, dtype)
-    x = to_dev(a, dtype)
+    got = plan.position_moments(to_dev(a, dtype))
+    plan.close()
+    cov = observables.position_covariance(dim, psi)
+    scale = float(np.abs(cov).max())
+    tol = (2e-5 if dtype == "c64" else 1e-10) * scale
+    err = max(abs(got["cov"][i][j] - cov[i, j]) for i in range(dim) for j in range(dim))
+    assert err <= tol, (err, scale)
+
+
+def check_moments(plan, dim, N, dtype, a, x):
+    npdt = np.complex64 if dtype == "c64" else np.complex128
+    psi = walk.from_device(dim, N, a.astype(npdt))
     got = plan.position_moments(x)
     obs = plan.observables(x)
-    plan.close()
     rtol = 1e-12 if dtype == "c128" else 1e-6
     ctol = (1e-12 if dtype == "c128" else 1e-6) * N * N
     nrm = observables.norm(psi)

@@ -170,3 +170,29 @@ def test_misaligned_complex64_projection_matches_aligned(qb):
         assert np.abs(p_off - ref).max() <= 2e-6 * scale, keep
         assert np.abs(p_al - ref).max() <= 2e-6 * scale, keep
     plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("N", [64, 42])
+def test_bcc_density_writes_every_point(qb, dtype, N):
+    """The BCC site density (every axis kept) writes each of the N^3 physical points, the
+    zeros of the points that are not sites included, whatever the output held before; an
+    8-byte aligned output takes scalar stores and gives the same values."""
+    dim = 3
+    a = inputs.random_field(dim, N, seed=31 + N)
+    npdt = np.complex64 if dtype == "c64" else np.complex128
+    psi = walk.from_device(dim, N, a.astype(npdt))
+    ref = expected(dim, psi, 7)
+    plan = qb.Plan(dim, N, 0.1, dtype)
+    x = to_dev(a, dtype)
+    n = N ** 3
+    buf = torch.full((n + 1,), float("nan"), dtype=torch.float64, device="cuda")
+    for out in (buf[:n], buf[1:]):
+        out.fill_(float("nan"))
+        qb.qw_projection(plan.handle, x, 7, out)
+        got = out.cpu().numpy().reshape(ref.shape)
+        assert not np.isnan(got).any()
+        assert np.all(got[ref == 0] == 0.0)
+        check(got, ref, dtype)
+    assert buf[1:].data_ptr() % 16 == 8
+    plan.close()
