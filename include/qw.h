@@ -170,11 +170,12 @@ qw_status qw_step(qw_plan plan, void* psi_dev, int64_t nsteps, void* stream);
 
 /* Build the spectral-path state of the plan: FFT pass plans and twiddle
  * tables, and the table of omega_k = atan2(sin omega_k, n u_k) (Sec. 3.2,
- * cos omega_k = n u_k) for every stored wave vector (one per site in 1D/2D,
- * two per cell on the BCC lattice): complex128 plans hold omega_k as a
- * double-double (16 bytes per site, ~1e-31 accurate, so that the phase
- * omega_k t keeps ~1e-16 at any t), complex64 plans omega_k / 2 pi as a pair of
- * FP32 numbers (8 bytes per site).  Synchronous; done
+ * cos omega_k = n u_k) for every stored wave vector (one per site in 1D/2D; on
+ * the BCC lattice one per cell, the wave vector q0 of its pair, since
+ * omega_q1 = pi - omega_q0): complex128 plans hold omega_k as a double-double
+ * (16 bytes per entry, ~1e-31 accurate, so that the phase omega_k t keeps ~1e-16
+ * at any t), complex64 plans omega_k / 2 pi as a pair of FP32 numbers (8 bytes
+ * per entry).  Synchronous; done
  * implicitly by the first qw_evolve_spectral / qw_observables call.
  * Needs every axis length (N, or N/2 for dim 3) of the form 2^a 3^b.
  * Errors: QW_EINVAL (axis length not 2^a 3^b), QW_ENOMEM, QW_ECUDA. */

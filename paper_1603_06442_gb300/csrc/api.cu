@@ -182,10 +182,9 @@ static qw_status prepare_spectral(qw_plan_s* p) {
     fft_plan_destroy(&p->fft);
     return st;
   }
-  const int nq = p->g.dim == 3 ? 2 : 1;
   // 8 bytes per stored wave vector (complex64: the split nu pair), 16 for complex128
-  // (omega as a double-double)
-  QW_CHECK_CUDA(cudaMalloc(&p->omega, (p->dtype == QW_C64 ? 8 : 16) * nq * p->g.vol));
+  // (omega as a double-double); BCC stores q0 of each cell only
+  QW_CHECK_CUDA(cudaMalloc(&p->omega, (p->dtype == QW_C64 ? 8 : 16) * p->g.vol));
   QW_CHECK_CUDA(cudaMalloc(&p->spec_partials, sizeof(double) * 2 * kObsBlocks));
   if (fused_x_supported(p->g, p->fft, p->dtype))
     QW_CHECK_CUDA(cudaMalloc(&p->xw_partials, sizeof(double) * 2 * fused_x_grid(p->g)));

@@ -244,8 +244,8 @@ struct qw_plan_s {
   // spectral path (allocated by the first spectral call or qw_plan_prepare_spectral)
   bool spec_ready;
   qw::FftPlan fft;
-  double* omega;        // omega_k per stored wave vector (two per cell on the BCC lattice): a double-
-                        // double (16 B) for complex128, nu = omega / 2 pi as an FP32 pair (8 B) for complex64
+  double* omega;        // omega_k per stored wave vector (BCC: q0 of each cell): a double-double
+                        // (16 B) for complex128, nu = omega / 2 pi as an FP32 pair (8 B) for complex64
   double* spec_partials;  // 2 * kObsBlocks doubles for the particle-weight reduction
   double* xw_partials;    // 2 doubles per CTA of the x-pass weights (when the x pass is fused)
   double* red_partials; // 10 * kMom2MaxBlocks doubles (>= 4 * kObsBlocks)

@@ -237,12 +237,12 @@ __device__ __forceinline__ void phase32(double omega, double tt, float& c, float
   sincosf((float)r, &s, &c);
 }
 
-// out = cos(phi) v - i sin(phi) G^ v for one wave vector, s = 2 or 4 components.
+// w = G^ v for one wave vector, s = 2 or 4 components: (gx, gy, gz) = n n~ / sin(omega),
+// gm = m / sin(omega).
 template <typename T, int S>
-__device__ __forceinline__ void apply_dt(typename Cx2<T>::t (&v)[S], T c, T s, T gn, T gx, T gy, T gz, T gm) {
+__device__ __forceinline__ void ghat_mul(const typename Cx2<T>::t (&v)[S], T gx, T gy, T gz, T gm,
+                                         typename Cx2<T>::t (&w)[S]) {
   using V = typename Cx2<T>::t;
-  // G^ v: gn = n / sin(omega) scaled n~ components (gx, gy, gz), gm = m / sin(omega)
-  V w[S];
   if (S == 2) {
     // G^ = [[gz, -gm], [-gm, -gz]] (1D: gz = n sin k / sin omega)
     w[0].x = gz * v[0].x - gm * v[1].x;
@@ -269,6 +269,14 @@ __device__ __forceinline__ void apply_dt(typename Cx2<T>::t (&v)[S], T c, T s, T
     w[3].x = -gm * v[1].x - sl1.x;
     w[3].y = -gm * v[1].y - sl1.y;
   }
+}
+
+// out = cos(phi) v - i sin(phi) G^ v for one wave vector, s = 2 or 4 components.
+template <typename T, int S>
+__device__ __forceinline__ void apply_dt(typename Cx2<T>::t (&v)[S], T c, T s, T gn, T gx, T gy, T gz, T gm) {
+  using V = typename Cx2<T>::t;
+  V w[S];
+  ghat_mul<T, S>(v, gx, gy, gz, gm, w);
   (void)gn;
 #pragma unroll
   for (int q = 0; q < S; ++q) {
@@ -532,7 +540,7 @@ __device__ __forceinline__ void evolve_point(int dim, const AxesDev& a, int64_t 
       // omega_q1 = pi - omega_q0 and D_q1 = -Gamma D_q0 Gamma with Gamma = diag(I, -I):
       // D_q1^t = (-1)^t Gamma D_q0^t Gamma.  One phase and one G^ serve both half spectra.
       T c, s, gx, gy, gz, gm;
-      cs_at<T, 4>(3, a, f, 0, 2 * idx, ms, omega, ta, c, s);
+      cs_at<T, 4>(3, a, f, 0, idx, ms, omega, ta, c, s);
       ghat<T>(3, a, f, 0, ms, gx, gy, gz, gm);
       apply_dt<T, 4>(c0, c, s, (T)0, gx, gy, gz, gm);
       c1[2] = make_vec(c1[2], (T)-1);
@@ -626,6 +634,125 @@ __device__ __forceinline__ void weights_point(int dim, const AxesDev& a, int64_t
   }
 }
 
+// Byte offset of the row constants after the L x CP line buffer (16-byte aligned).
+__host__ __device__ constexpr size_t fused_rowc_offset(int L, int CP) {
+  return (((size_t)L * CP * sizeof(float2)) + 15) & ~size_t(15);
+}
+
+// Row constants of the BCC symbol for the fused x pass.  With (cy, sy), (cz, sz) the
+// half-angle table entries of a row's y and z frequencies, A = cy cz, B = sy sz,
+// Cc = sy cz, D = cy sz give, for the x entry (cx, sx) of wave vector q0,
+//   n~ = (sx A - cx B, cx Cc + sx D, cx D - sx Cc)   (u = cx A + sx B is not needed: the
+// phase comes from the table), and the coset phase a = (cx + i sx)((A - B) + i (D + Cc)).
+__device__ __forceinline__ float4 bcc_row_consts(const AxesDev& a, int64_t row) {
+  const int ny = (int)a.len[1], rowi = (int)row;  // rows per plane < 2^31
+  const int64_t fy = freq_of(rowi % ny, a, 1), fz = freq_of(rowi / ny, a, 2);
+  float cy, sy, cz, sz;
+  tab<float>(a, 1, fy, cy, sy);
+  tab<float>(a, 2, fz, cz, sz);
+  return make_float4(cy * cz, sy * sz, sy * cz, cy * sz);
+}
+
+// evolve_point for a BCC cell in complex64 from its row constants rc and x frequency k
+// (the table slot of q0 is slot): G^ from an FP32 reciprocal square root with one Newton
+// step, and the scale, the halves of the coset mix and (-1)^t folded into cos and sin.
+__device__ __forceinline__ void evolve_bcc_row(const AxesDev& a, int k, float4 rc, const Mass& ms,
+                                               const float2* __restrict__ nu_tab, int64_t slot,
+                                               const TimeArg& ta, float scale, float2 (&v)[8]) {
+  using V = float2;
+  float cx, sx;
+  tab<float>(a, 0, k, cx, sx);
+  const float nx = sx * rc.x - cx * rc.y, ny = cx * rc.z + sx * rc.w, nz = cx * rc.w - sx * rc.z;
+  const float S2 = fmaf(ms.nf * ms.nf, fmaf(nx, nx, fmaf(ny, ny, nz * nz)), ms.mf * ms.mf);  // sin^2 omega
+  float inv = 0.f;
+  if (S2 > 0.f) {
+    const float r = rsqrtf(S2);
+    inv = r * fmaf(-0.5f * S2 * r, r, 1.5f);
+  }
+  const float ni = ms.nf * inv;
+  const float gx = ni * nx, gy = ni * ny, gz = ni * nz, gm = ms.mf * inv;
+  const float pr = rc.x - rc.y, pim = rc.w + rc.z;
+  const float ar = cx * pr - sx * pim, ai = cx * pim + sx * pr;  // a = exp(i (k1 + k2 + k3) / 2)
+  float c, s;
+  const float2 nu = nu_tab[slot];
+  if (ta.small) {
+    phase_split(nu, ta.tf, c, s);
+  } else {
+    cs_of<float, 4>(6.283185307179586232 * ((double)nu.x + (double)nu.y), ta.tt, c, s);
+  }
+  const float hs = 0.5f * scale;
+  c *= hs;
+  s *= hs;
+  // c0 = Psi0 + a* Psi1, and Gamma c1 with c1 = Psi0 - a* Psi1 (the halves are in hs)
+  V c0[4], c1[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    V b;
+    b.x = ar * v[4 + q].x + ai * v[4 + q].y;
+    b.y = ar * v[4 + q].y - ai * v[4 + q].x;
+    c0[q].x = v[q].x + b.x;
+    c0[q].y = v[q].y + b.y;
+    c1[q].x = q < 2 ? v[q].x - b.x : b.x - v[q].x;
+    c1[q].y = q < 2 ? v[q].y - b.y : b.y - v[q].y;
+  }
+  // D_q0^t c0 and D_q1^t c1 = (-1)^t Gamma D_q0^t (Gamma c1)
+  apply_dt<float, 4>(c0, c, s, 0.f, gx, gy, gz, gm);
+  const float sg = ta.odd ? -1.f : 1.f;
+  apply_dt<float, 4>(c1, sg * c, sg * s, 0.f, gx, gy, gz, gm);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float ex = q < 2 ? c1[q].x : -c1[q].x, ey = q < 2 ? c1[q].y : -c1[q].y;  // Gamma
+    const float dx = c0[q].x - ex, dy = c0[q].y - ey;
+    v[q].x = c0[q].x + ex;
+    v[q].y = c0[q].y + ey;
+    v[4 + q].x = ar * dx - ai * dy;
+    v[4 + q].y = ar * dy + ai * dx;
+  }
+}
+
+// weights_point for a BCC cell in complex64 from its row constants rc and x frequency k
+// (G^ as in evolve_bcc_row): acc[0] += |c0|^2 + |c1|^2, acc[1] += c0^dag G^_q0 c0 +
+// c1^dag G^_q1 c1 with G^_q1 = -Gamma G^_q0 Gamma.
+__device__ __forceinline__ void weights_bcc_row(const AxesDev& a, int k, float4 rc, const Mass& ms,
+                                                const float2 (&v)[8], float (&acc)[2]) {
+  using V = float2;
+  float cx, sx;
+  tab<float>(a, 0, k, cx, sx);
+  const float nx = sx * rc.x - cx * rc.y, ny = cx * rc.z + sx * rc.w, nz = cx * rc.w - sx * rc.z;
+  const float S2 = fmaf(ms.nf * ms.nf, fmaf(nx, nx, fmaf(ny, ny, nz * nz)), ms.mf * ms.mf);
+  float inv = 0.f;
+  if (S2 > 0.f) {
+    const float r = rsqrtf(S2);
+    inv = r * fmaf(-0.5f * S2 * r, r, 1.5f);
+  }
+  const float ni = ms.nf * inv;
+  const float gx = ni * nx, gy = ni * ny, gz = ni * nz, gm = ms.mf * inv;
+  const float pr = rc.x - rc.y, pim = rc.w + rc.z;
+  const float ar = cx * pr - sx * pim, ai = cx * pim + sx * pr;
+  V c0[4], c1[4];  // c0 = Psi0 + a* Psi1 and Gamma c1, c1 = Psi0 - a* Psi1
+  float nrm = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    V b;
+    b.x = ar * v[4 + q].x + ai * v[4 + q].y;
+    b.y = ar * v[4 + q].y - ai * v[4 + q].x;
+    c0[q].x = v[q].x + b.x;
+    c0[q].y = v[q].y + b.y;
+    c1[q].x = q < 2 ? v[q].x - b.x : b.x - v[q].x;
+    c1[q].y = q < 2 ? v[q].y - b.y : b.y - v[q].y;
+    nrm += c0[q].x * c0[q].x + c0[q].y * c0[q].y + c1[q].x * c1[q].x + c1[q].y * c1[q].y;
+  }
+  V w0[4], w1[4];
+  ghat_mul<float, 4>(c0, gx, gy, gz, gm, w0);
+  ghat_mul<float, 4>(c1, gx, gy, gz, gm, w1);
+  float g = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    g += (c0[q].x * w0[q].x + c0[q].y * w0[q].y) - (c1[q].x * w1[q].x + c1[q].y * w1[q].y);
+  acc[0] += nrm;
+  acc[1] += g;
+}
+
 // Fused x pass of the Fourier form (complex64): for RW rows of every component
 // plane, the forward DFT along x, D_k^t per wave vector (BCC coset mix included)
 // and the inverse DFT along x, with one read and one write of those rows.  The y
@@ -642,12 +769,14 @@ __global__ void __launch_bounds__(256, 3) fused_x_kernel(int dim, AxesDev a, int
   constexpr int CP = (C % 2 == 0) ? C + 1 : C;
   extern __shared__ __align__(16) unsigned char fx_smem[];
   V* sm = reinterpret_cast<V*>(fx_smem);
+  float4* rowc = reinterpret_cast<float4*>(fx_smem + fused_rowc_offset(L, CP));  // BCC row constants
   const float scale = norm0 ? scale_in * rsqrtf((float)norm0[0]) : scale_in;
   const int P = planes_of(dim);
   const int RW = C / P;                     // rows per CTA (C >= 8 >= P)
   const int CU = RW * P;                    // lines in use
   const int64_t nrows = count / L;          // rows per plane
   const int64_t row0 = (int64_t)blockIdx.x * RW;
+  const bool bcc_rows = dim == 3 && omega != nullptr;
   const int tid = threadIdx.x, c = tid % C, r = tid / C;
   const TwRow<V> tw{tw_line, r};
   // ---- load (cp.async): consecutive threads read consecutive x of one line; line cc = w P + p
@@ -667,24 +796,40 @@ __global__ void __launch_bounds__(256, 3) fused_x_kernel(int dim, AxesDev a, int
     const bool ok = cc < CU && row0 + w < nrows;
     if (cc < C) cp_async_elem(&sm[cc + CP * xx], ok ? data + p * count + (row0 + w) * L + xx : data, ok);
   }
+  if (bcc_rows && tid < RW && row0 + tid < nrows) rowc[tid] = bcc_row_consts(a, row0 + tid);  // while loading
   cp_async_wait_all();
   __syncthreads();
   reg_fft_steps<float, false, R1, R2, CP>(sm, c, r, tw);
   // ---- D_k^t at every (row, k) of the CTA
-  for (int q = tid; q < RW * L; q += 256) {
-    const int w = q / L, k = q - w * L;
-    const int64_t row = row0 + w;
-    if (row >= nrows) continue;
-    const int ny = (int)a.len[1], rowi = (int)row;  // rows per plane < 2^31
-    const int64_t yy = rowi % ny, zz = rowi / ny;
-    V v[8];
+  if (bcc_rows) {
+    const float2* nu_tab = reinterpret_cast<const float2*>(omega);
+    for (int q = tid; q < RW * L; q += 256) {
+      const int w = q / L, k = q - w * L;
+      const int64_t row = row0 + w;
+      if (row >= nrows) continue;
+      V v[8];
 #pragma unroll
-    for (int pp = 0; pp < 8; ++pp)
-      if (pp < P) v[pp] = sm[w * P + pp + CP * k];
-    evolve_point<float>(dim, a, k, yy, zz, row * L + k, ms, omega, ta, scale, v);
+      for (int pp = 0; pp < 8; ++pp) v[pp] = sm[w * 8 + pp + CP * k];
+      evolve_bcc_row(a, k, rowc[w], ms, nu_tab, row * L + k, ta, scale, v);
 #pragma unroll
-    for (int pp = 0; pp < 8; ++pp)
-      if (pp < P) sm[w * P + pp + CP * k] = v[pp];
+      for (int pp = 0; pp < 8; ++pp) sm[w * 8 + pp + CP * k] = v[pp];
+    }
+  } else {
+    for (int q = tid; q < RW * L; q += 256) {
+      const int w = q / L, k = q - w * L;
+      const int64_t row = row0 + w;
+      if (row >= nrows) continue;
+      const int ny = (int)a.len[1], rowi = (int)row;  // rows per plane < 2^31
+      const int64_t yy = rowi % ny, zz = rowi / ny;
+      V v[8];
+#pragma unroll
+      for (int pp = 0; pp < 8; ++pp)
+        if (pp < P) v[pp] = sm[w * P + pp + CP * k];
+      evolve_point<float>(dim, a, k, yy, zz, row * L + k, ms, omega, ta, scale, v);
+#pragma unroll
+      for (int pp = 0; pp < 8; ++pp)
+        if (pp < P) sm[w * P + pp + CP * k] = v[pp];
+    }
   }
   __syncthreads();
   reg_fft_steps<float, true, R1, R2, CP>(sm, c, r, tw);
@@ -710,7 +855,7 @@ qw_status launch_fused(const Geometry& g, const SpecAxes& ax, double n, double m
   const int RW = C / P;
   const int64_t nrows = g.vol / L;
   const int64_t grid = (nrows + RW - 1) / RW;
-  const size_t smem = (size_t)L * CP * sizeof(float2);
+  const size_t smem = fused_rowc_offset(L, CP) + 8 * sizeof(float4);  // lines, then up to 8 row constants
   const qw_status sa = smem_attr(fused_x_kernel<R1, R2>, (int)smem);
   if (sa != QW_OK) return sa;
   fused_x_kernel<R1, R2><<<(unsigned)grid, 256, smem, st>>>(
@@ -734,6 +879,7 @@ __global__ void __launch_bounds__(256, 3) weights_x_kernel(int dim, AxesDev a, i
   constexpr int CP = (C % 2 == 0) ? C + 1 : C;
   extern __shared__ __align__(16) unsigned char wx_smem[];
   V* sm = reinterpret_cast<V*>(wx_smem);
+  float4* rowc = reinterpret_cast<float4*>(wx_smem + fused_rowc_offset(L, CP));  // BCC row constants
   const int P = planes_of(dim);
   const int RW = C / P, CU = RW * P;
   const int64_t nrows = count / L;
@@ -754,21 +900,33 @@ __global__ void __launch_bounds__(256, 3) weights_x_kernel(int dim, AxesDev a, i
     const bool ok = cc < CU && row0 + w < nrows;
     if (cc < C) cp_async_elem(&sm[cc + CP * xx], ok ? data + p * count + (row0 + w) * L + xx : data, ok);
   }
+  if (dim == 3 && tid < RW && row0 + tid < nrows) rowc[tid] = bcc_row_consts(a, row0 + tid);  // while loading
   cp_async_wait_all();
   __syncthreads();
   reg_fft_steps<float, false, R1, R2, CP>(sm, c, r, tw);
   float facc[2] = {0.f, 0.f};  // a thread sums RW L / 256 points (2-4) in FP32
-  for (int q = tid; q < RW * L; q += 256) {
-    const int w = q / L, k = q - w * L;
-    const int64_t row = row0 + w;
-    if (row >= nrows) continue;
-    const int ny = (int)a.len[1], rowi = (int)row;
-    const int64_t yy = rowi % ny, zz = rowi / ny;
-    V v[8];
+  if (dim == 3) {
+    for (int q = tid; q < RW * L; q += 256) {
+      const int w = q / L, k = q - w * L;
+      if (row0 + w >= nrows) continue;
+      V v[8];
 #pragma unroll
-    for (int pp = 0; pp < 8; ++pp)
-      if (pp < P) v[pp] = sm[w * P + pp + CP * k];
-    weights_point<float>(dim, a, k, yy, zz, ms, v, facc);
+      for (int pp = 0; pp < 8; ++pp) v[pp] = sm[w * 8 + pp + CP * k];
+      weights_bcc_row(a, k, rowc[w], ms, v, facc);
+    }
+  } else {
+    for (int q = tid; q < RW * L; q += 256) {
+      const int w = q / L, k = q - w * L;
+      const int64_t row = row0 + w;
+      if (row >= nrows) continue;
+      const int ny = (int)a.len[1], rowi = (int)row;
+      const int64_t yy = rowi % ny, zz = rowi / ny;
+      V v[8];
+#pragma unroll
+      for (int pp = 0; pp < 8; ++pp)
+        if (pp < P) v[pp] = sm[w * P + pp + CP * k];
+      weights_point<float>(dim, a, k, yy, zz, ms, v, facc);
+    }
   }
   // warp sums in FP32 (64 points), the eight warp sums in FP64 in a fixed order: an FP64
   // block reduction per thread would cost more than the thread's points here
@@ -807,7 +965,7 @@ qw_status launch_weights_x(const Geometry& g, const SpecAxes& ax, double n, doub
                            const void* tw_line, double* partials, cudaStream_t st) {
   constexpr int L = R1 * R2, TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
   constexpr int CP = (C % 2 == 0) ? C + 1 : C;
-  const size_t smem = (size_t)L * CP * sizeof(float2);
+  const size_t smem = fused_rowc_offset(L, CP) + 8 * sizeof(float4);  // lines, then up to 8 row constants
   const qw_status sa = smem_attr(weights_x_kernel<R1, R2>, (int)smem);
   if (sa != QW_OK) return sa;
   weights_x_kernel<R1, R2><<<(unsigned)fused_x_ctas<R1, R2>(g), 256, smem, st>>>(

@@ -8,7 +8,8 @@
 //     D_k^t = cos(omega_k t) I - i sin(omega_k t) G^_k ,
 // the Chebyshev form (sin(omega t)/sin(omega) = U_{t-1}(cos omega)).
 // omega_k = atan2(sin omega_k, n u_k) (the paper's arccos(n u_k), Sec. 3.2) is
-// tabulated once per plan: complex128 plans hold it as a double-double (~1e-31,
+// tabulated once per plan (BCC: for q0 only, see below): complex128 plans hold it as a
+// double-double (~1e-31,
 // qw_dd.cuh), so the phase omega_k t reduced modulo 2 pi carries ~1e-16 of
 // rounding at any t instead of t ulp(omega_k); complex64 plans hold nu = omega/2pi
 // as an FP32 pair for an FP32 phase.  Where sin(omega_k) = 0 (m = 0 and
@@ -18,7 +19,9 @@
 // wave vector kappa in [0, 2 pi)^3 hold the two BCC wave vectors
 // q0 = kappa/2 and q1 = kappa/2 + (pi, 0, 0); with a = exp(i (k1+k2+k3)/2),
 //     c0 = (Psi^0 + a* Psi^1)/2,  c1 = (Psi^0 - a* Psi^1)/2,
-// each evolves with its own D_q^t, and Psi^0 = c0 + c1, Psi^1 = a (c0 - c1).
+// each evolves with its own D_q^t, and Psi^0 = c0 + c1, Psi^1 = a (c0 - c1).  q1 flips
+// the signs of u and n~, so omega_q1 = pi - omega_q0 and D_q1^t = (-1)^t Gamma D_q0^t Gamma
+// (Gamma = diag(I, -I)): the tables and G^ serve q0 alone.
 // This is the paper's two-rectangular-DFT reduction written for the
 // exp(-i k.x) forward convention.
 #include <cuda_runtime.h>
@@ -60,15 +63,12 @@ __global__ void omega_split_kernel(int dim, AxesDev a, double n, double m, float
     const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
     int64_t f[3], fs;
     wave_vectors(dim, x, y, z, a, f, fs);
-    const int nq = dim == 3 ? 2 : 1;
-    for (int q = 0; q < nq; ++q) {
-      double u, nx, ny, nz;
-      symbol_tab<double>(dim, a, f[0], f[1], f[2], q, u, nx, ny, nz);
-      const double sw = sqrt(m * m + n * n * (nx * nx + ny * ny + nz * nz));
-      const double nu = atan2(sw, n * u) * 0.15915494309189533577;
-      const float hi = (float)nu;
-      nu_out[idx * nq + q] = make_float2(hi, (float)(nu - (double)hi));
-    }
+    double u, nx, ny, nz;
+    symbol_tab<double>(dim, a, f[0], f[1], f[2], 0, u, nx, ny, nz);
+    const double sw = sqrt(m * m + n * n * (nx * nx + ny * ny + nz * nz));
+    const double nu = atan2(sw, n * u) * 0.15915494309189533577;
+    const float hi = (float)nu;
+    nu_out[idx] = make_float2(hi, (float)(nu - (double)hi));
   }
 }
 
@@ -100,10 +100,9 @@ __global__ void omega_dd_kernel(int dim, AxesDev a, double m, const double2* __r
   const int64_t idx = (z * a.len[1] + y) * a.len[0] + x;
   int64_t f[3], fs;
   wave_vectors(dim, x, y, z, a, f, fs);
-  const int nq = dim == 3 ? 2 : 1;
   const dd n = dd{nbox->x, nbox->y};
   const dd m2 = dd_two_prod(m, m), n2 = dd_mul(n, n);
-  for (int q = 0; q < nq; ++q) {
+  {
     dd u, t1, t2, t3;  // u_k and n~_k (Eqs. weyl1d, weyl2d, weyl3d)
     if (dim == 1) {
       dd c, s;
@@ -128,10 +127,6 @@ __global__ void omega_dd_kernel(int dim, AxesDev a, double m, const double2* __r
       dd_from4(tab0[f[0]], cx, sx);
       dd_from4(tab1[f[1]], cy, sy);
       dd_from4(tab2[f[2]], cz, sz);
-      if (q) {
-        cx = dd_neg(cx);
-        sx = dd_neg(sx);
-      }
       u = dd_add(dd_mul(dd_mul(cx, cy), cz), dd_mul(dd_mul(sx, sy), sz));
       t1 = dd_sub(dd_mul(dd_mul(sx, cy), cz), dd_mul(dd_mul(cx, sy), sz));
       t2 = dd_add(dd_mul(dd_mul(cx, sy), cz), dd_mul(dd_mul(sx, cy), sz));
@@ -140,7 +135,7 @@ __global__ void omega_dd_kernel(int dim, AxesDev a, double m, const double2* __r
     const dd nt2 = dd_add(dd_add(dd_mul(t1, t1), dd_mul(t2, t2)), dd_mul(t3, t3));
     const dd S = dd_sqrt(dd_add(m2, dd_mul(n2, nt2)));  // sin omega
     const dd w = dd_omega(S, dd_mul(n, u), anch);
-    omega[idx * nq + q] = make_double2(w.hi, w.lo);
+    omega[idx] = make_double2(w.hi, w.lo);
   }
 }
 

@@ -175,6 +175,20 @@ def test_config_bcc128_spectral_t1000(qb, dtype):
     assert err <= TOL[dtype]
 
 
+@pytest.mark.parametrize("m,t", [(0.0, 5), (1.0, 5), (0.19, 7), (0.19, 8), (0.19, (1 << 24) + 3)])
+def test_bcc_fused_x_pass_vs_oracle(qb, m, t):
+    """BCC N = 128 in complex64 takes the fused x pass (x length 64) with its row-factored
+    symbol: degenerate masses (sin omega_k = 0 at some k for m = 0), odd and even t (the
+    (-1)^t of the second half spectrum), and t >= 2^24 (FP64 phase instead of the split nu)."""
+    N = 128
+    a = inputs.random_field(3, N, seed=29)
+    got = run_spectral(qb, 3, N, m, "c64", a, t)
+    exp = walk.to_device(3, N, spectral.evolve(3, m, walk.from_device(3, N, a.astype(np.complex64).astype(complex)), t))
+    err = rel_l2(got, exp)
+    print("BCC128 fused x pass m=%g t=%d c64 rel-L2 %.3e" % (m, t, err))
+    assert err <= TOL["c64"]
+
+
 @pytest.mark.parametrize("m", [0.01, 0.1, 0.3])
 @pytest.mark.parametrize("t", [10 ** 4, 10 ** 6])
 def test_config3_like_long_times_vs_oracle(qb, m, t):
