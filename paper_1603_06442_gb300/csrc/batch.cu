@@ -87,6 +87,9 @@ struct BatchDebug {
 
 constexpr long long kBatchSpin = 1ll << 24;
 constexpr int kBatchThreads = 256;   // plain (depth-1) launches
+// plain launches: CTAs per SM the register budget is cut for (64 registers, no spills; 6 and 3
+// CTAs, and cells taken two at a time, measured 2-15% slower on the uneven 256-walk mix)
+constexpr int kBatchMinBlocks = 4;
 constexpr int kFusedThreads = 256;   // launches with fused rounds (512 measured slower: 172 vs 232 G on the chain)
 
 // Largest i in [0, n) with a[i] <= v (a ascending, a[0] <= v), searched by the 32 lanes
@@ -259,6 +262,43 @@ __device__ __forceinline__ void fused_round(const BatchWalk& W, const int (&t3)[
   }
 }
 
+// U psi at site (x, y, z) of coset c: r[0..ncomp) and the index of its first output
+// component (component q at i + q vol, vol the sites of one coset).
+__device__ __forceinline__ int site_result(const BatchWalk& W, int c, int x, int y, int z, const float2* in,
+                                           float2 (&r)[4]) {
+  const int nx = W.n[0];
+  if (W.dim == 1) {
+    float2 r2[2];
+    core_1d<false>(in + wrapm<int>(x - 1, nx), in + wrapm<int>(x + 1, nx), in + x, nx, r2, W.cf);
+    r[0] = r2[0];
+    r[1] = r2[1];
+    return x;
+  }
+  if (W.dim == 2) {
+    const int vol = nx * nx, i = y * nx + x;
+    const int xm = wrapm<int>(x - 1, nx), xp = wrapm<int>(x + 1, nx);
+    const int ym = wrapm<int>(y - 1, nx), yp = wrapm<int>(y + 1, nx);
+    core_2d<false>(in + y * nx + xm, in + y * nx + xp, in + ym * nx + x, in + yp * nx + x, in + i, vol, r, W.cf);
+    return i;
+  }
+  const int M = nx, plane = M * M, vol = plane * M;
+  const int xa = wrapm<int>(x - 1 + c, M), xb = wrapm<int>(x + c, M);
+  const int ya = wrapm<int>(y - 1 + c, M), yb = wrapm<int>(y + c, M);
+  const int za = wrapm<int>(z - 1 + c, M), zb = wrapm<int>(z + c, M);
+  const int i = z * plane + y * M + x;
+  core_3d<false>(in + (1 - c) * 4 * vol, plane, M, za, zb, ya, yb, xa, xb, vol, in + c * 4 * vol + i, r, W.cf);
+  return c * 4 * vol + i;
+}
+
+__device__ __forceinline__ void site_store(const BatchWalk& W, int i, const float2 (&r)[4], float2* out) {
+  out[i] = r[0];
+  out[i + W.vol] = r[1];
+  if (W.ncomp == 4) {
+    out[i + 2 * W.vol] = r[2];
+    out[i + 3 * W.vol] = r[3];
+  }
+}
+
 // The plain round of tile (t0, t1, t2): every cell of the tile (both cosets) updated once
 // from global memory, or (copy round) copied from buf[1] to buf[0].
 template <int NT>
@@ -275,12 +315,10 @@ __device__ __forceinline__ void plain_round(const BatchWalk& W, const int (&t3)[
       if (copy) {
         const int64_t base = (int64_t)c * W.ncomp * W.vol + ((int64_t)z * ny + y) * nx + x;
         for (int q = 0; q < W.ncomp; ++q) out[base + (int64_t)q * W.vol] = in[base + (int64_t)q * W.vol];
-      } else if (W.dim == 1) {
-        site_update_1d<float, false, int>(in, out, nx, x, W.cf);
-      } else if (W.dim == 2) {
-        site_update_2d<float, false, int>(in, out, nx, x, y, W.cf);
       } else {
-        site_update_3d<float, false, int>(in, out, nx, c, z, y, x, W.cf);
+        float2 r[4];
+        const int i = site_result(W, c, x, y, z, in, r);
+        site_store(W, i, r, out);
       }
     });
   }
@@ -289,7 +327,7 @@ __device__ __forceinline__ void plain_round(const BatchWalk& W, const int (&t3)[
 // FUSED = false: every walk has depth 1 (no shared memory, high occupancy);
 // FUSED = true: walks of depth >= 2 run fused rounds in dynamic shared memory.
 template <bool FUSED>
-__global__ void __launch_bounds__(FUSED ? kFusedThreads : kBatchThreads, FUSED ? 3 : 6)
+__global__ void __launch_bounds__(FUSED ? kFusedThreads : kBatchThreads, FUSED ? 3 : kBatchMinBlocks)
     batch_kernel(const BatchWalk* __restrict__ walks, const BatchGroup* __restrict__ groups,
                  const int64_t* __restrict__ group_item0, int ngroups, const int64_t* __restrict__ tile_prefix,
                  const int64_t* __restrict__ round_prefix, int64_t total_items, unsigned int* __restrict__ done,
