@@ -515,6 +515,15 @@ static qw_status fft_plan_t(FftPlan* f, const Geometry& g, TableDst* dst) {
       set_error("spectral path needs 2^a 3^b axis lengths (got %lld)", (long long)L);
       return QW_EINVAL;
     }
+    if (L == 1) {  // the DFT of length 1 is the identity: no pass
+      FftAxis& A = f->axis[ax];
+      A.nparts = 1;
+      A.part[0] = 1;
+      A.part[1] = A.part[2] = 1;
+      A.first = f->npass;
+      A.count = 0;
+      continue;
+    }
     std::vector<int> parts;
     if (!split_axis<T>(L, maxline, &parts)) {
       set_error("axis length %lld cannot be split into <= 3 passes of <= %d", (long long)L, maxline);
@@ -592,6 +601,7 @@ qw_status fft_plan_create(FftPlan* f, const Geometry& g, qw_dtype dt, TableDst* 
   *f = FftPlan();
   f->dtype = dt;
   f->external_tables = dst != nullptr;
+  f->field_bytes = (size_t)g.elems * (dt == QW_C64 ? 8 : 16);
   qw_status st = dt == QW_C64 ? fft_plan_t<float>(f, g, dst) : fft_plan_t<double>(f, g, dst);
   if (st != QW_OK) return st;
   return trig_tables(f, g, dst);
@@ -668,6 +678,8 @@ qw_status fft_forward_axis(const FftPlan& f, int ax, void* data, cudaStream_t st
 
 qw_status fft_forward_axis_from(const FftPlan& f, int ax, const void* src, void* dst, cudaStream_t st) {
   const FftAxis& A = f.axis[ax];
+  if (A.count == 0 && src != dst)
+    QW_CHECK_CUDA(cudaMemcpyAsync(dst, src, f.field_bytes, cudaMemcpyDeviceToDevice, st));
   for (int q = 0; q < A.count; ++q) {
     const FftPass& p = f.pass[A.first + q];
     const void* from = q == 0 ? src : nullptr;

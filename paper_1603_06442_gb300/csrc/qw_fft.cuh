@@ -61,6 +61,8 @@ struct FftPlan {
   void* trigdf[3] = {nullptr, nullptr, nullptr};
   void* angdf = nullptr;
   bool external_tables = false;  // tables carved from a caller's region (not freed here)
+  size_t field_bytes = 0;        // one field (an axis of length 1 has no pass: an out-of-place
+                                 // transform along it is a copy)
 };
 
 // Destination of a plan's tables when they are not cudaMalloc'd: a region of device
