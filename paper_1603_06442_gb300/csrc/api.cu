@@ -186,8 +186,15 @@ static qw_status prepare_spectral(qw_plan_s* p) {
   // (omega as a double-double); BCC stores q0 of each cell only
   QW_CHECK_CUDA(cudaMalloc(&p->omega, (p->dtype == QW_C64 ? 8 : 16) * p->g.vol));
   QW_CHECK_CUDA(cudaMalloc(&p->spec_partials, sizeof(double) * 2 * kObsBlocks));
-  if (fused_x_supported(p->g, p->fft, p->dtype))
+  if (fused_x_supported(p->g, p->fft, p->dtype)) {
     QW_CHECK_CUDA(cudaMalloc(&p->xw_partials, sizeof(double) * 2 * fused_x_grid(p->g)));
+    // the observables' first pass (outermost axis, from the field) also takes norm and <x>
+    const int64_t ctas = fft_moment_ctas(p->fft, p->g.dim - 1);
+    if (ctas > 0) {
+      QW_CHECK_CUDA(cudaMalloc(&p->zm_partials, sizeof(double) * 4 * ctas));
+      p->zm_ctas = ctas;
+    }
+  }
   st = launch_omega_table(p->g, spec_axes(p->g, p->fft), p->n, p->mass, p->omega, 0, p->dtype == QW_C64);
   if (st != QW_OK) return st;
   QW_CHECK_CUDA(cudaDeviceSynchronize());
@@ -300,6 +307,7 @@ qw_status qw_plan_destroy(qw_plan p) {
   if (p->omega) cudaFree(p->omega);
   if (p->spec_partials) cudaFree(p->spec_partials);
   if (p->xw_partials) cudaFree(p->xw_partials);
+  if (p->zm_partials) cudaFree(p->zm_partials);
   for (int b = 0; b < 2; ++b) {
     if (p->hbuf[b]) cudaFree(p->hbuf[b]);
     if (p->ev_copied[b]) cudaEventDestroy(p->ev_copied[b]);
@@ -547,19 +555,31 @@ qw_status qw_sync(qw_plan p, void* stream) {
 static qw_status obs_enqueue(qw_plan_s* p, const void* psi, cudaStream_t s, double* host_dst, bool* kspace_out) {
   if (debug_poison())
     QW_CHECK_CUDA(cudaMemsetAsync(p->scratch, kPoisonByte, (size_t)p->g.elems * p->elem_bytes, s));
-  qw_status st = launch_position_moments(p->g, p->dtype, psi, p->red_partials, p->red_result, s);
-  if (st != QW_OK) return st;
   // particle weights need the spectrum (computed into the scratch field)
   const bool kspace = fft_size_ok(p->g.nx) && fft_size_ok(p->g.ny) && fft_size_ok(p->g.nz);
   *kspace_out = kspace;
+  qw_status st = QW_OK;
   if (kspace) {
     st = prepare_spectral(p);
     if (st != QW_OK) return st;
+  }
+  if (!(kspace && p->xw_partials && p->zm_ctas > 0)) {
+    st = launch_position_moments(p->g, p->dtype, psi, p->red_partials, p->red_result, s);
+    if (st != QW_OK) return st;
+  }
+  if (kspace) {
     const SpecAxes ax = spec_axes(p->g, p->fft);
     if (p->xw_partials) {
-      // the outermost axis reads psi and writes the scratch field, the middle axis works in
-      // place, and the x transform is done in shared memory by the weights kernel itself
-      st = fft_forward_axis_from(p->fft, p->g.dim - 1, psi, p->scratch, s);
+      // the outermost axis reads psi and writes the scratch field (taking norm and <x> of psi
+      // on the way where it can), the middle axis works in place, and the x transform is done
+      // in shared memory by the weights kernel itself
+      if (p->zm_ctas > 0) {
+        const FftMoments mom{p->g.dim, (int)p->g.nx, p->g.s, p->zm_partials};
+        st = fft_forward_axis_from_moments(p->fft, p->g.dim - 1, psi, p->scratch, mom, s);
+        if (st == QW_OK) st = launch_fold_moments(p->zm_partials, p->zm_ctas, p->red_result, s);
+      } else {
+        st = fft_forward_axis_from(p->fft, p->g.dim - 1, psi, p->scratch, s);
+      }
       for (int a = p->g.dim - 2; a >= 1 && st == QW_OK; --a) st = fft_forward_axis(p->fft, a, p->scratch, s);
       if (st != QW_OK) return st;
       st = launch_weights_fused_x(p->g, ax, p->fft, p->n, p->mass, p->scratch, p->xw_partials, p->red_result + 4, s);

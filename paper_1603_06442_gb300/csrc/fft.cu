@@ -22,6 +22,7 @@
 
 #include <cmath>
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "qw_fft.cuh"
@@ -171,11 +172,14 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(typename Cx<T>::t* __rest
   }
 }
 
-template <typename T, bool INV, int R1, int R2, bool CONTIG>
+// MOM (forward strided passes of the observables): the position moments of the loaded lines
+// (FftMoments) are summed before the transform, one partial per CTA.
+template <typename T, bool INV, int R1, int R2, bool CONTIG, bool MOM = false>
 __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* data, const typename Cx<T>::t* src, FftPass p,
                                                     const typename Cx<T>::t* __restrict__ tw_line,
                                                     const typename Cx<T>::t* __restrict__ tw_hi,
-                                                    const typename Cx<T>::t* __restrict__ tw_lo) {
+                                                    const typename Cx<T>::t* __restrict__ tw_lo,
+                                                    FftMoments mom = FftMoments{}) {
   using V = typename Cx<T>::t;
   constexpr int L = R1 * R2;
   constexpr int TPL = R1 > R2 ? R1 : R2;  // threads per line
@@ -234,7 +238,58 @@ __global__ void __launch_bounds__(256) fft2f_kernel(typename Cx<T>::t* data, con
     }
   }
   __syncthreads();
+  __shared__ float mom_wsum[MOM ? 8 : 1][4];  // MOM: the warp sums, combined after the transform
+  if constexpr (MOM) {
+    // this thread's elements n = r + TPL j of line l: |v|^2 and the four sums in FP32 (the axis
+    // coordinate from the local index j), FP32 warp sums, the CTA's eight warp sums in FP64 (an
+    // FP64 operation costs ~64 FP32 ones here)
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    if (live) {
+      constexpr int NL = (L + TPL - 1) / TPL;
+      float g0 = 0.f, g1 = 0.f;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        const int n = r + TPL * j;
+        if (n < L) {
+          const V v = sm[c + CP * n];
+          const float d = v.x * v.x + v.y * v.y;
+          g0 += d;
+          g1 = fmaf((float)j, d, g1);
+        }
+      }
+      const int o = (int)(l / S), i = (int)(l - (int64_t)o * S);  // plane (coset * s + component), position
+      const float an = fmaf((float)r, g0, (float)TPL * g1);          // sum n d
+      a[0] = g0;
+      if (mom.dim == 3) {
+        const float off = (float)(o / mom.s);
+        a[1] = (2.f * (float)(i % mom.nx) + off) * g0;
+        a[2] = (2.f * (float)(i / mom.nx) + off) * g0;
+        a[3] = fmaf(2.f, an, off * g0);
+      } else {  // 2D: lines along y at x = i
+        a[1] = (float)i * g0;
+        a[2] = an;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int w = 16; w > 0; w >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], w);
+    if ((tid & 31) == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) mom_wsum[tid >> 5][q] = a[q];
+    }
+  }
   reg_fft_steps<T, INV, R1, R2, CP>(sm, c, r, tw);
+  if constexpr (MOM) {  // the transform's barriers have published the warp sums
+    if (tid == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double acc = 0.0;
+        for (int w = 0; w < 8; ++w) acc += (double)mom_wsum[w][q];
+        mom.partials[(int64_t)blockIdx.x * 4 + q] = acc;
+      }
+    }
+  }
   // ---- store
   if (CONTIG) {
     constexpr int NE = (C * L + 255) / 256;
@@ -285,6 +340,70 @@ static qw_status launch_2f(const FftPass& p, void* data, const void* src, cudaSt
   }
   QW_CHECK_LAUNCH("fft two-factor pass launch");
   return QW_OK;
+}
+
+// f(R1, R2) (as integral constants) for a register length L >= 64; false for other lengths.
+template <typename F>
+static bool with_reg_factors64(int L, F&& f) {
+  switch (L) {
+#define QW_2FF(LEN, A, B)                                                           \
+  case LEN:                                                                         \
+    if constexpr (LEN >= 64) {                                                      \
+      f(std::integral_constant<int, A>{}, std::integral_constant<int, B>{});        \
+      return true;                                                                  \
+    }                                                                               \
+    return false;
+    QW_REG_LENGTHS_POW2(QW_2FF)
+    QW_REG_LENGTHS_F32(QW_2FF)
+#undef QW_2FF
+    default:
+      return false;
+  }
+}
+
+// The moments-taking pass is a forward, untwiddled, strided complex64 register pass.
+static bool moment_pass_ok(const FftPlan& f, int ax) {
+  if (f.dtype != QW_C64 || ax < 0 || ax > 2) return false;
+  const FftAxis& A = f.axis[ax];
+  if (A.count != 1) return false;
+  const FftPass& p = f.pass[A.first];
+  return p.S > 1 && !p.twiddle && with_reg_factors64(p.L, [](auto, auto) {});
+}
+
+int64_t fft_moment_ctas(const FftPlan& f, int ax) {
+  if (!moment_pass_ok(f, ax)) return 0;
+  const FftPass& p = f.pass[f.axis[ax].first];
+  int64_t ctas = 0;
+  with_reg_factors64(p.L, [&](auto a, auto b) {
+    constexpr int TPL = decltype(a)::value > decltype(b)::value ? decltype(a)::value : decltype(b)::value;
+    constexpr int C = 256 / TPL;
+    ctas = (p.O * p.S + C - 1) / C;
+  });
+  return ctas;
+}
+
+qw_status fft_forward_axis_from_moments(const FftPlan& f, int ax, const void* src, void* dst, const FftMoments& m,
+                                        cudaStream_t st) {
+  if (!moment_pass_ok(f, ax)) {
+    set_error("moments pass: axis %d is not a single strided complex64 register pass", ax);
+    return QW_EINVAL;
+  }
+  const FftPass& p = f.pass[f.axis[ax].first];
+  qw_status out = QW_OK;
+  with_reg_factors64(p.L, [&](auto a, auto b) {
+    constexpr int R1 = decltype(a)::value, R2 = decltype(b)::value;
+    constexpr int L = R1 * R2, TPL = R1 > R2 ? R1 : R2, C = 256 / TPL;
+    const size_t smem = (size_t)L * ((C % 2 == 0) ? C + 1 : C) * sizeof(float2);
+    const int64_t grid = (p.O * p.S + C - 1) / C;
+    out = smem_attr(fft2f_kernel<float, false, R1, R2, false, true>, (int)smem);
+    if (out != QW_OK) return;
+    fft2f_kernel<float, false, R1, R2, false, true><<<(unsigned)grid, 256, smem, st>>>(
+        static_cast<float2*>(dst), static_cast<const float2*>(src), p, static_cast<const float2*>(p.tw_line),
+        static_cast<const float2*>(p.tw_hi), static_cast<const float2*>(p.tw_lo), m);
+    const cudaError_t e = cudaGetLastError();
+    out = e == cudaSuccess ? QW_OK : cuda_fail(e, "fft moments pass launch");
+  });
+  return out;
 }
 
 // Lengths with a two-factor register kernel; returns false for the generic path.

@@ -357,4 +357,45 @@ qw_status launch_position_moments(const Geometry& g, qw_dtype dt, const void* ps
   return QW_OK;
 }
 
+// Four sums from nblk partials of four doubles: one CTA of 1024 threads, each with four
+// independent chains (a fixed order, so deterministic).
+constexpr int kFold4Threads = 1024;
+__global__ void __launch_bounds__(kFold4Threads) fold4_kernel(const double* __restrict__ partials, int64_t nblk,
+                                                              double* __restrict__ result) {
+  const double4* p = reinterpret_cast<const double4*>(partials);
+  double a[4][4] = {};
+  int64_t b = threadIdx.x;
+  for (; b + 3 * kFold4Threads < nblk; b += 4 * kFold4Threads) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const double4 v = p[b + u * kFold4Threads];
+      a[u][0] += v.x;
+      a[u][1] += v.y;
+      a[u][2] += v.z;
+      a[u][3] += v.w;
+    }
+  }
+  for (; b < nblk; b += kFold4Threads) {
+    const double4 v = p[b];
+    a[0][0] += v.x;
+    a[0][1] += v.y;
+    a[0][2] += v.z;
+    a[0][3] += v.w;
+  }
+  double acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = (a[0][q] + a[1][q]) + (a[2][q] + a[3][q]);
+  block_sum<4, kFold4Threads>(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) result[q] = acc[q];
+  }
+}
+
+qw_status launch_fold_moments(const double* partials, int64_t nblk, double* result, cudaStream_t st) {
+  fold4_kernel<<<1, kFold4Threads, 0, st>>>(partials, nblk, result);
+  QW_CHECK_LAUNCH("fold launch");
+  return QW_OK;
+}
+
 }  // namespace qw

@@ -35,6 +35,16 @@ struct FftPass {
   void* tw_lo = nullptr;
 };
 
+// Position moments taken by the out-of-place first pass of an axis while it holds its
+// source in shared memory (observables): per CTA the FP64 sums (n, sum X d, sum Y d,
+// sum Z d), d = |psi_q(x)|^2 of the CTA's lines, X physical (BCC: 2 m + c).
+struct FftMoments {
+  int dim;
+  int nx;
+  int s;              // spinor components per coset
+  double* partials;   // 4 doubles per CTA
+};
+
 struct FftAxis {
   int nparts;       // 1..3 digits of the axis length
   int part[3];
@@ -94,5 +104,12 @@ qw_status fft_inverse_axis(const FftPlan& f, int ax, void* data, cudaStream_t st
 // Forward passes of one axis reading src and writing dst (the first pass out of place,
 // the rest in place on dst); src is not modified.
 qw_status fft_forward_axis_from(const FftPlan& f, int ax, const void* src, void* dst, cudaStream_t st);
+// CTAs of the moments-taking form of fft_forward_axis_from along axis ax: 0 when it has none
+// (complex64 axes transformed in one register pass with a stride, i.e. not the x axis).
+int64_t fft_moment_ctas(const FftPlan& f, int ax);
+// fft_forward_axis_from that also writes the position moments of src (FftMoments) into
+// m.partials, fft_moment_ctas(f, ax) CTAs of four doubles; QW_EINVAL where that is 0.
+qw_status fft_forward_axis_from_moments(const FftPlan& f, int ax, const void* src, void* dst, const FftMoments& m,
+                                        cudaStream_t st);
 
 }  // namespace qw

@@ -164,6 +164,8 @@ qw_status launch_position_moments2(const Geometry& g, qw_dtype dt, const void* p
                                    double* result, cudaStream_t st);
 qw_status launch_position_moments(const Geometry& g, qw_dtype dt, const void* psi, double* partials,
                                   double* result, cudaStream_t st);
+// The same four sums from nblk partials of four doubles (the FFT pass that takes them).
+qw_status launch_fold_moments(const double* partials, int64_t nblk, double* result, cudaStream_t st);
 
 // ---- spectral path (spectral.cu) ---------------------------------------------
 struct SpecAxes {  // digit split of each axis (storage order -> frequency) and trig tables
@@ -248,6 +250,8 @@ struct qw_plan_s {
                         // (16 B) for complex128, nu = omega / 2 pi as an FP32 pair (8 B) for complex64
   double* spec_partials;  // 2 * kObsBlocks doubles for the particle-weight reduction
   double* xw_partials;    // 2 doubles per CTA of the x-pass weights (when the x pass is fused)
+  double* zm_partials;    // 4 doubles per CTA of the first forward pass of the observables, when it
+  int64_t zm_ctas;        // takes the norm and <x> of the field it reads (0: a separate kernel does)
   double* red_partials; // 10 * kMom2MaxBlocks doubles (>= 4 * kObsBlocks)
   double* red_result;   // 16 doubles (device)
   double* red_host;     // 16 doubles (pinned host); the last holds the copied error word
