@@ -280,10 +280,11 @@ def run_ours(args, rank, world, local):
     stencil_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
     ms = max_over_ranks(total_ms, world, dev)
     value = job_value(sites, S, args.steps, world, ms)
-    # stencil launches (S / fused, S even) + moments/fold + the z and y FFT passes + the x-pass
-    # weights kernel/fold (the x transform happens inside the weights kernel)
+    # stencil launches (S / fused, S even) + the observables: the z FFT pass (which also takes norm
+    # and <x>) and its two-stage fold, the y pass, the x-pass weights kernel (the x transform happens
+    # inside it) and its two-stage fold
     stencil_launches = (S + fused - 1) // fused
-    launches_per_step = stencil_launches + 2 + 2 + 2
+    launches_per_step = stencil_launches + 3 + 1 + 3
 
     # end-to-end through the C ABI with host buffers: qw_run_host copies every step's field
     # from pinned host memory, runs S steps and reads the observables back to the host; the

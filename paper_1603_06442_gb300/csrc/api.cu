@@ -187,11 +187,11 @@ static qw_status prepare_spectral(qw_plan_s* p) {
   QW_CHECK_CUDA(cudaMalloc(&p->omega, (p->dtype == QW_C64 ? 8 : 16) * p->g.vol));
   QW_CHECK_CUDA(cudaMalloc(&p->spec_partials, sizeof(double) * 2 * kObsBlocks));
   if (fused_x_supported(p->g, p->fft, p->dtype)) {
-    QW_CHECK_CUDA(cudaMalloc(&p->xw_partials, sizeof(double) * 2 * fused_x_grid(p->g)));
+    QW_CHECK_CUDA(cudaMalloc(&p->xw_partials, sizeof(double) * 2 * (fused_x_grid(p->g) + kFoldCtas)));
     // the observables' first pass (outermost axis, from the field) also takes norm and <x>
     const int64_t ctas = fft_moment_ctas(p->fft, p->g.dim - 1);
     if (ctas > 0) {
-      QW_CHECK_CUDA(cudaMalloc(&p->zm_partials, sizeof(double) * 4 * ctas));
+      QW_CHECK_CUDA(cudaMalloc(&p->zm_partials, sizeof(double) * 4 * (ctas + kFoldCtas)));
       p->zm_ctas = ctas;
     }
   }
@@ -576,7 +576,8 @@ static qw_status obs_enqueue(qw_plan_s* p, const void* psi, cudaStream_t s, doub
       if (p->zm_ctas > 0) {
         const FftMoments mom{p->g.dim, (int)p->g.nx, p->g.s, p->zm_partials};
         st = fft_forward_axis_from_moments(p->fft, p->g.dim - 1, psi, p->scratch, mom, s);
-        if (st == QW_OK) st = launch_fold_moments(p->zm_partials, p->zm_ctas, p->red_result, s);
+        if (st == QW_OK)
+          st = launch_fold_partials(p->zm_partials, p->zm_ctas, 4, p->zm_partials + 4 * p->zm_ctas, p->red_result, s);
       } else {
         st = fft_forward_axis_from(p->fft, p->g.dim - 1, psi, p->scratch, s);
       }

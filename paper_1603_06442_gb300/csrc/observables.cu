@@ -357,43 +357,59 @@ qw_status launch_position_moments(const Geometry& g, qw_dtype dt, const void* ps
   return QW_OK;
 }
 
-// Four sums from nblk partials of four doubles: one CTA of 1024 threads, each with four
-// independent chains (a fixed order, so deterministic).
-constexpr int kFold4Threads = 1024;
-__global__ void __launch_bounds__(kFold4Threads) fold4_kernel(const double* __restrict__ partials, int64_t nblk,
-                                                              double* __restrict__ result) {
-  const double4* p = reinterpret_cast<const double4*>(partials);
-  double a[4][4] = {};
-  int64_t b = threadIdx.x;
-  for (; b + 3 * kFold4Threads < nblk; b += 4 * kFold4Threads) {
+// K sums over nblk partials [nblk][K], in a fixed order: CTA b of the grid folds the partials
+// [b nblk / G, (b + 1) nblk / G) into out[b][K] (two chains per thread, then a block sum).
+template <int K>
+__global__ void __launch_bounds__(kObsThreads) fold_range_kernel(const double* __restrict__ partials, int64_t nblk,
+                                                                 double* __restrict__ out) {
+  const int64_t b0 = (int64_t)blockIdx.x * nblk / gridDim.x, b1 = ((int64_t)blockIdx.x + 1) * nblk / gridDim.x;
+  double a0[K], a1[K];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const double4 v = p[b + u * kFold4Threads];
-      a[u][0] += v.x;
-      a[u][1] += v.y;
-      a[u][2] += v.z;
-      a[u][3] += v.w;
+  for (int q = 0; q < K; ++q) a0[q] = a1[q] = 0.0;
+  int64_t b = b0 + threadIdx.x;
+  for (; b + kObsThreads < b1; b += 2 * kObsThreads) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      a0[q] += partials[b * K + q];
+      a1[q] += partials[(b + kObsThreads) * K + q];
     }
   }
-  for (; b < nblk; b += kFold4Threads) {
-    const double4 v = p[b];
-    a[0][0] += v.x;
-    a[0][1] += v.y;
-    a[0][2] += v.z;
-    a[0][3] += v.w;
-  }
-  double acc[4];
+  for (; b < b1; b += kObsThreads) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) acc[q] = (a[0][q] + a[1][q]) + (a[2][q] + a[3][q]);
-  block_sum<4, kFold4Threads>(acc);
+    for (int q = 0; q < K; ++q) a0[q] += partials[b * K + q];
+  }
+  double acc[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) acc[q] = a0[q] + a1[q];
+  block_sum<K, kObsThreads>(acc);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) result[q] = acc[q];
+    for (int q = 0; q < K; ++q) out[(int64_t)blockIdx.x * K + q] = acc[q];
   }
 }
 
-qw_status launch_fold_moments(const double* partials, int64_t nblk, double* result, cudaStream_t st) {
-  fold4_kernel<<<1, kFold4Threads, 0, st>>>(partials, nblk, result);
+qw_status launch_fold_partials(const double* partials, int64_t nblk, int K, double* stage, double* result,
+                               cudaStream_t st) {
+  if (K != 2 && K != 4) {
+    set_error("fold of %d sums", K);
+    return QW_EINVAL;
+  }
+  const bool two = nblk > 4 * kObsThreads;  // many partials: kFoldCtas CTAs first, then one
+  const double* src = partials;
+  int64_t n = nblk;
+  if (two) {
+    if (K == 2)
+      fold_range_kernel<2><<<kFoldCtas, kObsThreads, 0, st>>>(partials, nblk, stage);
+    else
+      fold_range_kernel<4><<<kFoldCtas, kObsThreads, 0, st>>>(partials, nblk, stage);
+    QW_CHECK_LAUNCH("fold launch");
+    src = stage;
+    n = kFoldCtas;
+  }
+  if (K == 2)
+    fold_range_kernel<2><<<1, kObsThreads, 0, st>>>(src, n, result);
+  else
+    fold_range_kernel<4><<<1, kObsThreads, 0, st>>>(src, n, result);
   QW_CHECK_LAUNCH("fold launch");
   return QW_OK;
 }

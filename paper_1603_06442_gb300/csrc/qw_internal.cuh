@@ -164,8 +164,11 @@ qw_status launch_position_moments2(const Geometry& g, qw_dtype dt, const void* p
                                    double* result, cudaStream_t st);
 qw_status launch_position_moments(const Geometry& g, qw_dtype dt, const void* psi, double* partials,
                                   double* result, cudaStream_t st);
-// The same four sums from nblk partials of four doubles (the FFT pass that takes them).
-qw_status launch_fold_moments(const double* partials, int64_t nblk, double* result, cudaStream_t st);
+// K (2 or 4) sums over nblk partials [nblk][K] into result, in a fixed order; with many partials
+// kFoldCtas CTAs fold ranges into stage (K * kFoldCtas doubles) first.
+constexpr int kFoldCtas = 64;
+qw_status launch_fold_partials(const double* partials, int64_t nblk, int K, double* stage, double* result,
+                               cudaStream_t st);
 
 // ---- spectral path (spectral.cu) ---------------------------------------------
 struct SpecAxes {  // digit split of each axis (storage order -> frequency) and trig tables
@@ -194,7 +197,7 @@ qw_status launch_evolve_fused_x(const Geometry& g, const SpecAxes& ax, const Fft
                                 const double* norm0 = nullptr);
 // With the same tiling, the particle-weight sums of a spectrum still to be transformed
 // along x (complex64): 2 doubles per CTA (fused_x_grid CTAs) into partials, folded into
-// result[0..1]; data is only read.
+// result[0..1] through the 2 * kFoldCtas doubles after them; data is only read.
 int64_t fused_x_grid(const Geometry& g);
 qw_status launch_weights_fused_x(const Geometry& g, const SpecAxes& ax, const FftPlan& f, double n, double m,
                                  const void* data, double* partials, double* result, cudaStream_t st);
@@ -249,9 +252,11 @@ struct qw_plan_s {
   double* omega;        // omega_k per stored wave vector (BCC: q0 of each cell): a double-double
                         // (16 B) for complex128, nu = omega / 2 pi as an FP32 pair (8 B) for complex64
   double* spec_partials;  // 2 * kObsBlocks doubles for the particle-weight reduction
-  double* xw_partials;    // 2 doubles per CTA of the x-pass weights (when the x pass is fused)
+  double* xw_partials;    // 2 doubles per CTA of the x-pass weights (when the x pass is fused), then
+                          // 2 * kFoldCtas for the fold's first stage
   double* zm_partials;    // 4 doubles per CTA of the first forward pass of the observables, when it
-  int64_t zm_ctas;        // takes the norm and <x> of the field it reads (0: a separate kernel does)
+  int64_t zm_ctas;        // takes the norm and <x> of the field it reads (0: a separate kernel does),
+                          // then 4 * kFoldCtas for the fold's first stage
   double* red_partials; // 10 * kMom2MaxBlocks doubles (>= 4 * kObsBlocks)
   double* red_result;   // 16 doubles (device)
   double* red_host;     // 16 doubles (pinned host); the last holds the copied error word

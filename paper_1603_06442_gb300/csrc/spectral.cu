@@ -502,9 +502,9 @@ qw_status launch_weights_fused_x(const Geometry& g, const SpecAxes& ax, const Ff
       return QW_EINVAL;
   }
   if (s2 != QW_OK) return s2;
-  fold2_kernel<<<1, kFoldThreads, 0, st>>>(partials, (int)fused_x_grid(g), result);
-  QW_CHECK_LAUNCH("x-pass weights fold launch");
-  return QW_OK;
+  // partials holds 2 * (CTAs + kFoldCtas) doubles: the CTAs' pairs, then the fold's first stage
+  const int64_t nblk = fused_x_grid(g);
+  return launch_fold_partials(partials, nblk, 2, partials + 2 * nblk, result, st);
 }
 
 qw_status launch_particle_weights(const Geometry& g, const SpecAxes& ax, qw_dtype dt, double n, double m,
