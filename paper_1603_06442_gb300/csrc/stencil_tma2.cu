@@ -182,15 +182,18 @@ struct Step1Src {
   float *p1c1, *p1c0;                  // psi1 destinations: coset 1 at L1, coset 0 at L1 + 1
 };
 
+// A thread's two psi1 pair results are written after both pair steps: the stores and the next
+// pair's loads touch the same shared array, so the compiler keeps a store in order before them;
+// with the stores last, both steps' loads can overlap (0.7% faster per launch at BCC N=512).
 __device__ __forceinline__ void step1(const Step1Src& s, Row3 (&k1)[2][2], Row3 (&k0)[2][2], bool first,
                                       const Coef32& cf, int tx, int ty, int tid) {
-  float4 res[4];
+  float4 res1[4], res0[4];
   // coset 1: la = coset 0 at L1 (h_z = +1), lb = coset 0 at L1 + 1, own coset 1 at L1
-  pair_step<1, 0>(k1, first, s.c0a, s.c0b, s.c1a, ty, tx, cf, res);
-  store_smem<0>(s.p1c1, ty, tx, res);
+  pair_step<1, 0>(k1, first, s.c0a, s.c0b, s.c1a, ty, tx, cf, res1);
   // coset 0 at L1 + 1: la = coset 1 at L1, lb = coset 1 at L1 + 1, own coset 0 at L1 + 1
-  pair_step<0, 2>(k0, first, s.c1a, s.c1b, s.c0b, ty + 1, tx, cf, res);
-  store_smem<2>(s.p1c0, ty + 1, tx, res);
+  pair_step<0, 2>(k0, first, s.c1a, s.c1b, s.c0b, ty + 1, tx, cf, res0);
+  store_smem<0>(s.p1c1, ty, tx, res1);
+  store_smem<2>(s.p1c0, ty + 1, tx, res0);
   // remainder, one warp per kind: warp 0 coset 1 row TY2, warp 1 coset 0 row TY2 + 1,
   // warp 2 coset 1 pair k = 32 of rows 0..TY2, warp 3 coset 0 pair k = 32 of rows 1..TY2+1
   const int w = tid >> 5;
@@ -200,12 +203,12 @@ __device__ __forceinline__ void step1(const Step1Src& s, Row3 (&k1)[2][2], Row3 
     const int kk = col ? 32 : tx;
     if ((w & 1) == 0) {
       const int R = col ? tx : TY2;
-      pair_step<1, 0>(tmp, true, s.c0a, s.c0b, s.c1a, R, kk, cf, res);
-      store_smem<0>(s.p1c1, R, kk, res);
+      pair_step<1, 0>(tmp, true, s.c0a, s.c0b, s.c1a, R, kk, cf, res1);
+      store_smem<0>(s.p1c1, R, kk, res1);
     } else {
       const int R = col ? tx + 1 : TY2 + 1;
-      pair_step<0, 2>(tmp, true, s.c1a, s.c1b, s.c0b, R, kk, cf, res);
-      store_smem<2>(s.p1c0, R, kk, res);
+      pair_step<0, 2>(tmp, true, s.c1a, s.c1b, s.c0b, R, kk, cf, res1);
+      store_smem<2>(s.p1c0, R, kk, res1);
     }
   }
 }
