@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 # (14,155,776 sites), per site.  Traffic grows in proportion to the sites, so bench.py reports
 # sites x this figure; kernels without a capture get null.
 NCU_TRAFFIC_BYTES_PER_SITE = {"step3d_c64_tma_kernel": (469785600 + 409331968) / 14155776,
-                              "step3d_c64_tma2_kernel": (476947968 + 407557376) / 14155776}
+                              "step3d_c64_tma2_kernel": (476398848 + 408239360) / 14155776}
 
 
 def parse():
