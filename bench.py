@@ -253,12 +253,12 @@ def run_ours(args, rank, world, local):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    # warm-up (the first qw_run_host call also allocates the plan's two host-run device fields;
-    # two fields pass through both of them)
+    # warm-up (the first qw_run_host call also allocates the plan's three host-run device fields;
+    # three fields pass through all of them)
     for _ in range(args.warmup):
         plan.step(psi, S, stream)
         plan.observables(psi, stream)
-    plan.run_host([host, host], S, stream=stream)
+    plan.run_host([host, host, host], S, stream=stream)
     barrier()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
@@ -290,10 +290,12 @@ def run_ours(args, rank, world, local):
     # from pinned host memory, runs S steps and reads the observables back to the host; the
     # library copies the next step's field on its own copy stream while this one computes.
     e2e_steps = max(2, args.steps)
-    # warm-up of the end-to-end path: a pinned buffer left idle copies several times slower
-    # on its first transfer (measured up to 65 ms against 5.1 ms for the 1.07 GB field), and
-    # a run's first copy has nothing to overlap with
-    plan.run_host([host, host], S, stream=stream)
+    # warm-up of the end-to-end path right before it is timed: a pinned buffer left idle (here
+    # through the device-timed steps) copies several times slower on its first transfer
+    # (measured 7-65 ms against 5.1 ms for the 1.07 GB field), and a run's first copy has
+    # nothing to overlap with
+    for _ in range(args.warmup):
+        plan.run_host([host, host, host], S, stream=stream)
     barrier()
     t0 = time.perf_counter()
     plan.run_host([host] * e2e_steps, S, stream=stream)
@@ -363,7 +365,7 @@ def run_ours(args, rank, world, local):
                 "h2d_bytes_per_step": field_bytes, "d2h_bytes_per_step": 48, "ms_per_step": e2e_ms,
                 "h2d_GBps": h2d_GBps, "api": "qw_run_host", "overlap": overlap,
                 "note": "pinned host field copied every step inside qw_run_host; the library copies the next "
-                        "step's field on its copy stream while this one computes (two device buffers)"},
+                        "fields' copies on its copy stream while this one computes (three device buffers)"},
         "gpu_launches": args.steps * launches_per_step,
         "clocks": clocks.summary(),
         "final_obs": obs,

@@ -256,10 +256,11 @@ int64_t qw_projection_elems(qw_plan plan, int keep);
  * nsteps applications of the update rule (as qw_step) and compute its
  * observables into out[j] (as qw_observables).  If psi_out_host is not NULL,
  * psi_out_host[j] (host memory, same size; may equal psi_host[j]) receives the
- * evolved field.  The fields pass through two device buffers owned by the plan
- * (allocated by the first call, freed with the plan): the copy of field j + 1
- * runs on the plan's copy stream while field j is advanced on `stream`, and the
- * read-back of field j on the copy stream overlaps field j + 1.  Synchronous:
+ * evolved field.  The fields pass through three device buffers owned by the
+ * plan (allocated by the first call, freed with the plan): the copy of field
+ * j + 2 starts on the plan's copy stream once field j - 1's observables are done
+ * and runs while field j is advanced on `stream`, so a transfer has two steps to
+ * land; the read-back of field j on the copy stream overlaps field j + 1.  Synchronous:
  * returns when every result is on the host.  count = 0 does nothing.
  * Errors: QW_EINVAL (null plan, count < 0, nsteps < 0, null psi_host / out or a
  * null entry), QW_ENOMEM (device buffers), QW_ECUDA, QW_ETIMEOUT (as qw_sync). */

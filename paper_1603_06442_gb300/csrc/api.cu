@@ -308,7 +308,7 @@ qw_status qw_plan_destroy(qw_plan p) {
   if (p->spec_partials) cudaFree(p->spec_partials);
   if (p->xw_partials) cudaFree(p->xw_partials);
   if (p->zm_partials) cudaFree(p->zm_partials);
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < kHostBufs; ++b) {
     if (p->hbuf[b]) cudaFree(p->hbuf[b]);
     if (p->ev_copied[b]) cudaEventDestroy(p->ev_copied[b]);
     if (p->ev_freed[b]) cudaEventDestroy(p->ev_freed[b]);
@@ -709,7 +709,7 @@ static qw_status host_run_setup(qw_plan_s* p) {
   if (p->copy_stream) return QW_OK;
   const size_t bytes = (size_t)p->g.elems * p->elem_bytes;
   cudaError_t e = cudaSuccess;
-  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+  for (int b = 0; b < kHostBufs && e == cudaSuccess; ++b) {
     // written once here, so that a run's first copy into each buffer is not the first
     // write into freshly allocated device memory
     if (!p->hbuf[b]) {
@@ -752,10 +752,13 @@ qw_status qw_run_host(qw_plan p, const void* const* psi_host, void* const* psi_o
   if (st != QW_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream), cs = p->copy_stream;
   const size_t bytes = (size_t)p->g.elems * p->elem_bytes;
-  // field j lives in hbuf[j % 2]; on the copy stream: in(0), in(1), out(0), in(2), out(1), ...
-  // in(j + 2) waits for field j's observables (ev_freed) and follows out(j) in stream order.
-  // Field j's sums go to the pinned stage j % 2; the host reads them only after field
-  // j + 1's step is enqueued, so the device never waits for the host between fields.
+  // field j lives in hbuf[j % NB] (NB = kHostBufs = 3); on the copy stream: in(0), in(1),
+  // then per field j: in(j + 2), out(j).  in(j + 2) waits for field j - 1's observables (its
+  // buffer's previous field) and follows out(j - 1) in stream order, so it overlaps field j's
+  // step and has until field j + 2's step to land.  Field j's sums go to the pinned stage
+  // j % 2; the host reads them only after field j + 1's step is enqueued, so the device never
+  // waits for the host between fields.
+  constexpr int NB = kHostBufs;
   const bool timing = p->host_timing;
   if (timing) {
     while ((int)p->tev.size() < 5 * count) {
@@ -769,21 +772,25 @@ qw_status qw_run_host(qw_plan p, const void* const* psi_host, void* const* psi_o
   auto mark = [&](int j, int i, cudaStream_t on) -> cudaError_t {
     return timing ? cudaEventRecord(p->tev[5 * j + i], on) : cudaSuccess;
   };
-  QW_CHECK_CUDA(mark(0, 0, cs));
-  QW_CHECK_CUDA(cudaMemcpyAsync(p->hbuf[0], psi_host[0], bytes, cudaMemcpyHostToDevice, cs));
-  QW_CHECK_CUDA(mark(0, 1, cs));
-  QW_CHECK_CUDA(cudaEventRecord(p->ev_copied[0], cs));
+  // the copy of field k into its buffer, with its completion event
+  auto copy_in = [&](int k) -> qw_status {
+    const int kb = k % NB;
+    QW_CHECK_CUDA(mark(k, 0, cs));
+    QW_CHECK_CUDA(cudaMemcpyAsync(p->hbuf[kb], psi_host[k], bytes, cudaMemcpyHostToDevice, cs));
+    QW_CHECK_CUDA(mark(k, 1, cs));
+    QW_CHECK_CUDA(cudaEventRecord(p->ev_copied[kb], cs));
+    return QW_OK;
+  };
+  for (int k = 0; k < NB - 1 && k < count; ++k)
+    if ((st = copy_in(k)) != QW_OK) return st;
   bool kspace = false;
   int done = 0;  // fields whose observables are on the host
   for (int j = 0; j < count && st == QW_OK; ++j) {
-    const int b = j & 1;
-    if (j + 1 < count) {
-      const int nb = b ^ 1;
-      if (j >= 1) QW_CHECK_CUDA(cudaStreamWaitEvent(cs, p->ev_freed[nb], 0));
-      QW_CHECK_CUDA(mark(j + 1, 0, cs));
-      QW_CHECK_CUDA(cudaMemcpyAsync(p->hbuf[nb], psi_host[j + 1], bytes, cudaMemcpyHostToDevice, cs));
-      QW_CHECK_CUDA(mark(j + 1, 1, cs));
-      QW_CHECK_CUDA(cudaEventRecord(p->ev_copied[nb], cs));
+    const int b = j % NB;
+    if (j + NB - 1 < count) {
+      // field j + NB - 1 reuses field j - 1's buffer (none before the first field)
+      if (j >= 1) QW_CHECK_CUDA(cudaStreamWaitEvent(cs, p->ev_freed[(j - 1) % NB], 0));
+      if ((st = copy_in(j + NB - 1)) != QW_OK) break;
     }
     QW_CHECK_CUDA(cudaStreamWaitEvent(s, p->ev_copied[b], 0));
     QW_CHECK_CUDA(mark(j, 2, s));
@@ -795,18 +802,18 @@ qw_status qw_run_host(qw_plan p, const void* const* psi_host, void* const* psi_o
       QW_CHECK_CUDA(cudaStreamWaitEvent(cs, p->ev_stepped[b], 0));
       QW_CHECK_CUDA(cudaMemcpyAsync(psi_out_host[j], p->hbuf[b], bytes, cudaMemcpyDeviceToHost, cs));
     }
-    st = obs_enqueue(p, p->hbuf[b], s, p->hstage + 8 * b, &kspace);
+    st = obs_enqueue(p, p->hbuf[b], s, p->hstage + 8 * (j & 1), &kspace);
     if (st != QW_OK) break;
     QW_CHECK_CUDA(cudaEventRecord(p->ev_freed[b], s));
     QW_CHECK_CUDA(mark(j, 4, s));
     if (timing) p->tev_fields = j + 1;
     if (j >= 1) {  // the previous field's sums
-      const cudaError_t e = cudaEventSynchronize(p->ev_freed[b ^ 1]);
+      const cudaError_t e = cudaEventSynchronize(p->ev_freed[(j - 1) % NB]);
       if (e != cudaSuccess) {
         st = cuda_fail(e, "qw_run_host: observables");
         break;
       }
-      obs_fill(p, p->hstage + 8 * (b ^ 1), kspace, &out[j - 1]);
+      obs_fill(p, p->hstage + 8 * ((j - 1) & 1), kspace, &out[j - 1]);
       done = j;
     }
   }

@@ -230,6 +230,10 @@ qw_status launch_particle_weights(const Geometry& g, const SpecAxes& ax, qw_dtyp
 }  // namespace qw
 
 // ---- the plan ---------------------------------------------------------------
+// Device fields of a host-field run: field j lives in buffer j % kHostBufs, so a field's copy
+// can start two steps before its step (a slow transfer has two steps to finish).
+constexpr int kHostBufs = 3;
+
 struct qw_plan_s {
   qw::Geometry g;
   double mass;
@@ -260,11 +264,11 @@ struct qw_plan_s {
   double* red_partials; // 10 * kMom2MaxBlocks doubles (>= 4 * kObsBlocks)
   double* red_result;   // 16 doubles (device)
   double* red_host;     // 16 doubles (pinned host); the last holds the copied error word
-  // host-field runs (qw_run_host): two device fields, a copy stream and its events,
+  // host-field runs (qw_run_host): kHostBufs device fields, a copy stream and its events,
   // allocated by the first call
-  void* hbuf[2];
+  void* hbuf[kHostBufs];
   cudaStream_t copy_stream;
-  cudaEvent_t ev_copied[2], ev_freed[2], ev_stepped[2];
+  cudaEvent_t ev_copied[kHostBufs], ev_freed[kHostBufs], ev_stepped[kHostBufs];
   double* hstage;  // 2 x 8 doubles (pinned): observables of the two fields in flight
   // optional per-field timing of qw_run_host: for field j, events (timing enabled) at its copy's
   // start and end (copy stream) and at its step's start and end and its observables' end

@@ -38,7 +38,7 @@ CASES += [(3, 128, "c64", 6)]
 def test_run_host_matches_oracle(qb, dim, N, dtype, t):
     npdt = np.complex64 if dtype == "c64" else np.complex128
     m = 0.3
-    count = 3
+    count = 7  # every one of the three device buffers and both observables stages reused
     fields = [np.ascontiguousarray(inputs.random_field(dim, N, seed=70 + j).astype(npdt)) for j in range(count)]
     # one pageable numpy field, the others page-locked torch tensors
     hosts = [fields[0]] + [torch.from_numpy(f.copy()).pin_memory() for f in fields[1:]]
